@@ -1,0 +1,203 @@
+"""FP64 CPU oracle for the near-field force: TEST INFRASTRUCTURE ONLY.
+
+The oracle is the plain, slow reference the CUDA path is checked against
+(binning, near-field accelerations, their adjoint, and a local energy for
+finite differences).  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import it.  The product path never calls
+it and shares no code with it.
+
+The arithmetic lives in ``nf_oracle.c`` (plain C, FP64, OpenMP over sinks),
+compiled here with ``-O2 -ffp-contract=off`` so no FMA contraction changes the
+binning's rounding.  Each function below cites what it follows in the paper
+(Garrison et al., "The Abacus Cosmological N-body Code"):
+
+* :func:`bin_particles` - cell-centred FP32 offsets on the K^3 grid
+  (Sec. "Force Accuracy" overview; Sec. "Two-Stage Execution").
+* :func:`forces` - near-field sum over the (2R+1)^3 neighbour cells with the
+  spline softening of Eq. (spline), eps_s = 2.16 eps_p (Sec. "Force Softening";
+  Sec. "GPU Near-Field Computation").
+* :func:`adjoint` - gradient of L = sum_i g_i . a_i (not in the paper; the
+  derivative of the sum above).
+* :func:`local_energy` - the part of L that depends on one particle, for
+  finite differences with frozen cell assignment.
+
+Every function has at least one pin in ``tests/test_oracle_pins.py`` against
+closed forms, brute force, symmetry or the paper's printed values.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "nf_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_nf_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2 -fopenmp -ffp-contract=off)."""
+    if force or not os.path.exists(_LIB_PATH) or \
+            os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+               "-std=c11", "-o", tmp, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = ctypes.CDLL(_LIB_PATH)
+    P = ctypes.c_void_p
+    i64, i32, f64 = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    lib.oracle_bin.restype = i64
+    lib.oracle_bin.argtypes = [P, i64, f64, i32, P, P, P, P]
+    lib.oracle_forces.restype = i32
+    lib.oracle_forces.argtypes = [P, i64, f64, i32, i32, f64, P, i64, P, i32]
+    lib.oracle_adjoint.restype = i32
+    lib.oracle_adjoint.argtypes = [P, P, i64, f64, i32, i32, f64, P, i64, P, i32]
+    lib.oracle_local_energy.restype = i32
+    lib.oracle_local_energy.argtypes = [P, P, i64, f64, i32, i32, f64, P, i64, P, P]
+    lib.oracle_wrapped_positions.restype = i32
+    lib.oracle_wrapped_positions.argtypes = [P, i64, f64, i32, P]
+    lib.oracle_num_threads.restype = i32
+    lib.oracle_num_threads.argtypes = []
+    _lib = lib
+    return lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _pos(pos) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(pos, dtype=np.float32))
+    assert a.ndim == 2 and a.shape[1] == 3
+    return a
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+def bin_particles(pos, box: float, K: int):
+    """Stable binning: returns (cell_offsets int32[K^3+1], rel float32[N,4], perm int32[N]).
+
+    rel[:, :3] are FP32 offsets from the cell centre in cell units; rel[:, 3]
+    holds the bits of the original index.  Raises on non-finite input.
+    """
+    pos = _pos(pos)
+    N = pos.shape[0]
+    off = np.zeros(K ** 3 + 1, np.int32)
+    rel = np.zeros((max(N, 1), 4), np.float32)
+    perm = np.zeros(max(N, 1), np.int32)
+    bad = _load().oracle_bin(_p(pos), N, float(box), int(K), _p(off), _p(rel), _p(perm), None)
+    if bad:
+        raise ValueError(f"{bad} non-finite coordinates")
+    return off, rel[:N], perm[:N]
+
+
+def cell_of(pos, box: float, K: int) -> np.ndarray:
+    """Linear cell index (cx*K + cy)*K + cz of every particle, input order."""
+    pos = _pos(pos)
+    N = pos.shape[0]
+    off = np.zeros(K ** 3 + 1, np.int32)
+    rel = np.zeros((max(N, 1), 4), np.float32)
+    perm = np.zeros(max(N, 1), np.int32)
+    cid = np.zeros(max(N, 1), np.int32)
+    bad = _load().oracle_bin(_p(pos), N, float(box), int(K), _p(off), _p(rel), _p(perm), _p(cid))
+    if bad:
+        raise ValueError(f"{bad} non-finite coordinates")
+    return cid[:N]
+
+
+def forces(pos, box: float, K: int, R: int, eps: float,
+           sinks: Optional[np.ndarray] = None, threads: int = 0) -> np.ndarray:
+    """Near-field accelerations in FP64, [N, 3] (or [len(sinks), 3]).
+
+    eps is the Plummer-equivalent softening in box units; mass 1/N, G = 1.
+    """
+    pos = _pos(pos)
+    N = pos.shape[0]
+    s = None if sinks is None else np.ascontiguousarray(np.asarray(sinks, np.int64))
+    n = N if s is None else s.shape[0]
+    out = np.zeros((max(n, 1), 3), np.float64)
+    rc = _load().oracle_forces(_p(pos), N, float(box), int(K), int(R), float(eps),
+                               None if s is None else _p(s), n, _p(out), int(threads))
+    if rc:
+        raise ValueError("non-finite coordinates")
+    return out[:n]
+
+
+def adjoint(pos, g, box: float, K: int, R: int, eps: float,
+            sinks: Optional[np.ndarray] = None, threads: int = 0) -> np.ndarray:
+    """dL/dx for L = sum_i g_i . a_i, FP64 [N, 3] (or at the listed sinks)."""
+    pos = _pos(pos)
+    N = pos.shape[0]
+    gg = np.ascontiguousarray(np.asarray(g, np.float64).reshape(N, 3))
+    s = None if sinks is None else np.ascontiguousarray(np.asarray(sinks, np.int64))
+    n = N if s is None else s.shape[0]
+    out = np.zeros((max(n, 1), 3), np.float64)
+    rc = _load().oracle_adjoint(_p(pos), _p(gg), N, float(box), int(K), int(R), float(eps),
+                                None if s is None else _p(s), n, _p(out), int(threads))
+    if rc:
+        raise ValueError("non-finite coordinates")
+    return out[:n]
+
+
+def local_energy(pos, g, box: float, K: int, R: int, eps: float,
+                 ks: np.ndarray, xk: np.ndarray) -> np.ndarray:
+    """L_k with particle ks[q] moved to the FP64 position xk[q] (cells frozen)."""
+    pos = _pos(pos)
+    N = pos.shape[0]
+    gg = np.ascontiguousarray(np.asarray(g, np.float64).reshape(N, 3))
+    ks = np.ascontiguousarray(np.asarray(ks, np.int64))
+    xk = np.ascontiguousarray(np.asarray(xk, np.float64).reshape(ks.shape[0], 3))
+    out = np.zeros(max(ks.shape[0], 1), np.float64)
+    rc = _load().oracle_local_energy(_p(pos), _p(gg), N, float(box), int(K), int(R), float(eps),
+                                     _p(ks), ks.shape[0], _p(xk), _p(out))
+    if rc:
+        raise ValueError("non-finite coordinates")
+    return out[:ks.shape[0]]
+
+
+def wrapped_positions(pos, box: float, K: int) -> np.ndarray:
+    """FP64 positions moved into [0, box) by whole boxes, as the force sums use them."""
+    pos = _pos(pos)
+    out = np.zeros((max(pos.shape[0], 1), 3), np.float64)
+    if _load().oracle_wrapped_positions(_p(pos), pos.shape[0], float(box), int(K), _p(out)):
+        raise ValueError("non-finite coordinates")
+    return out[:pos.shape[0]]
+
+
+def fd_gradient(pos, g, box: float, K: int, R: int, eps: float, ks: np.ndarray,
+                h: float = 1e-6) -> np.ndarray:
+    """Central finite differences of the local energy, step h (box units), [len(ks), 3]."""
+    xw = wrapped_positions(pos, box, K)
+    ks = np.asarray(ks, np.int64)
+    grad = np.zeros((ks.shape[0], 3))
+    for d in range(3):
+        xp = xw[ks].copy()
+        xm = xw[ks].copy()
+        xp[:, d] += h
+        xm[:, d] -= h
+        lp = local_energy(pos, g, box, K, R, eps, ks, xp)
+        lm = local_energy(pos, g, box, K, R, eps, ks, xm)
+        grad[:, d] = (lp - lm) / (2.0 * h)
+    return grad
+
+
+def frac_error(a: np.ndarray, ref: np.ndarray) -> np.ndarray:
+    """|a_i - ref_i|_2 / |ref_i|_2 per particle (no floor)."""
+    a = np.asarray(a, np.float64)
+    ref = np.asarray(ref, np.float64)
+    return np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
