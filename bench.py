@@ -1,0 +1,499 @@
+#!/usr/bin/env python
+"""Benchmark of the near-field force path on GB300 (one JSON line on stdout).
+
+Step: one forward pass (nf_forces: binning, work list, pair kernel, FP64
+combine) plus one adjoint pass (nf_forces_adjoint) over the clustered
+128^3 workload (2,097,152 particles, K = 32, R = 2, eps = 1/(40 * 128)),
+inputs resident in HBM.  `value` counts the pair interactions the step computes
+(P forward + P adjoint, P = sum_c n_c S_c) per second of device time.  L2 is
+flushed (a 512 MB write) before every timed step; each step is bracketed by
+CUDA events on the launching stream.
+
+Also reported, from the same run:
+  roofline      the forward pair kernel against the FP32 peak (23 flop per pair)
+  bin_roofline  the binning stage against the measured HBM copy bandwidth
+  e2e           the same step through the public API from pinned host buffers
+  batched       64 boxes (the batched recipe) in one captured CUDA graph
+  error         fractional force error of this run's output on the oracle sample
+  cpu_baseline  the FP64 oracle on the host cores, on a bounded sample of sinks
+
+With --gpus N > 1 (torchrun, one rank per GPU) every rank runs its own box
+(seed offset by rank): weak scaling, no data-path communication.
+`--impl reference` times the FP64 CPU oracle as it stands instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "near-field pair-interactions/s on 1 GB300: fwd, fwd+adjoint, batched; at stated error"
+UNIT = "pair-interactions/s"
+FLOP_PER_PAIR = 23  # convention fixed for this metric (the paper quotes ~26 incl. rsqrt)
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="clustered", choices=["plain", "clustered", "large", "adjoint"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle CPU baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tune", default=None, help="sinks_per_lane,stage,warps,blocks_per_sm")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_workload(name: str, rank: int):
+    import workloads as W
+    if name == "plain":
+        w = W.config_plain(seed=0 + 1000 * rank)
+    elif name == "clustered":
+        w = W.config_clustered(seed=1 + 1000 * rank)
+    elif name == "large":
+        w = W.config_large(seed=2 + 1000 * rank)
+    else:
+        w = W.config_adjoint(seed=3 + 1000 * rank)
+    g = W.upstream_gradient(w.N, 33 + 1000 * rank)
+    return w, g
+
+
+def describe(w) -> str:
+    return (f"{w.name}: N={w.N} {'clustered recipe' if w.name != 'plain' else 'uniform'}, "
+            f"K={w.K}, R={w.R}, eps={w.eps:.6g} (Plummer-equivalent), unit box")
+
+
+# ---------------------------------------------------------------------------
+# pair counts (measurement only: P = sum_c n_c S_c from cell occupancies)
+# ---------------------------------------------------------------------------
+
+def stencil_sums(counts: np.ndarray, R: int) -> np.ndarray:
+    """S_c = sum of occupancies over the (2R+1)^3 cells around every cell."""
+    S = np.zeros_like(counts, dtype=np.int64)
+    c64 = counts.astype(np.int64)
+    for a in range(-R, R + 1):
+        for b in range(-R, R + 1):
+            for c in range(-R, R + 1):
+                S += np.roll(c64, (a, b, c), axis=(0, 1, 2))
+    return S
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = bus_id
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "100"]
+            if self.bus_id:
+                cmd += ["-i", self.bus_id]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r.split(",") for r in out.strip().splitlines() if r.count(",") >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        # several GPUs visible to nvidia-smi: keep the one that drew the most power
+        by_gpu = {}
+        for r in rows:
+            by_gpu.setdefault(r[0].strip(), []).append(r)
+
+        def mean_power(rs):
+            v = [float(r[4]) for r in rs if r[4].strip() not in ("[N/A]", "N/A")]
+            return float(np.mean(v)) if v else 0.0
+
+        rows = max(by_gpu.values(), key=mean_power)
+        sm = [float(r[2]) for r in rows]
+        mx = max(float(r[3]) for r in rows)
+        power = [float(r[4]) for r in rows if r[4].strip() not in ("[N/A]", "N/A")]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[6 + k].strip() == "Active"})
+        loaded = [s for s in sm if s > 0.5 * mx] or sm
+        return {"sm_mhz": float(np.median(loaded)), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------------------
+# oracle CPU baseline (test infrastructure, host cores)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(w, g, seconds: float, seed: int = 22):
+    """Time the FP64 oracle (forces + adjoint) on a random sample of sinks sized
+    to about `seconds` of host work.  Returns (stats dict, sinks, acc_ref)."""
+    import oracle
+    off, _, _ = oracle.bin_particles(w.pos, w.box, w.K)
+    counts = np.diff(off).reshape(w.K, w.K, w.K)
+    S = stencil_sums(counts, w.R).reshape(-1)
+    cid = oracle.cell_of(w.pos, w.box, w.K)
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(w.N)
+    g64 = g.astype(np.float64)
+    # calibrate on a small sample
+    n0 = min(w.N, 256)
+    t0 = time.perf_counter()
+    oracle.forces(w.pos, w.box, w.K, w.R, w.eps, sinks=np.sort(order[:n0]))
+    oracle.adjoint(w.pos, g64, w.box, w.K, w.R, w.eps, sinks=np.sort(order[:n0]))
+    dt0 = time.perf_counter() - t0
+    pairs0 = 2 * int(S[cid[order[:n0]]].sum())
+    rate0 = pairs0 / max(dt0, 1e-6)
+    # per-call set-up (binning of all N) is part of the oracle's time as it stands
+    n = int(min(w.N, max(n0, n0 * seconds / max(dt0, 1e-3) * 0.8)))
+    sinks = np.sort(order[:n])
+    t0 = time.perf_counter()
+    acc_ref = oracle.forces(w.pos, w.box, w.K, w.R, w.eps, sinks=sinks)
+    oracle.adjoint(w.pos, g64, w.box, w.K, w.R, w.eps, sinks=sinks)
+    dt = time.perf_counter() - t0
+    pairs = 2 * int(S[cid[sinks]].sum())
+    del rate0
+    return ({"value": pairs / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+             "sample": f"forces + adjoint for {n} random sinks (seed {seed}) of {w.N}; "
+                       f"{pairs:.3e} pair interactions in {dt:.1f} s, FP64, OpenMP"},
+            sinks, acc_ref)
+
+
+# ---------------------------------------------------------------------------
+# native arm
+# ---------------------------------------------------------------------------
+
+def run_native(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+    import paper_2110_11392_gb300 as nf
+    from paper_2110_11392_gb300 import _lib
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    if args.tune:
+        _lib.nf_set_default_tuning(tuple(int(x) for x in args.tune.split(",")))
+
+    w, g_np = make_workload(args.workload, rank)
+    N = w.N
+    pos = torch.from_numpy(w.pos).to(dev)
+    g = torch.from_numpy(g_np).to(dev)
+    ws = torch.empty(_lib.nf_workspace_bytes(N, w.K, w.R), dtype=torch.uint8, device=dev)
+    acc = torch.empty_like(pos)
+    grad = torch.empty_like(pos)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        _lib.nf_forces(pos, w.box, w.K, w.R, w.eps, acc, None, ws)
+        _lib.nf_forces_adjoint(pos, g, w.box, w.K, w.R, w.eps, grad, ws)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st = _lib.nf_stats_read(ws)
+    P = st["pairs"]
+
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(dev).pci_bus_id  # type: ignore[attr-defined]
+    except Exception:
+        bus = None
+    clocks = ClockSampler(bus if isinstance(bus, str) else None)
+
+    # ---- timed region: device time of exactly K steps, L2 flushed before each
+    _lib.nf_profile_enable(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    prof_fwd, prof_adj = [], []
+    launches0 = _lib.nf_kernel_launches()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+        prof_fwd.append(_lib.nf_profile_read(1))
+        prof_adj.append(_lib.nf_profile_read(0))
+    torch.cuda.synchronize()
+    launches = _lib.nf_kernel_launches() - launches0
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    _lib.nf_profile_enable(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_total = sum(step_ms) / 1e3
+    t_max = t_total
+    pairs_all = 2 * P * args.steps
+    if world > 1:
+        t = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        pp = torch.tensor([pairs_all], dtype=torch.float64, device=dev)
+        dist.all_reduce(pp, op=dist.ReduceOp.SUM)
+        pairs_all = float(pp.item())
+    value = pairs_all / t_max
+
+    fwd_pair_ms = float(np.mean([p["pair_ms"] for p in prof_fwd]))
+    adj_pair_ms = float(np.mean([p["pair_ms"] for p in prof_adj]))
+    fwd_ms = float(np.mean([p["total_ms"] for p in prof_fwd]))
+    adj_ms = float(np.mean([p["total_ms"] for p in prof_adj]))
+    bin_ms = float(np.mean([p["bin_ms"] for p in prof_fwd]))
+
+    # ---- roofline of the forward pair kernel (FP32 issue-bound: "alu")
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    max_mhz = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    fp32_peak = sms * 128 * 2 * max_mhz * 1e6 / 1e12  # TFLOP/s, 128 FP32 lanes/SM, FMA = 2 flop
+    achieved = FLOP_PER_PAIR * P / (fwd_pair_ms / 1e3) / 1e12
+    traffic = kernel_traffic("force")
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": traffic,
+                "kernel": "k_force (forward pair loop)",
+                "peak_basis": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x {max_mhz:.0f} MHz max SM clock",
+                "frac_at_sampled_clock": (achieved / (sms * 256 * clk["sm_mhz"] * 1e6 / 1e12)
+                                          if clk.get("sm_mhz") else None),
+                "flop_per_pair": FLOP_PER_PAIR}
+    hbm = peaks.get("hbm_gbs", 6786.2)
+    bin_bytes = 32.0 * N + 8.0 * (w.K ** 3 + 1)
+    bin_roof = {"bound": "hbm", "achieved": bin_bytes / (bin_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": bin_bytes / (bin_ms / 1e3) / 1e9 / hbm, "traffic": kernel_traffic("bin"),
+                "bytes_per_particle": 32, "note": "algorithmic bytes: pos 12 + rel 16 + perm 4 per particle + offsets"}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": describe(w), "pairs_per_pass": P, "pairs_per_step": 2 * P,
+                   "step": "nf_forces + nf_forces_adjoint", "l2": "flushed (512 MB write) before each step",
+                   "parallelism": f"replicas: one box per GPU x {world}",
+                   "tuning": list(_lib.nf_get_default_tuning())},
+        "fwd": {"pairs_per_s": P / (fwd_ms / 1e3), "particle_updates_per_s": N / (fwd_ms / 1e3),
+                "ms": fwd_ms, "pair_kernel_ms": fwd_pair_ms, "bin_ms": bin_ms},
+        "fwd_adjoint": {"pairs_per_s": P / ((fwd_ms + adj_ms) / 1e3), "ms": fwd_ms + adj_ms,
+                        "adjoint_pair_kernel_ms": adj_pair_ms, "over_fwd": (fwd_ms + adj_ms) / fwd_ms},
+        "roofline": roofline, "bin_roofline": bin_roof,
+        "gpu_launches": int(launches), "clocks": clk,
+        "stats": {"max_cell_occupancy": st["max_occupancy"], "work_items": st["items"],
+                  "lane_utilisation": st["pairs"] / max(st["lane_pairs"], 1)},
+    }
+
+    if not args.no_e2e:
+        out["e2e"] = measure_e2e(args, w, g_np, dev, P, flush)
+    if not args.no_batched and rank == 0:
+        out["batched"] = measure_batched(dev, flush)
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        cb, sinks, ref = oracle_sample(w, g_np, args.cpu_seconds)
+        out["cpu_baseline"] = cb
+        import oracle
+        a = acc.cpu().numpy()[sinks]
+        e = oracle.frac_error(a, ref)
+        out["error"] = {"median": float(np.median(e)), "p99": float(np.percentile(e, 99)),
+                        "max": float(e.max()), "sample": int(len(sinks)),
+                        "bar": {"median": 1e-6, "max": 1e-4}}
+    elif rank == 0:
+        out["cpu_baseline"] = None
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def measure_e2e(args, w, g_np, dev, P, flush):
+    """Same step through the public API with pinned host inputs and outputs."""
+    import torch
+    import paper_2110_11392_gb300 as nf
+    hp = torch.from_numpy(w.pos).pin_memory()
+    hg = torch.from_numpy(g_np).pin_memory()
+    ha = torch.empty_like(hp).pin_memory()
+    hgr = torch.empty_like(hp).pin_memory()
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        pos = hp.to(dev, non_blocking=True)
+        g = hg.to(dev, non_blocking=True)
+        acc = nf.forces(pos, w.box, w.K, w.R, w.eps)
+        grad = nf.forces_adjoint(pos, g, w.box, w.K, w.R, w.eps)
+        ha.copy_(acc, non_blocking=True)
+        hgr.copy_(grad, non_blocking=True)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    n = max(3, args.steps // 3)
+    tot = 0.0
+    for _ in range(n):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        b.synchronize()
+        tot += a.elapsed_time(b) / 1e3
+    return {"value": 2 * P * n / tot, "unit": UNIT, "h2d_bytes_per_step": 2 * w.pos.nbytes,
+            "d2h_bytes_per_step": 2 * w.pos.nbytes, "steps": n,
+            "note": "pinned host pos and g in, acc and grad out, per step"}
+
+
+def measure_batched(dev, flush):
+    """64 boxes (batched recipe): one captured graph of nf_forces_batched vs 64 nf_forces calls."""
+    import torch
+    import paper_2110_11392_gb300 as nf
+    from paper_2110_11392_gb300 import _lib
+    import workloads as W
+    w = W.config_batched()
+    run = nf.BatchedNearField(w.boxes, device=dev)
+    run.pos.copy_(torch.from_numpy(w.pos).to(dev))
+    run()
+    torch.cuda.synchronize()
+    P = run.stats()["pairs"]
+    run.capture()
+    stream = torch.cuda.current_stream(dev)
+    reps = 5
+
+    def timed(fn):
+        tot = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b) / 1e3
+        return tot / reps
+
+    t_graph = timed(lambda: run())
+    parts, off = [], 0
+    for bx in w.boxes:
+        parts.append((run.pos[off:off + bx["N"]], run.acc[off:off + bx["N"]], bx))
+        off += bx["N"]
+    ws = torch.empty(max(_lib.nf_workspace_bytes(bx["N"], bx["K"], bx["R"]) for bx in w.boxes),
+                     dtype=torch.uint8, device=dev)
+
+    def separate():
+        for p, a, bx in parts:
+            _lib.nf_forces(p, bx["box"], bx["K"], bx["R"], bx["eps"], a, None, ws)
+
+    separate()
+    t_sep = timed(separate)
+    return {"pairs_per_s": P / t_graph, "separate_pairs_per_s": P / t_sep, "speedup": t_sep / t_graph,
+            "boxes": len(w.boxes), "N_total": w.N, "pairs": P, "graph_ms": t_graph * 1e3,
+            "separate_ms": t_sep * 1e3}
+
+
+def kernel_traffic(which: str):
+    """DRAM bytes per launch from a committed ncu summary, if it matches the current source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))[which]
+    except (OSError, ValueError, KeyError):
+        return None
+    src = os.path.join(ROOT, "paper_2110_11392_gb300", "csrc", rec.get("source", ""))
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return rec.get("bytes_per_launch") if h == rec.get("sha256_16") else None
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle as it stands, on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    w, g_np = make_workload(args.workload, 0)
+    budget = max(2.0, 150.0 / (args.steps + args.warmup))
+    # one calibration sample fixes the per-step sample size
+    cb, sinks, _ = oracle_sample(w, g_np, budget)
+    g64 = g_np.astype(np.float64)
+    off, _, _ = oracle.bin_particles(w.pos, w.box, w.K)
+    S = stencil_sums(np.diff(off).reshape(w.K, w.K, w.K), w.R).reshape(-1)
+    cid = oracle.cell_of(w.pos, w.box, w.K)
+    n = len(sinks)
+    rng = np.random.default_rng(23)
+    times, pairs = [], []
+    for k in range(args.warmup + args.steps):
+        sk = np.sort(rng.choice(w.N, n, replace=False))
+        t0 = time.perf_counter()
+        oracle.forces(w.pos, w.box, w.K, w.R, w.eps, sinks=sk)
+        oracle.adjoint(w.pos, g64, w.box, w.K, w.R, w.eps, sinks=sk)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+            pairs.append(2 * int(S[cid[sk]].sum()))
+    value = sum(pairs) / sum(times)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": describe(w), "step": f"oracle forces + adjoint on {n} random sinks"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"{n} random sinks of {w.N} per step, forces + adjoint, FP64"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_native(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

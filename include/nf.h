@@ -1,0 +1,250 @@
+/*
+ * nf.h - C ABI of the GB300 near-field force library (libnf).
+ *
+ * The library computes the near-field part of the Abacus force split
+ * (Garrison et al., "The Abacus Cosmological N-body Code"): particles are
+ * binned into a periodic K^3 grid of cells, and every particle receives the
+ * spline-softened 1/r^2 acceleration of every particle in the (2R+1)^3 cells
+ * around its own cell, with the source image taken in the unwrapped neighbour
+ * cell (Sec. "Force Solver": exact near/far split; Sec. "GPU Near-Field
+ * Computation": 5^3 neighbour cells for R = 2).
+ *
+ * Conventions shared by every entry point
+ *   - Every pointer named pos, g, acc, grad, rel, perm, cell_offsets or ws is
+ *     CUDA device memory owned by the caller.  Host-side arrays are marked
+ *     "host".  The library allocates no memory.
+ *   - `stream` is a cudaStream_t passed as void*.  Every call only enqueues
+ *     work on that stream and returns; none of them synchronises, except
+ *     nf_status_read.
+ *   - Positions are FP32 [N][3] in box units.  Coordinates outside [0, box)
+ *     are taken periodically.  Masses are all 1/N and G = 1 (the paper's
+ *     particle state has no mass field, Sec. "Memory Model").
+ *   - `eps` is the Plummer-equivalent softening in box units.  Internally the
+ *     spline softening length is eps_s = 2.16 eps (Sec. "Force Softening").
+ *     The pair force is Eq. (spline):
+ *         F(d) = [10 - 15u + 6u^2] d / eps_s^3  for u = |d|/eps_s < 1,
+ *         F(d) = d / |d|^3                      otherwise,
+ *     with d = x_j - x_i, so the acceleration of i points towards j.
+ *   - Arguments are checked on the host before anything is enqueued.  A
+ *     rejected call returns NF_ERR_ARG or NF_ERR_WORKSPACE and launches
+ *     nothing.  The checks are: N >= 1, N < 2^31; box > 0 and finite;
+ *     K >= 2R+1 (else the stencil would count a cell twice) and K^3 < 2^31;
+ *     1 <= R <= NF_MAX_R; eps > 0 with 1e-5 w <= eps_s <= R w, w = box/K
+ *     (the softening must return to 1/r^2 inside the near field,
+ *     Sec. "Force Softening"); non-null pointers; ws_bytes large enough.
+ *   - Problems found on the device (non-finite coordinates) are recorded in a
+ *     status word inside the workspace; nf_status_read returns it.  A
+ *     non-finite particle is placed at the centre of cell 0 so the call
+ *     still completes; its outputs and those of its neighbours are then
+ *     meaningless.
+ *   - Every call is asynchronous and can be captured in a CUDA graph.  Calls
+ *     that share a workspace must not run concurrently.
+ *   - Return value: an nf_status.  nf_last_error() describes the last
+ *     non-OK return of the calling thread.
+ */
+#ifndef NF_H
+#define NF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NF_MAX_R 4
+
+typedef enum {
+    NF_OK = 0,
+    NF_ERR_ARG = 1,        /* invalid argument (checked on the host, nothing launched) */
+    NF_ERR_CUDA = 2,       /* a CUDA runtime call failed */
+    NF_ERR_WORKSPACE = 3,  /* ws is NULL or ws_bytes is below the required size */
+    NF_ERR_NONFINITE = 4,  /* device status: a coordinate was NaN or infinite */
+    NF_ERR_TIMEOUT = 5     /* device status: a bounded device-side wait gave up */
+} nf_status;
+
+/* Message for the last non-OK return on the calling thread ("" if none). */
+const char *nf_last_error(void);
+
+/* Library version string. */
+const char *nf_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Sizes                                                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Bytes of device workspace that nf_bin, nf_forces and nf_forces_adjoint need
+ * for one box of N particles on a K^3 grid with radius R.  Returns 0 for
+ * arguments nf_forces would reject.  The workspace's first 256 bytes hold the
+ * device status word read by nf_status_read. */
+size_t nf_workspace_bytes(int64_t N, int K, int R);
+
+/* ------------------------------------------------------------------------ */
+/* Binning (Sec. "Force Accuracy" overview: FP32 offsets from cell centres;  */
+/* Sec. "Two-Stage Execution": the K^3 cell grid)                            */
+/* ------------------------------------------------------------------------ */
+
+/* Stable counting sort of N particles into K^3 cells.
+ *   pos           [N][3] FP32, box units (input).
+ *   cell_offsets  [K^3 + 1] int32 (output): first sorted slot of cell
+ *                 c = (cx*K + cy)*K + cz; cell_offsets[K^3] = N.
+ *   rel           [N][4] FP32 (output), sorted by cell, input order inside a
+ *                 cell: (t_x - c_x - 1/2, t_y - c_y - 1/2, t_z - c_z - 1/2,
+ *                 bits of the int32 original index), where t = x K / box is
+ *                 formed in FP64 and c = floor(t); each offset is rounded once
+ *                 from FP64 to FP32, so it lies in [-1/2, 1/2] cell widths.
+ *                 Must be 16-byte aligned.
+ *   perm          [N] int32 (output): sorted slot -> original index.
+ * The result is bit-exact: it equals the plain CPU definition above. */
+int nf_bin(const float *pos, int64_t N, double box, int K,
+           int32_t *cell_offsets, float *rel, int32_t *perm,
+           void *ws, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Forces (Sec. "GPU Near-Field Computation"; Eq. (spline))                  */
+/* ------------------------------------------------------------------------ */
+
+/* Near-field accelerations of one periodic box.
+ *   pos  [N][3] FP32 box units (input).
+ *   acc  [N][3] FP32 (output), original particle order:
+ *        a_i = (1/N) sum_{j in N(i)} F(x_j - x_i), the sum running over the
+ *        (2R+1)^3 cells around i's cell (j = i included; it adds 0).
+ *   net  [3] FP64 (output) or NULL: sum_i (1/N) a_i of the FP32 results,
+ *        accumulated in FP64 (zero up to roundoff by Newton's third law).
+ * The pair arithmetic runs in FP32 on cell-relative coordinates; the partial
+ * sums of the 2R+1 pencils that reach each particle are added in FP64. */
+int nf_forces(const float *pos, int64_t N, double box, int K, int R, double eps,
+              float *acc, double *net, void *ws, size_t ws_bytes, void *stream);
+
+/* Adjoint of nf_forces: for a loss L with g = dL/da,
+ *   g     [N][3] FP32 (input), original order;
+ *   grad  [N][3] FP32 (output), original order:
+ *         dL/dx_i = (1/N) sum_{j in N(i)} J(x_j - x_i) (g_j - g_i),
+ *         J(d) = f(|d|) I + (f'(|d|)/|d|) d d^T the Jacobian of F (F = f d),
+ *         J(0) = f(0) I.
+ * The cell assignment is the one nf_forces uses for the same positions (the
+ * gradient of the piecewise-smooth map with cells held fixed).  It is not
+ * in the paper; it is the exact derivative of the sum nf_forces computes.
+ * Nothing is stored between the two calls: binning is recomputed. */
+int nf_forces_adjoint(const float *pos, const float *g, int64_t N, double box,
+                      int K, int R, double eps, float *grad,
+                      void *ws, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batched boxes and tuning                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* One box of a batch.  Boxes are packed back to back: box b's particles are
+ * rows [pos_offset, pos_offset + N) of pos_cat/acc_cat, and pos_offset must
+ * equal the sum of N over the boxes before b. */
+typedef struct {
+    int64_t N;
+    int64_t pos_offset;
+    double box;
+    double eps;
+    int K;
+    int R;
+} nf_box;
+
+/* Shape of the force kernel's work (picked by the autotuner or by hand).
+ *   sinks_per_lane  sinks each lane keeps in registers: 1, 2 or 4
+ *                   (a sink chunk is 32 * sinks_per_lane particles);
+ *   stage           sources staged in shared memory per step: 64 or 128;
+ *   warps_per_block 4 or 8;
+ *   blocks_per_sm   resident blocks of the persistent kernel per SM, 0 = as
+ *                   many as fit.
+ * Unsupported combinations are rejected with NF_ERR_ARG. */
+typedef struct {
+    int sinks_per_lane;
+    int stage;
+    int warps_per_block;
+    int blocks_per_sm;
+} nf_tuning;
+
+/* The tuning nf_forces and nf_forces_adjoint use when no tuning is given.
+ * nf_set_default_tuning copies *t (validated; NULL restores the built-in
+ * default); both are process-wide and not thread-safe against running calls. */
+int nf_set_default_tuning(const nf_tuning *t);
+void nf_get_default_tuning(nf_tuning *t);
+
+/* Workspace for a batch (host array boxes[nboxes]); 0 if the batch is invalid. */
+size_t nf_workspace_bytes_batched(const nf_box *boxes, int nboxes);
+
+/* Near-field accelerations of nboxes independent periodic boxes in one pass:
+ * one binning over all boxes, one work list, one persistent force launch and
+ * one combine.  Each box uses its own N (mass 1/N), box, K, R and eps.
+ *   boxes    host array [nboxes];
+ *   pos_cat  [sum N][3] FP32 (input), acc_cat [sum N][3] FP32 (output);
+ *   net      [nboxes][3] FP64 (output) or NULL: per-box sum of m a;
+ *   tune     NULL = default tuning.
+ * Equivalent to nf_forces on each box (same arithmetic, bit-identical
+ * results for the same tuning). */
+int nf_forces_batched(const nf_box *boxes, int nboxes, const float *pos_cat,
+                      float *acc_cat, double *net, const nf_tuning *tune,
+                      void *ws, size_t ws_bytes, void *stream);
+
+/* Adjoint of nf_forces_batched (same packing; g_cat and grad_cat [sum N][3]). */
+int nf_forces_adjoint_batched(const nf_box *boxes, int nboxes, const float *pos_cat,
+                              const float *g_cat, float *grad_cat,
+                              const nf_tuning *tune, void *ws, size_t ws_bytes,
+                              void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Status and statistics                                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Synchronises `stream`, then returns the device status word of the last call
+ * that used `ws` (NF_OK, NF_ERR_NONFINITE or NF_ERR_TIMEOUT), or NF_ERR_CUDA
+ * if synchronisation failed.  Every call clears the word when it starts. */
+int nf_status_read(void *ws, void *stream);
+
+/* Statistics of the last call that used `ws`, copied to the host after a
+ * stream synchronisation (host array out[4]):
+ *   out[0] = pair interactions computed, P = sum_c n_c S_c (self pairs
+ *            included), summed over boxes;
+ *   out[1] = work items (sink chunks) in the persistent queue;
+ *   out[2] = largest cell occupancy;
+ *   out[3] = sink lanes issued (32 * sinks_per_lane rounded up per chunk),
+ *            so out[0] / (out[3] * sources) measures lane utilisation. */
+int nf_stats_read(void *ws, int64_t *out, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Measurement                                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Device time of the stages of a recent nf_forces / nf_forces_adjoint /
+ * batched call, from CUDA events recorded on the caller's stream around each
+ * stage while profiling is on (milliseconds):
+ *   bin_ms       cell ids, offsets, radix sort, cell-centred offsets;
+ *   worklist_ms  pencil sizes, cost order, work items (and the gather of g);
+ *   pair_ms      the persistent force or adjoint kernel alone;
+ *   combine_ms   FP64 combine of the partial sums and scatter (and net force);
+ *   total_ms     first event to last. */
+typedef struct {
+    double bin_ms;
+    double worklist_ms;
+    double pair_ms;
+    double combine_ms;
+    double total_ms;
+} nf_profile;
+
+#define NF_PROFILE_RING 8
+
+/* Turns per-stage event recording on (1) or off (0), process-wide, and
+ * forgets earlier records.  While it is on, calls must not be captured into a
+ * CUDA graph.  Not thread-safe against concurrent calls. */
+int nf_profile_enable(int on);
+
+/* Synchronises on the events of a profiled call and fills *out (host).
+ * back = 0 is the most recent profiled call, 1 the one before, and so on up
+ * to NF_PROFILE_RING - 1.  Returns NF_ERR_ARG if there is no such call. */
+int nf_profile_read(int back, nf_profile *out);
+
+/* Number of kernels libnf has launched in this process (all entry points). */
+int64_t nf_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NF_H */

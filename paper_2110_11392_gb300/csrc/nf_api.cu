@@ -1,0 +1,500 @@
+// C-ABI entry points of libnf: argument checks, workspace layout, launch order.
+//
+// Every entry point is a thin host function: it validates its arguments
+// (nothing is enqueued when they are rejected), carves the caller's workspace
+// into regions, and enqueues the kernels of nf_bin.cu and nf_force.cu on the
+// caller's stream.  No entry point allocates memory or synchronises, except
+// nf_status_read and nf_stats_read which read results back.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <map>
+#include <mutex>
+#include <utility>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "nf_internal.cuh"
+
+namespace nf {
+
+namespace {
+std::atomic<long long> g_launches{0};
+std::mutex g_smem_mutex;
+std::map<std::pair<int, const void*>, int> g_smem_set;
+}  // namespace
+
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+cudaError_t ensure_smem(const void* fn, int bytes)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_smem_mutex);
+    auto key = std::make_pair(dev, fn);
+    auto it = g_smem_set.find(key);
+    if (it != g_smem_set.end() && it->second >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) g_smem_set[key] = bytes;
+    return e;
+}
+
+namespace {
+
+thread_local std::string g_last_error;
+
+// Per-stage profiling events of the last NF_PROFILE_RING calls (process-wide;
+// off by default).  g_prof_count counts completed profiled calls.
+bool g_profile_on = false;
+long long g_prof_count = 0;
+cudaEvent_t g_ev[NF_PROFILE_RING][5] = {};
+
+cudaError_t prof_mark(int i, cudaStream_t s)
+{
+    if (!g_profile_on) return cudaSuccess;
+    cudaEvent_t& ev = g_ev[g_prof_count % NF_PROFILE_RING][i];
+    if (!ev) {
+        cudaError_t e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaEventRecord(ev, s);
+}
+ForceTuning g_default_tuning = {4, 128, 8, 0};
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where)
+{
+    return fail(NF_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+constexpr double kEpsRatio = 2.16;  // eps_s / eps_p, Sec. "Force Softening"
+
+struct Plan {
+    int nboxes = 0;
+    int64_t N = 0;       // total particles
+    int64_t C = 0;       // total cells
+    int64_t max_items = 0;
+    int max_R = 1;
+    int max_nseg = 9;
+    int nchunks = 0;     // combine chunks
+    RadixPlan rx{};
+    std::vector<BoxDev> boxes;
+    // region offsets (bytes from ws)
+    size_t o_boxes, o_keys_a, o_keys_b, o_vals_a, o_vals_b, o_off, o_hist, o_aux, o_rel, o_perm,
+        o_chunks, o_bucket_of, o_bucket_count, o_items, o_gs, o_partial, o_chunk_sums, total;
+};
+
+// Validates one box; fills the device constants.
+int make_box(const nf_box& in, bool need_force, BoxDev* out)
+{
+    if (in.N < 1 || in.N >= (int64_t(1) << 31)) return fail(NF_ERR_ARG, "N = %lld out of [1, 2^31)", (long long)in.N);
+    if (!(in.box > 0.0) || !std::isfinite(in.box)) return fail(NF_ERR_ARG, "box = %g must be finite and > 0", in.box);
+    if (in.K < 1) return fail(NF_ERR_ARG, "K = %d must be >= 1", in.K);
+    if ((int64_t)in.K * in.K * in.K >= (int64_t(1) << 31)) return fail(NF_ERR_ARG, "K^3 must be < 2^31 (K = %d)", in.K);
+    BoxDev b;
+    std::memset(&b, 0, sizeof b);
+    b.K = in.K;
+    b.R = in.R;
+    b.N = (int)in.N;
+    b.kl = (double)in.K / in.box;
+    const double w = in.box / in.K;
+    b.scale_acc = 1.0 / ((double)in.N * w * w);
+    b.scale_grad = 1.0 / ((double)in.N * w * w * w);
+    if (need_force) {
+        if (in.R < 1 || in.R > NF_MAX_R) return fail(NF_ERR_ARG, "R = %d out of [1, %d]", in.R, NF_MAX_R);
+        if (in.K < 2 * in.R + 1)
+            return fail(NF_ERR_ARG, "K = %d < 2R+1 = %d: the stencil would count a cell twice", in.K, 2 * in.R + 1);
+        if (!(in.eps > 0.0) || !std::isfinite(in.eps)) return fail(NF_ERR_ARG, "eps = %g must be finite and > 0", in.eps);
+        const double e = kEpsRatio * in.eps / w;  // eps_s in cell units
+        if (e > in.R)
+            return fail(NF_ERR_ARG, "eps_s = 2.16 eps = %g cells exceeds R = %d cells: the softening must end inside the near field", e, in.R);
+        if (e < 1e-5) return fail(NF_ERR_ARG, "eps_s = %g cells is below 1e-5 cells", e);
+        const double e2 = e * e, e3 = e2 * e, e4 = e3 * e, e5 = e4 * e;
+        b.c0 = (float)(10.0 / e3);
+        b.c1 = (float)(-15.0 / e4);
+        b.c2 = (float)(6.0 / e5);
+        b.e0 = (float)(-15.0 / e4);
+        b.e1 = (float)(12.0 / e5);
+        b.eps2 = (float)e2;
+    }
+    *out = b;
+    return NF_OK;
+}
+
+int make_plan(const nf_box* boxes, int nboxes, bool need_force, int chunk_lanes, Plan* p)
+{
+    if (!boxes || nboxes < 1) return fail(NF_ERR_ARG, "need at least one box");
+    p->nboxes = nboxes;
+    p->boxes.resize(nboxes);
+    int64_t N = 0, C = 0, items = 0, nchunks = 0;
+    int max_R = 1;
+    for (int b = 0; b < nboxes; ++b) {
+        int rc = make_box(boxes[b], need_force, &p->boxes[b]);
+        if (rc) {
+            if (nboxes > 1) g_last_error = "box " + std::to_string(b) + ": " + g_last_error;
+            return rc;
+        }
+        if (boxes[b].pos_offset != N)
+            return fail(NF_ERR_ARG, "box %d: pos_offset = %lld, boxes must be packed back to back (expected %lld)", b,
+                        (long long)boxes[b].pos_offset, (long long)N);
+        BoxDev& d = p->boxes[b];
+        d.part_base = (int)N;
+        d.cell_base = (int)C;
+        d.chunk_base = (int)nchunks;
+        const int64_t cells = (int64_t)d.K * d.K * d.K;
+        N += boxes[b].N;
+        C += cells;
+        nchunks += (boxes[b].N + kCombineChunk - 1) / kCombineChunk;
+        if (need_force) {
+            items += (2 * (int64_t)d.R + 1) * boxes[b].N / chunk_lanes + cells + 1;
+            if (d.R > max_R) max_R = d.R;
+        }
+        if (N >= (int64_t(1) << 31)) return fail(NF_ERR_ARG, "total N must be < 2^31");
+        if (C >= (int64_t(1) << 31) - 1) return fail(NF_ERR_ARG, "total cells must be < 2^31");
+    }
+    if (items >= (int64_t(1) << 31)) return fail(NF_ERR_ARG, "too many work items");
+    p->N = N;
+    p->C = C;
+    p->max_items = items;
+    p->max_R = max_R;
+    p->max_nseg = (2 * max_R + 1) * (2 * max_R + 1);
+    p->nchunks = (int)nchunks;
+    p->rx = radix_plan(N, C);
+
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    take(sizeof(WsHeader));
+    p->o_boxes = take(sizeof(BoxDev) * nboxes);
+    p->o_keys_a = take(4 * (size_t)N);
+    p->o_keys_b = take(4 * (size_t)N);
+    p->o_vals_a = take(4 * (size_t)N);
+    p->o_vals_b = take(4 * (size_t)N);
+    p->o_off = take(4 * (size_t)(C + 1));
+    p->o_hist = take(4 * radix_hist_words(p->rx));
+    size_t aux = scan_aux_words((size_t)C + 1);
+    size_t aux2 = scan_aux_words(radix_hist_words(p->rx));
+    p->o_aux = take(4 * (aux > aux2 ? aux : aux2));
+    p->o_rel = take(16 * (size_t)N);
+    p->o_perm = take(4 * (size_t)N);
+    if (need_force) {
+        p->o_chunks = take(4 * (size_t)C);
+        p->o_bucket_of = take((size_t)C);
+        p->o_bucket_count = take(4 * kBuckets);
+        p->o_items = take(16 * (size_t)items);
+        p->o_gs = take(16 * (size_t)N);
+        p->o_partial = take(4 * 3 * (size_t)(2 * max_R + 1) * (size_t)N);
+        p->o_chunk_sums = take(8 * 3 * (size_t)nchunks);
+    } else {
+        p->o_chunks = p->o_bucket_of = p->o_bucket_count = p->o_items = p->o_gs = p->o_partial =
+            p->o_chunk_sums = 0;
+    }
+    p->total = o;
+    return NF_OK;
+}
+
+template <typename T>
+T* at(void* ws, size_t off)
+{
+    return reinterpret_cast<T*>(static_cast<char*>(ws) + off);
+}
+
+int check_tuning(const nf_tuning* t, ForceTuning* out)
+{
+    if (!t) {
+        *out = g_default_tuning;
+        return NF_OK;
+    }
+    ForceTuning f = {t->sinks_per_lane, t->stage, t->warps_per_block, t->blocks_per_sm};
+    if (!force_tuning_supported(f))
+        return fail(NF_ERR_ARG, "unsupported tuning (sinks_per_lane %d, stage %d, warps %d, blocks %d)",
+                    t->sinks_per_lane, t->stage, t->warps_per_block, t->blocks_per_sm);
+    *out = f;
+    return NF_OK;
+}
+
+#define NF_CUDA(call, where)                                  \
+    do {                                                      \
+        cudaError_t e__ = (call);                             \
+        if (e__ != cudaSuccess) return cuda_fail(e__, where); \
+    } while (0)
+
+// Clears the header, uploads the box table, bins every particle.
+int run_binning(const Plan& p, const float* pos, void* ws, int32_t* cell_off, float4* rel, int32_t* perm,
+                cudaStream_t s)
+{
+    WsHeader* hdr = at<WsHeader>(ws, 0);
+    BoxDev* boxes = at<BoxDev>(ws, p.o_boxes);
+    NF_CUDA(cudaMemsetAsync(hdr, 0, sizeof(WsHeader), s), "clear header");
+    NF_CUDA(cudaMemsetAsync(cell_off, 0, 4 * (size_t)(p.C + 1), s), "clear counts");
+    for (int first = 0; first < p.nboxes; first += kMaxBoxesPerFill) {
+        BoxFill f;
+        std::memset(&f, 0, sizeof f);
+        f.first = first;
+        f.count = std::min(kMaxBoxesPerFill, p.nboxes - first);
+        for (int q = 0; q < f.count; ++q) f.b[q] = p.boxes[first + q];
+        NF_CUDA(launch_fill_boxes(f, boxes, s), "box table");
+    }
+    int* keys_a = at<int>(ws, p.o_keys_a);
+    NF_CUDA(launch_shift(pos, (int)p.N, boxes, p.nboxes, keys_a, cell_off, hdr, s), "cell ids");
+    NF_CUDA(launch_scan(reinterpret_cast<unsigned*>(cell_off), (size_t)p.C + 1, at<unsigned>(ws, p.o_aux), s),
+            "cell offsets");
+    NF_CUDA(radix_sort(p.rx, (int)p.N, keys_a, at<int>(ws, p.o_keys_b), at<int>(ws, p.o_vals_a),
+                       at<int>(ws, p.o_vals_b), perm, at<unsigned>(ws, p.o_hist), at<unsigned>(ws, p.o_aux), s),
+            "radix sort");
+    NF_CUDA(launch_rel(pos, (int)p.N, boxes, p.nboxes, perm, rel, s), "offsets");
+    return NF_OK;
+}
+
+int run_forces(const Plan& p, bool adjoint, const ForceTuning& t, const float* pos, const float* g, float* out,
+               double* net, void* ws, cudaStream_t s)
+{
+    WsHeader* hdr = at<WsHeader>(ws, 0);
+    BoxDev* boxes = at<BoxDev>(ws, p.o_boxes);
+    int32_t* off = at<int32_t>(ws, p.o_off);
+    float4* rel = at<float4>(ws, p.o_rel);
+    int32_t* perm = at<int32_t>(ws, p.o_perm);
+    NF_CUDA(prof_mark(0, s), "profile");
+    int rc = run_binning(p, pos, ws, off, rel, perm, s);
+    if (rc) return rc;
+    NF_CUDA(prof_mark(1, s), "profile");
+    unsigned* bucket_count = at<unsigned>(ws, p.o_bucket_count);
+    NF_CUDA(cudaMemsetAsync(bucket_count, 0, 4 * kBuckets, s), "clear buckets");
+    const int CH = 32 * t.sinks_per_lane;
+    NF_CUDA(launch_pencils(boxes, p.nboxes, (int)p.C, off, CH, at<int>(ws, p.o_chunks), bucket_count,
+                           at<unsigned char>(ws, p.o_bucket_of), hdr, s),
+            "pencils");
+    NF_CUDA(launch_items(boxes, p.nboxes, (int)p.C, at<int>(ws, p.o_chunks), at<unsigned char>(ws, p.o_bucket_of),
+                         bucket_count, at<int4>(ws, p.o_items), hdr, s),
+            "work items");
+    float4* gs = at<float4>(ws, p.o_gs);
+    if (adjoint) NF_CUDA(launch_gather_g(g, perm, (int)p.N, gs, s), "gather g");
+    float* partial = at<float>(ws, p.o_partial);
+    NF_CUDA(prof_mark(2, s), "profile");
+    NF_CUDA(launch_force(adjoint, t, boxes, off, rel, gs, at<int4>(ws, p.o_items), hdr, partial, (int)p.N,
+                         p.max_nseg, s),
+            adjoint ? "adjoint kernel" : "force kernel");
+    NF_CUDA(prof_mark(3, s), "profile");
+    double* chunk_sums = net ? at<double>(ws, p.o_chunk_sums) : nullptr;
+    NF_CUDA(launch_combine(adjoint, boxes, p.nboxes, p.nchunks, partial, perm, (int)p.N, out, chunk_sums, s),
+            "combine");
+    if (net) NF_CUDA(launch_net(boxes, p.nboxes, chunk_sums, net, s), "net force");
+    NF_CUDA(prof_mark(4, s), "profile");
+    if (g_profile_on) ++g_prof_count;
+    return NF_OK;
+}
+
+int check_ws(const Plan& p, void* ws, size_t ws_bytes)
+{
+    if (!ws) return fail(NF_ERR_WORKSPACE, "workspace is NULL");
+    if ((reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)) != 0)
+        return fail(NF_ERR_WORKSPACE, "workspace must be %zu-byte aligned", kAlign);
+    if (ws_bytes < p.total)
+        return fail(NF_ERR_WORKSPACE, "workspace too small: %zu bytes given, %zu needed", ws_bytes, p.total);
+    return NF_OK;
+}
+
+nf_box one_box(int64_t N, double box, int K, int R, double eps)
+{
+    nf_box b;
+    b.N = N;
+    b.pos_offset = 0;
+    b.box = box;
+    b.eps = eps;
+    b.K = K;
+    b.R = R;
+    return b;
+}
+
+int forces_entry(const nf_box* boxes, int nboxes, bool adjoint, const float* pos, const float* g, float* out,
+                 double* net, const nf_tuning* tune, void* ws, size_t ws_bytes, void* stream)
+{
+    g_last_error.clear();
+    ForceTuning t;
+    int rc = check_tuning(tune, &t);
+    if (rc) return rc;
+    Plan p;
+    rc = make_plan(boxes, nboxes, true, 32 * t.sinks_per_lane, &p);
+    if (rc) return rc;
+    if (!pos || !out || (adjoint && !g)) return fail(NF_ERR_ARG, "null pointer argument");
+    rc = check_ws(p, ws, ws_bytes);
+    if (rc) return rc;
+    return run_forces(p, adjoint, t, pos, g, out, net, ws, static_cast<cudaStream_t>(stream));
+}
+
+}  // namespace
+}  // namespace nf
+
+using namespace nf;
+
+extern "C" {
+
+const char* nf_last_error(void) { return g_last_error.c_str(); }
+
+const char* nf_version(void) { return "nf 0.1 (sm_103a)"; }
+
+size_t nf_workspace_bytes(int64_t N, int K, int R)
+{
+    // the size does not depend on box or eps: use box 1 and a valid softening
+    nf_box b = one_box(N, 1.0, K, R, K > 0 ? 0.5 / (kEpsRatio * K) : 1.0);
+    Plan p;
+    if (make_plan(&b, 1, true, 32, &p)) return 0;
+    return p.total;
+}
+
+size_t nf_workspace_bytes_batched(const nf_box* boxes, int nboxes)
+{
+    Plan p;
+    if (make_plan(boxes, nboxes, true, 32, &p)) return 0;
+    return p.total;
+}
+
+int nf_bin(const float* pos, int64_t N, double box, int K, int32_t* cell_offsets, float* rel, int32_t* perm,
+           void* ws, size_t ws_bytes, void* stream)
+{
+    g_last_error.clear();
+    nf_box b = one_box(N, box, K, 0, 0.0);
+    Plan p;
+    int rc = make_plan(&b, 1, false, 32, &p);
+    if (rc) return rc;
+    if (!pos || !cell_offsets || !rel || !perm) return fail(NF_ERR_ARG, "null pointer argument");
+    if ((reinterpret_cast<uintptr_t>(rel) & 15) != 0) return fail(NF_ERR_ARG, "rel must be 16-byte aligned");
+    // nf_bin needs only the binning regions, which precede the force regions
+    rc = check_ws(p, ws, ws_bytes);
+    if (rc) return rc;
+    return run_binning(p, pos, ws, cell_offsets, reinterpret_cast<float4*>(rel), perm,
+                       static_cast<cudaStream_t>(stream));
+}
+
+int nf_forces(const float* pos, int64_t N, double box, int K, int R, double eps, float* acc, double* net, void* ws,
+              size_t ws_bytes, void* stream)
+{
+    nf_box b = one_box(N, box, K, R, eps);
+    return forces_entry(&b, 1, false, pos, nullptr, acc, net, nullptr, ws, ws_bytes, stream);
+}
+
+int nf_forces_adjoint(const float* pos, const float* g, int64_t N, double box, int K, int R, double eps, float* grad,
+                      void* ws, size_t ws_bytes, void* stream)
+{
+    nf_box b = one_box(N, box, K, R, eps);
+    return forces_entry(&b, 1, true, pos, g, grad, nullptr, nullptr, ws, ws_bytes, stream);
+}
+
+int nf_forces_batched(const nf_box* boxes, int nboxes, const float* pos_cat, float* acc_cat, double* net,
+                      const nf_tuning* tune, void* ws, size_t ws_bytes, void* stream)
+{
+    return forces_entry(boxes, nboxes, false, pos_cat, nullptr, acc_cat, net, tune, ws, ws_bytes, stream);
+}
+
+int nf_forces_adjoint_batched(const nf_box* boxes, int nboxes, const float* pos_cat, const float* g_cat,
+                              float* grad_cat, const nf_tuning* tune, void* ws, size_t ws_bytes, void* stream)
+{
+    return forces_entry(boxes, nboxes, true, pos_cat, g_cat, grad_cat, nullptr, tune, ws, ws_bytes, stream);
+}
+
+int nf_set_default_tuning(const nf_tuning* t)
+{
+    g_last_error.clear();
+    if (!t) {
+        g_default_tuning = ForceTuning{4, 128, 8, 0};
+        return NF_OK;
+    }
+    ForceTuning f;
+    int rc = check_tuning(t, &f);
+    if (rc) return rc;
+    g_default_tuning = f;
+    return NF_OK;
+}
+
+void nf_get_default_tuning(nf_tuning* t)
+{
+    if (!t) return;
+    t->sinks_per_lane = g_default_tuning.sinks_per_lane;
+    t->stage = g_default_tuning.stage;
+    t->warps_per_block = g_default_tuning.warps_per_block;
+    t->blocks_per_sm = g_default_tuning.blocks_per_sm;
+}
+
+int nf_status_read(void* ws, void* stream)
+{
+    g_last_error.clear();
+    if (!ws) return fail(NF_ERR_WORKSPACE, "workspace is NULL");
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "status sync");
+    int bits = 0;
+    e = cudaMemcpy(&bits, ws, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (bits & (1 << NF_ERR_NONFINITE)) return fail(NF_ERR_NONFINITE, "non-finite coordinates in the input");
+    if (bits & (1 << NF_ERR_TIMEOUT)) return fail(NF_ERR_TIMEOUT, "a device-side wait timed out");
+    return NF_OK;
+}
+
+int nf_profile_enable(int on)
+{
+    g_profile_on = on != 0;
+    g_prof_count = 0;
+    return NF_OK;
+}
+
+int nf_profile_read(int back, nf_profile* out)
+{
+    g_last_error.clear();
+    if (!out) return fail(NF_ERR_ARG, "null pointer argument");
+    if (back < 0 || back >= NF_PROFILE_RING || back >= g_prof_count)
+        return fail(NF_ERR_ARG, "no profiled call %d back (%lld recorded)", back, g_prof_count);
+    cudaEvent_t* ev = g_ev[(g_prof_count - 1 - back) % NF_PROFILE_RING];
+    cudaError_t e = cudaEventSynchronize(ev[4]);
+    if (e != cudaSuccess) return cuda_fail(e, "profile sync");
+    float ms[4];
+    for (int i = 0; i < 4; ++i) {
+        e = cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "profile elapsed");
+    }
+    out->bin_ms = ms[0];
+    out->worklist_ms = ms[1];
+    out->pair_ms = ms[2];
+    out->combine_ms = ms[3];
+    out->total_ms = (double)ms[0] + ms[1] + ms[2] + ms[3];
+    return NF_OK;
+}
+
+int64_t nf_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+int nf_stats_read(void* ws, int64_t* out, void* stream)
+{
+    g_last_error.clear();
+    if (!ws || !out) return fail(NF_ERR_ARG, "null pointer argument");
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "stats sync");
+    WsHeader h;
+    e = cudaMemcpy(&h, ws, sizeof h, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "stats read");
+    out[0] = (int64_t)h.pairs;
+    out[1] = h.n_items;
+    out[2] = h.max_occ;
+    out[3] = (int64_t)h.lane_pairs;
+    return NF_OK;
+}
+
+}  // extern "C"

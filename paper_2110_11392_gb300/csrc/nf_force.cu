@@ -1,0 +1,840 @@
+// Near-field force and adjoint on the sorted cell grid.
+//
+// Work decomposition (pencil on plane).  The paper groups sinks into pencils
+// of 2R+1 cells and sources into 2R+1 pencils so that every sink-source cell
+// pair is met exactly once and each sink cell collects 2R+1 partial
+// accelerations (Sec. "Pencil-on-Pencil").  Here the cell order is z-fastest,
+// so the roles are turned to keep every source run contiguous in memory:
+//   work item centre (i, j, k):
+//     sinks   = cells (i+c, j, k),   c in [-R, R]   (an x-pencil, 2R+1 cells)
+//     sources = cells (i, j+b, k+d), b, d in [-R, R] (2R+1 z-runs of 2R+1 cells)
+// A sink in cell (x, j, k) meets source cell (x+a, j+b, k+d) in the item
+// centred at x+a, with partial slot c = -a + R.  Every (sink, source-cell)
+// pair of the (2R+1)^3 stencil is therefore computed exactly once, and each
+// sink gets 2R+1 partial sums, one per slot, which k_combine adds in FP64.
+// Coordinates are cell-relative FP32 offsets shifted into the frame of the
+// item's centre cell (the paper's pencil-centred coordinates, Sec.
+// "Pencil-on-Pencil"), so the periodic wrap costs nothing in the pair loop.
+//
+// Scheduling.  A pencil's sinks are cut into chunks of 32 * SMAX; one chunk
+// is one work item for one warp.  k_pencils/k_items build the item list in
+// descending cost order (cost buckets of half powers of two: longest first,
+// as the paper's NUMA scheduler hands out work from a shared counter, Sec.
+// "Memory and Threads"), and the persistent kernel's warps pull items from an
+// atomic counter until the list is exhausted.
+//
+// Pair loop (one warp, one item).  Each lane keeps S <= SMAX sinks in
+// registers (S = ceil(chunk size / 32) is picked per item).  Sources are
+// staged B at a time into the warp's shared-memory buffers (double-buffered:
+// the next stage's global loads are issued before the current stage is
+// computed), shifted into the item's frame as they are staged.  Every lane
+// then reads each source with a broadcast shared load and accumulates S pairs
+// in FP32 with MUFU rsqrt.  Sums are kept per stage and added into the
+// running total after each stage (per-stage partial sums bound the FP32
+// accumulation error).
+//
+// Spline hand-off.  Eq. (spline) switches to 1/r^3 at r = eps_s.  The paper's
+// kernel takes min(poly, r^-3) instead of a branch (Sec. "Force Kernel");
+// that identity holds because u^3 poly(u) - 1 = -(1-u)^3 (6u^2+3u+1).  Here
+// the min form is the exact path ("slow").  A stage whose sources are all
+// farther than eps_s from every sink gives the same value with f = r^-3
+// alone, so the "fast" path computes only that and tracks the smallest r^2
+// it met; if any lane saw r < eps_s, the warp recomputes the stage with the
+// exact path.  Stages with the item's own centre cell (self pairs) always
+// take the exact path: the source list puts that cell first, in stages of
+// its own.
+#include <cuda_runtime.h>
+
+#include "nf_internal.cuh"
+
+namespace nf {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr float kTiny = 1e-25f;     // r^2 floor: coincident pairs stay finite (r^-3 < FLT_MAX)
+constexpr float kFarSrc = 1e18f;    // padding source coordinate: adds exactly 0
+constexpr float kFarSink = -1e18f;  // padding sink coordinate
+constexpr float kBig = 3.0e38f;
+
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ int wrap(int a, int K)
+{
+    a %= K;
+    return a < 0 ? a + K : a;
+}
+
+__device__ __forceinline__ int find_box_by_cell(const BoxDev* boxes, int nboxes, int g)
+{
+    int lo = 0, hi = nboxes - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (boxes[mid].cell_base <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int find_box_by_part(const BoxDev* boxes, int nboxes, int e)
+{
+    int lo = 0, hi = nboxes - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (boxes[mid].part_base <= e) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int cell_count(const int* off, int cid, int* start)
+{
+    int s = off[cid];
+    *start = s;
+    return off[cid + 1] - s;
+}
+
+__device__ __forceinline__ int cost_bucket(unsigned long long cost)
+{
+    if (cost == 0) return kBuckets - 1;
+    int h = (int)floorf(2.0f * log2f((float)cost));
+    int b = (kBuckets - 2) - h;
+    return b < 0 ? 0 : (b > kBuckets - 2 ? kBuckets - 2 : b);
+}
+
+// ---------------------------------------------------------------------------
+// Work list
+// ---------------------------------------------------------------------------
+
+__global__ void k_pencils(const BoxDev* __restrict__ boxes, int nboxes, int Ctot,
+                          const int* __restrict__ off, int CH, int* __restrict__ chunks,
+                          unsigned* __restrict__ bucket_count, unsigned char* __restrict__ bucket_of,
+                          WsHeader* hdr)
+{
+    unsigned long long pairs = 0, lane_pairs = 0;
+    int max_occ = 0;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < Ctot; g += gridDim.x * blockDim.x) {
+        const BoxDev& B = boxes[find_box_by_cell(boxes, nboxes, g)];
+        const int K = B.K, R = B.R, cb = B.cell_base;
+        const int l = g - cb;
+        const int i = l / (K * K), j = (l / K) % K, k = l % K;
+        int st;
+        int n_sink = 0;
+        for (int c = -R; c <= R; ++c) n_sink += cell_count(off, cb + (wrap(i + c, K) * K + j) * K + k, &st);
+        int n_src = 0;
+        for (int b = -R; b <= R; ++b)
+            for (int d = -R; d <= R; ++d)
+                n_src += cell_count(off, cb + (i * K + wrap(j + b, K)) * K + wrap(k + d, K), &st);
+        int occ = cell_count(off, g, &st);
+        max_occ = max(max_occ, occ);
+        int nch = (n_sink + CH - 1) / CH;
+        chunks[g] = nch;
+        unsigned long long cost = (unsigned long long)n_src * (unsigned long long)min(n_sink, CH);
+        int bk = cost_bucket(cost);
+        bucket_of[g] = (unsigned char)bk;
+        if (nch) atomicAdd(&bucket_count[bk], (unsigned)nch);
+        pairs += (unsigned long long)n_sink * (unsigned long long)n_src;
+        if (nch) {
+            int rem = n_sink - (nch - 1) * CH;
+            unsigned long long lanes = (unsigned long long)(nch - 1) * CH + 32ull * ((rem + 31) / 32);
+            lane_pairs += lanes * (unsigned long long)n_src;
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        pairs += __shfl_xor_sync(kFull, pairs, o);
+        lane_pairs += __shfl_xor_sync(kFull, lane_pairs, o);
+        max_occ = max(max_occ, __shfl_xor_sync(kFull, max_occ, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&hdr->pairs, pairs);
+        atomicAdd(&hdr->lane_pairs, lane_pairs);
+        atomicMax(&hdr->max_occ, max_occ);
+    }
+}
+
+// Exclusive scan of the bucket counts (one warp pair of lanes per bucket);
+// writes the total to the header.
+__global__ void k_bucket_scan(unsigned* bucket_count, WsHeader* hdr)
+{
+    __shared__ unsigned v[kBuckets];
+    int t = threadIdx.x;
+    v[t] = bucket_count[t];
+    __syncthreads();
+    if (t == 0) {
+        unsigned run = 0;
+        for (int b = 0; b < kBuckets; ++b) {
+            unsigned c = v[b];
+            v[b] = run;
+            run += c;
+        }
+        hdr->n_items = (int)run;
+    }
+    __syncthreads();
+    bucket_count[t] = v[t];
+}
+
+__global__ void k_items(const BoxDev* __restrict__ boxes, int nboxes, int Ctot,
+                        const int* __restrict__ chunks, const unsigned char* __restrict__ bucket_of,
+                        unsigned* __restrict__ cursor, int4* __restrict__ items)
+{
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < Ctot; g += gridDim.x * blockDim.x) {
+        int nch = chunks[g];
+        if (!nch) continue;
+        int b = find_box_by_cell(boxes, nboxes, g);
+        unsigned base = atomicAdd(&cursor[bucket_of[g]], (unsigned)nch);
+        for (int q = 0; q < nch; ++q) items[base + q] = make_int4(g, q, b, 0);
+    }
+}
+
+__global__ void k_gather_g(const float* __restrict__ g, const int* __restrict__ perm, int Ntot,
+                           float4* __restrict__ gs)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < Ntot; s += gridDim.x * blockDim.x) {
+        int e = perm[s];
+        gs[s] = make_float4(g[3 * (size_t)e + 0], g[3 * (size_t)e + 1], g[3 * (size_t)e + 2], 0.0f);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pair arithmetic
+// ---------------------------------------------------------------------------
+
+struct Coef {
+    float c0, c1, c2;  // Eq. (spline) polynomial in cell units: c0 + r^2 (c2 + c1/r)
+    float e0, e1;      // f'(r)/r inside the softening: e1 + e0/r
+    float eps2;
+};
+
+template <int S>
+struct SinkSet {
+    float x[S], y[S], z[S];
+    float gx[S], gy[S], gz[S];
+    float ax[S], ay[S], az[S];  // running totals
+    float sx[S], sy[S], sz[S];  // current stage
+};
+
+// Forward, fast path: f = r^-3 for every pair, tracks the smallest r^2.
+template <int S>
+__device__ __forceinline__ void stage_fwd_fast(const float4* __restrict__ A, int cnt,
+                                               SinkSet<S>& k, float& trk)
+{
+#pragma unroll 1
+    for (int q = 0; q < cnt; q += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float4 sj = A[q + u];
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                float dx = sj.x - k.x[s], dy = sj.y - k.y[s], dz = sj.z - k.z[s];
+                float r2 = fmaf(dx, dx, kTiny);
+                r2 = fmaf(dy, dy, r2);
+                r2 = fmaf(dz, dz, r2);
+                trk = fminf(trk, r2);
+                float ri = rsqrt_approx(r2);
+                float ri2 = ri * ri;
+                float f = ri2 * ri;
+                k.sx[s] = fmaf(dx, f, k.sx[s]);
+                k.sy[s] = fmaf(dy, f, k.sy[s]);
+                k.sz[s] = fmaf(dz, f, k.sz[s]);
+            }
+        }
+    }
+}
+
+// Forward, exact path: f = min(poly(r), r^-3) (Eq. (spline) with the min hand-off).
+template <int S>
+__device__ __forceinline__ void stage_fwd_exact(const float4* __restrict__ A, int cnt,
+                                                SinkSet<S>& k, const Coef& cf)
+{
+#pragma unroll 1
+    for (int q = 0; q < cnt; q += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float4 sj = A[q + u];
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                float dx = sj.x - k.x[s], dy = sj.y - k.y[s], dz = sj.z - k.z[s];
+                float r2 = fmaf(dx, dx, kTiny);
+                r2 = fmaf(dy, dy, r2);
+                r2 = fmaf(dz, dz, r2);
+                float ri = rsqrt_approx(r2);
+                float p = fmaf(r2, fmaf(cf.c1, ri, cf.c2), cf.c0);
+                float ri2 = ri * ri;
+                float f = fminf(p, ri2 * ri);
+                k.sx[s] = fmaf(dx, f, k.sx[s]);
+                k.sy[s] = fmaf(dy, f, k.sy[s]);
+                k.sz[s] = fmaf(dz, f, k.sz[s]);
+            }
+        }
+    }
+}
+
+// Adjoint, fast path: J v = r^-3 (v - 3 r^-2 (d.v) d), v = g_j - g_i.
+template <int S>
+__device__ __forceinline__ void stage_adj_fast(const float4* __restrict__ A, const float4* __restrict__ Gv,
+                                               int cnt, SinkSet<S>& k, float& trk)
+{
+#pragma unroll 1
+    for (int q = 0; q < cnt; q += 2) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const float4 sj = A[q + u];   // x, y, z
+            const float4 sg = Gv[q + u];  // gx, gy, gz
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                float dx = sj.x - k.x[s], dy = sj.y - k.y[s], dz = sj.z - k.z[s];
+                float r2 = fmaf(dx, dx, kTiny);
+                r2 = fmaf(dy, dy, r2);
+                r2 = fmaf(dz, dz, r2);
+                trk = fminf(trk, r2);
+                float ri = rsqrt_approx(r2);
+                float ri2 = ri * ri;
+                float ri3 = ri2 * ri;
+                float vx = sg.x - k.gx[s], vy = sg.y - k.gy[s], vz = sg.z - k.gz[s];
+                float dv = dx * vx;
+                dv = fmaf(dy, vy, dv);
+                dv = fmaf(dz, vz, dv);
+                float c = dv * (-3.0f * ri2);
+                float wx = fmaf(c, dx, vx), wy = fmaf(c, dy, vy), wz = fmaf(c, dz, vz);
+                k.sx[s] = fmaf(ri3, wx, k.sx[s]);
+                k.sy[s] = fmaf(ri3, wy, k.sy[s]);
+                k.sz[s] = fmaf(ri3, wz, k.sz[s]);
+            }
+        }
+    }
+}
+
+// Adjoint, exact path: J v = F (v + G (d.v) d) with F = f, G = (f'/r) / f,
+// selecting the softened branch of Eq. (spline) for r^2 < eps_s^2.
+template <int S>
+__device__ __forceinline__ void stage_adj_exact(const float4* __restrict__ A, const float4* __restrict__ Gv,
+                                                int cnt, SinkSet<S>& k, const Coef& cf)
+{
+#pragma unroll 1
+    for (int q = 0; q < cnt; ++q) {
+        const float4 sj = A[q];
+        const float4 sg = Gv[q];
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            float dx = sj.x - k.x[s], dy = sj.y - k.y[s], dz = sj.z - k.z[s];
+            float r2 = fmaf(dx, dx, kTiny);
+            r2 = fmaf(dy, dy, r2);
+            r2 = fmaf(dz, dz, r2);
+            float ri = rsqrt_approx(r2);
+            float ri2 = ri * ri;
+            float F, G;
+            if (r2 < cf.eps2) {
+                F = fmaf(r2, fmaf(cf.c1, ri, cf.c2), cf.c0);
+                G = fmaf(cf.e0, ri, cf.e1) / F;
+            } else {
+                F = ri2 * ri;
+                G = -3.0f * ri2;
+            }
+            float vx = sg.x - k.gx[s], vy = sg.y - k.gy[s], vz = sg.z - k.gz[s];
+            float dv = dx * vx;
+            dv = fmaf(dy, vy, dv);
+            dv = fmaf(dz, vz, dv);
+            float c = dv * G;
+            k.sx[s] = fmaf(F, fmaf(c, dx, vx), k.sx[s]);
+            k.sy[s] = fmaf(F, fmaf(c, dy, vy), k.sy[s]);
+            k.sz[s] = fmaf(F, fmaf(c, dz, vz), k.sz[s]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent kernel
+// ---------------------------------------------------------------------------
+
+template <int B, bool ADJ>
+struct WarpSmem {
+    // A[2][B] float4 sources, G[2][B] float4 source gradients (adjoint),
+    // SH[2][B] float2 (dy, dz) frame shift of each staged source, then the
+    // segment table: seg_pre[max_nseg + 1], seg_start, seg_dy, seg_dz [max_nseg].
+    static constexpr size_t a_bytes = 2ull * B * sizeof(float4);
+    static constexpr size_t g_bytes = ADJ ? 2ull * B * sizeof(float4) : 0;
+    static constexpr size_t sh_bytes = 2ull * B * sizeof(float2);
+    static size_t __host__ __device__ bytes(int max_nseg)
+    {
+        size_t t = (size_t)(4 * max_nseg + 1) * 4;
+        return a_bytes + g_bytes + sh_bytes + ((t + 15) & ~size_t(15));
+    }
+};
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc)
+{
+    unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+struct ItemCtx {
+    int K, R, cb;
+    int i, j, k;
+    int ns;           // 2R+1
+    int sc_start;     // lane c < ns: first sorted slot of sink cell c
+    int sc_cnt;       // lane c < ns: occupancy of sink cell c
+    int sc_incl;      // lane c < ns: inclusive prefix of sink counts
+    int n_sink;
+    int chunk_begin;
+    int n_src;
+    int n_c0;         // sources of the centre cell (processed first, exact path)
+};
+
+// Sorted slot and partial slot of the sink at pencil position p.
+__device__ __forceinline__ void sink_lookup(const ItemCtx& it, int p, int* at, int* slot)
+{
+    int c_sel = 0, a = 0;
+    for (int c = 0; c < it.ns; ++c) {
+        int inc = __shfl_sync(kFull, it.sc_incl, c);
+        int cnt = __shfl_sync(kFull, it.sc_cnt, c);
+        int st = __shfl_sync(kFull, it.sc_start, c);
+        if (p >= inc - cnt && p < inc) {
+            c_sel = c;
+            a = st + (p - (inc - cnt));
+        }
+    }
+    *at = a;
+    *slot = c_sel;
+}
+
+template <int S, int B, bool ADJ>
+__device__ __forceinline__ void run_item(const ItemCtx& it, const Coef& cf,
+                                         const float4* __restrict__ rel, const float4* __restrict__ gs,
+                                         float4* bufA, float4* bufG, float2* bufSH, const int* seg_pre,
+                                         const int* seg_start, const float* seg_dy, const float* seg_dz,
+                                         float* __restrict__ partial, int Ntot)
+{
+    const int lane = threadIdx.x & 31;
+    SinkSet<S> k;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int p = it.chunk_begin + s * 32 + lane;
+        int at, slot;
+        sink_lookup(it, p, &at, &slot);
+        const bool ok = p < it.n_sink;
+        float4 r = ok ? rel[at] : make_float4(kFarSink, kFarSink, kFarSink, 0.0f);
+        k.x[s] = r.x + (float)(slot - it.R);
+        k.y[s] = r.y;
+        k.z[s] = r.z;
+        if constexpr (ADJ) {
+            float4 g = ok ? gs[at] : make_float4(0.f, 0.f, 0.f, 0.f);
+            k.gx[s] = g.x;
+            k.gy[s] = g.y;
+            k.gz[s] = g.z;
+        }
+        k.ax[s] = k.ay[s] = k.az[s] = 0.0f;
+    }
+
+    constexpr int PER = B / 32;
+    const int nst0 = (it.n_c0 + B - 1) / B;
+    const int nst = nst0 + (it.n_src - it.n_c0 + B - 1) / B;
+    int cur = 0;
+
+    auto stage_range = [&](int st, int& beg, int& end) {
+        if (st < nst0) {
+            beg = st * B;
+            end = min(beg + B, it.n_c0);
+        } else {
+            beg = it.n_c0 + (st - nst0) * B;
+            end = min(beg + B, it.n_src);
+        }
+    };
+    // Issue the asynchronous copies of stage st into buffer buf.  Each lane
+    // copies the sources it will later shift into the item's frame.
+    auto issue = [&](int st, int buf) {
+        int beg, end;
+        stage_range(st, beg, end);
+#pragma unroll
+        for (int t = 0; t < PER; ++t) {
+            const int p = beg + t * 32 + lane;
+            const int slot = buf * B + t * 32 + lane;
+            if (p < end) {
+                while (p >= seg_pre[cur + 1]) ++cur;
+                const int at = seg_start[cur] + (p - seg_pre[cur]);
+                cp_async16(&bufA[slot], &rel[at]);
+                if constexpr (ADJ) cp_async16(&bufG[slot], &gs[at]);
+                bufSH[slot] = make_float2(seg_dy[cur], seg_dz[cur]);
+            } else {
+                bufA[slot] = make_float4(kFarSrc, kFarSrc, kFarSrc, 0.0f);
+                if constexpr (ADJ) bufG[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+                bufSH[slot] = make_float2(0.0f, 0.0f);
+            }
+        }
+        cp_async_commit();
+    };
+    // Shift this lane's own staged sources into the item's frame.
+    auto fixup = [&](int buf) {
+#pragma unroll
+        for (int t = 0; t < PER; ++t) {
+            const int slot = buf * B + t * 32 + lane;
+            float4 v = bufA[slot];
+            const float2 sh = bufSH[slot];
+            v.y += sh.x;
+            v.z += sh.y;
+            bufA[slot] = v;
+        }
+    };
+
+    if (nst > 0) issue(0, 0);
+    for (int st = 0; st < nst; ++st) {
+        const int buf = st & 1;
+        if (st + 1 < nst) {
+            issue(st + 1, buf ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        fixup(buf);
+        __syncwarp();
+        int beg, end;
+        stage_range(st, beg, end);
+        const int cnt = (end - beg + 7) & ~7;
+        const float4* A = bufA + buf * B;
+        const float4* G = bufG + buf * B;
+        bool exact = st < nst0;
+        if (!exact) {
+#pragma unroll
+            for (int s = 0; s < S; ++s) k.sx[s] = k.sy[s] = k.sz[s] = 0.0f;
+            float trk = kBig;
+            if constexpr (ADJ) stage_adj_fast<S>(A, G, cnt, k, trk);
+            else stage_fwd_fast<S>(A, cnt, k, trk);
+            exact = __any_sync(kFull, trk < cf.eps2);
+        }
+        if (exact) {
+#pragma unroll
+            for (int s = 0; s < S; ++s) k.sx[s] = k.sy[s] = k.sz[s] = 0.0f;
+            if constexpr (ADJ) stage_adj_exact<S>(A, G, cnt, k, cf);
+            else stage_fwd_exact<S>(A, cnt, k, cf);
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            k.ax[s] += k.sx[s];
+            k.ay[s] += k.sy[s];
+            k.az[s] += k.sz[s];
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int p = it.chunk_begin + s * 32 + lane;
+        int at, slot;
+        sink_lookup(it, p, &at, &slot);
+        if (p < it.n_sink) {
+            const size_t base = (size_t)slot * 3 * (size_t)Ntot + (size_t)at;
+            partial[base] = k.ax[s];
+            partial[base + (size_t)Ntot] = k.ay[s];
+            partial[base + 2 * (size_t)Ntot] = k.az[s];
+        }
+    }
+}
+
+template <int SMAX, int B, bool ADJ>
+__global__ void __launch_bounds__(256, 2)
+k_force(const BoxDev* __restrict__ boxes, const int* __restrict__ off, const float4* __restrict__ rel,
+        const float4* __restrict__ gs, const int4* __restrict__ items, WsHeader* hdr,
+        float* __restrict__ partial, int Ntot, int max_nseg)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    using W = WarpSmem<B, ADJ>;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned char* w = smem + (size_t)wid * W::bytes(max_nseg);
+    float4* bufA = reinterpret_cast<float4*>(w);
+    float4* bufG = reinterpret_cast<float4*>(w + W::a_bytes);
+    float2* bufSH = reinterpret_cast<float2*>(w + W::a_bytes + W::g_bytes);
+    int* seg_pre = reinterpret_cast<int*>(w + W::a_bytes + W::g_bytes + W::sh_bytes);
+    int* seg_start = seg_pre + max_nseg + 1;
+    float* seg_dy = reinterpret_cast<float*>(seg_start + max_nseg);
+    float* seg_dz = seg_dy + max_nseg;
+
+    const int n_items = *((volatile int*)&hdr->n_items);
+    constexpr int CH = 32 * SMAX;
+    for (;;) {
+        int itn = 0;
+        if (lane == 0) itn = atomicAdd(&hdr->queue, 1);
+        itn = __shfl_sync(kFull, itn, 0);
+        if (itn >= n_items) break;
+        const int4 item = items[itn];
+        const BoxDev& Bx = boxes[item.z];
+        ItemCtx it;
+        it.K = Bx.K;
+        it.R = Bx.R;
+        it.cb = Bx.cell_base;
+        Coef cf;
+        cf.c0 = Bx.c0;
+        cf.c1 = Bx.c1;
+        cf.c2 = Bx.c2;
+        cf.e0 = Bx.e0;
+        cf.e1 = Bx.e1;
+        cf.eps2 = Bx.eps2;
+        const int K = it.K, R = it.R;
+        const int l = item.x - it.cb;
+        it.i = l / (K * K);
+        it.j = (l / K) % K;
+        it.k = l % K;
+        it.ns = 2 * R + 1;
+        // sink cells (lanes 0..2R)
+        it.sc_start = 0;
+        it.sc_cnt = 0;
+        if (lane < it.ns)
+            it.sc_cnt = cell_count(off, it.cb + (wrap(it.i + lane - R, K) * K + it.j) * K + it.k,
+                                   &it.sc_start);
+        int incl = it.sc_cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        it.sc_incl = incl;
+        it.n_sink = __shfl_sync(kFull, incl, it.ns - 1);
+        it.chunk_begin = item.y * CH;
+        // source segments: centre cell first, then (b, d) in row order without it
+        const int nseg = it.ns * it.ns;
+        int carry = 0;
+        for (int base = 0; base < nseg; base += 32) {
+            const int q = base + lane;
+            int cnt = 0, st = 0, b = 0, d = 0;
+            if (q < nseg) {
+                int r = q == 0 ? (nseg >> 1) : (q <= (nseg >> 1) ? q - 1 : q);
+                b = r / it.ns - R;
+                d = r % it.ns - R;
+                cnt = cell_count(off, it.cb + (it.i * K + wrap(it.j + b, K)) * K + wrap(it.k + d, K), &st);
+            }
+            int inc = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(kFull, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (q < nseg) {
+                seg_pre[q] = carry + inc - cnt;
+                seg_start[q] = st;
+                seg_dy[q] = (float)b;
+                seg_dz[q] = (float)d;
+            }
+            carry += __shfl_sync(kFull, inc, 31);
+        }
+        if (lane == 0) seg_pre[nseg] = carry;
+        it.n_src = carry;
+        __syncwarp();
+        it.n_c0 = seg_pre[1];
+        const int n_chunk = min(CH, it.n_sink - it.chunk_begin);
+        const int S = (n_chunk + 31) >> 5;
+        if (SMAX >= 4 && S >= 3)
+            run_item<(SMAX >= 4 ? 4 : 1), B, ADJ>(it, cf, rel, gs, bufA, bufG, bufSH, seg_pre, seg_start,
+                                                  seg_dy, seg_dz, partial, Ntot);
+        else if (SMAX >= 2 && S == 2)
+            run_item<(SMAX >= 2 ? 2 : 1), B, ADJ>(it, cf, rel, gs, bufA, bufG, bufSH, seg_pre, seg_start,
+                                                  seg_dy, seg_dz, partial, Ntot);
+        else
+            run_item<1, B, ADJ>(it, cf, rel, gs, bufA, bufG, bufSH, seg_pre, seg_start, seg_dy, seg_dz,
+                                partial, Ntot);
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Combine: sum the 2R+1 partials in FP64, scale, scatter to input order
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256)
+k_combine(const BoxDev* __restrict__ boxes, int nboxes, const float* __restrict__ partial,
+          const int* __restrict__ perm, int Ntot, float* __restrict__ out,
+          double* __restrict__ chunk_sums, bool adjoint)
+{
+    // block = one chunk of kCombineChunk sorted slots of a single box
+    __shared__ double red[3][8];
+    int chunk = blockIdx.x;
+    int lo = 0, hi = nboxes - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (boxes[mid].chunk_base <= chunk) lo = mid;
+        else hi = mid - 1;
+    }
+    const BoxDev& B = boxes[lo];
+    const int nslot = 2 * B.R + 1;
+    const double scale = adjoint ? B.scale_grad : B.scale_acc;
+    const double m = 1.0 / (double)B.N;
+    const int s0 = B.part_base + (chunk - B.chunk_base) * kCombineChunk;
+    const int s1 = min(s0 + kCombineChunk, B.part_base + B.N);
+    double net[3] = {0.0, 0.0, 0.0};
+    for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+        const int e = perm[s];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double v = 0.0;
+            for (int q = 0; q < nslot; ++q) v += (double)partial[((size_t)q * 3 + c) * (size_t)Ntot + s];
+            float a = (float)(v * scale);
+            out[3 * (size_t)e + c] = a;
+            net[c] += m * (double)a;
+        }
+    }
+    if (chunk_sums) {
+        int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double v = net[c];
+            for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+            if (lane == 0) red[c][w] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            double v = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += red[threadIdx.x][q];
+            chunk_sums[3 * (size_t)chunk + threadIdx.x] = v;
+        }
+    }
+}
+
+__global__ void k_net(const BoxDev* __restrict__ boxes, int nboxes, const double* __restrict__ chunk_sums,
+                      double* __restrict__ net)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nboxes) return;
+    const BoxDev& B = boxes[b];
+    int n = (B.N + kCombineChunk - 1) / kCombineChunk;
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int q = 0; q < n; ++q)
+        for (int c = 0; c < 3; ++c) v[c] += chunk_sums[3 * (size_t)(B.chunk_base + q) + c];
+    for (int c = 0; c < 3; ++c) net[3 * (size_t)b + c] = v[c];
+}
+
+int grid_for(size_t n, int threads)
+{
+    size_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 65535ull * 16) b = 65535ull * 16;
+    return (int)b;
+}
+
+typedef void (*ForceKernel)(const BoxDev*, const int*, const float4*, const float4*, const int4*,
+                            WsHeader*, float*, int, int);
+
+template <bool ADJ>
+ForceKernel pick_kernel(int smax, int stage)
+{
+    if (stage == 128) {
+        if (smax == 4) return k_force<4, 128, ADJ>;
+        if (smax == 2) return k_force<2, 128, ADJ>;
+        if (smax == 1) return k_force<1, 128, ADJ>;
+    } else if (stage == 64) {
+        if (smax == 4) return k_force<4, 64, ADJ>;
+        if (smax == 2) return k_force<2, 64, ADJ>;
+        if (smax == 1) return k_force<1, 64, ADJ>;
+    }
+    return nullptr;
+}
+
+size_t force_smem_bytes(bool adjoint, const ForceTuning& t, int max_nseg)
+{
+    size_t per = 0;
+    if (t.stage == 128) per = adjoint ? WarpSmem<128, true>::bytes(max_nseg) : WarpSmem<128, false>::bytes(max_nseg);
+    else per = adjoint ? WarpSmem<64, true>::bytes(max_nseg) : WarpSmem<64, false>::bytes(max_nseg);
+    return per * (size_t)t.warps_per_block;
+}
+
+}  // namespace
+
+bool force_tuning_supported(const ForceTuning& t)
+{
+    bool s_ok = t.sinks_per_lane == 1 || t.sinks_per_lane == 2 || t.sinks_per_lane == 4;
+    bool b_ok = t.stage == 64 || t.stage == 128;
+    bool w_ok = t.warps_per_block == 4 || t.warps_per_block == 8;
+    return s_ok && b_ok && w_ok && t.blocks_per_sm >= 0 && t.blocks_per_sm <= 8;
+}
+
+int force_blocks_per_sm(bool adjoint, const ForceTuning& t, int max_nseg)
+{
+    ForceKernel kfn = adjoint ? pick_kernel<true>(t.sinks_per_lane, t.stage)
+                              : pick_kernel<false>(t.sinks_per_lane, t.stage);
+    if (!kfn) return 0;
+    size_t smem = force_smem_bytes(adjoint, t, max_nseg);
+    if (ensure_smem((const void*)kfn, (int)smem) != cudaSuccess) return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)kfn, t.warps_per_block * 32, smem) !=
+        cudaSuccess)
+        return 0;
+    return nb;
+}
+
+cudaError_t launch_pencils(const BoxDev* boxes, int nboxes, int Ctot, const int* cell_off, int chunk,
+                           int* chunks, unsigned* bucket_count, unsigned char* bucket_of, WsHeader* hdr,
+                           cudaStream_t s)
+{
+    k_pencils<<<grid_for(Ctot, 256), 256, 0, s>>>(boxes, nboxes, Ctot, cell_off, chunk, chunks,
+                                                  bucket_count, bucket_of, hdr);
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_bucket_scan<<<1, kBuckets, 0, s>>>(bucket_count, hdr);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_items(const BoxDev* boxes, int nboxes, int Ctot, const int* chunks,
+                         const unsigned char* bucket_of, unsigned* bucket_count, int4* items,
+                         WsHeader* hdr, cudaStream_t s)
+{
+    (void)hdr;
+    k_items<<<grid_for(Ctot, 256), 256, 0, s>>>(boxes, nboxes, Ctot, chunks, bucket_of, bucket_count,
+                                                items);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_g(const float* g, const int* perm, int Ntot, float4* gs, cudaStream_t s)
+{
+    k_gather_g<<<grid_for(Ntot, 256), 256, 0, s>>>(g, perm, Ntot, gs);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_force(bool adjoint, const ForceTuning& t, const BoxDev* boxes, const int* cell_off,
+                         const float4* rel, const float4* gs, const int4* items, WsHeader* hdr,
+                         float* partial, int Ntot, int max_nseg, cudaStream_t s)
+{
+    ForceKernel kfn = adjoint ? pick_kernel<true>(t.sinks_per_lane, t.stage)
+                              : pick_kernel<false>(t.sinks_per_lane, t.stage);
+    if (!kfn) return cudaErrorInvalidValue;
+    size_t smem = force_smem_bytes(adjoint, t, max_nseg);
+    cudaError_t e = ensure_smem((const void*)kfn, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)kfn, t.warps_per_block * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (nb < 1) return cudaErrorInvalidConfiguration;
+    if (t.blocks_per_sm > 0 && t.blocks_per_sm < nb) nb = t.blocks_per_sm;
+    kfn<<<sms * nb, t.warps_per_block * 32, smem, s>>>(boxes, cell_off, rel, gs, items, hdr, partial, Ntot,
+                                                       max_nseg);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine(bool adjoint, const BoxDev* boxes, int nboxes, int nchunks, const float* partial,
+                           const int* perm, int Ntot, float* out, double* chunk_sums, cudaStream_t s)
+{
+    if (nchunks <= 0) return cudaSuccess;
+    k_combine<<<nchunks, 256, 0, s>>>(boxes, nboxes, partial, perm, Ntot, out, chunk_sums, adjoint);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_net(const BoxDev* boxes, int nboxes, const double* chunk_sums, double* net,
+                       cudaStream_t s)
+{
+    k_net<<<(nboxes + 63) / 64, 64, 0, s>>>(boxes, nboxes, chunk_sums, net);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace nf

@@ -1,0 +1,121 @@
+// Internal declarations of libnf (not part of the C ABI).
+//
+// Data layout in device memory (all regions caller-owned, carved out of the
+// workspace by nf_api.cu):
+//   keys/vals   int32 [N]       radix-sort double buffers (cell id, particle)
+//   cell_off    int32 [C+1]     first sorted slot of every global cell
+//   rel         float4 [N]      sorted cell-centred offsets, .w = index bits
+//   perm        int32 [N]       sorted slot -> particle (global index)
+//   items       int4 [<= M]     work items: (global centre cell, chunk, box, -)
+//   partial     float [(2R+1)*3][N]  per-pencil partial sums, sorted order
+// A "global cell" numbers the cells of all boxes of a batch back to back:
+// box b owns cells [cell_base_b, cell_base_b + K_b^3).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/nf.h"
+
+namespace nf {
+
+// Per-box constants in device memory.  Lengths in cell units unless noted.
+struct BoxDev {
+    int K;
+    int R;
+    int cell_base;   // first global cell of this box
+    int part_base;   // first particle (row of pos_cat) of this box
+    int N;
+    int chunk_base;  // first combine chunk of this box
+    double kl;       // K / box, multiplies a box-unit coordinate into cell units
+    double scale_acc;   // m / w^2: cell-unit pair sums -> box-unit acceleration
+    double scale_grad;  // m / w^3: cell-unit Jacobian sums -> box-unit gradient
+    // Eq. (spline) in cell units: f(r) = min(c0 + r^2 (c2 + c1 / r), 1 / r^3)
+    float c0, c1, c2;
+    float eps2;      // eps_s^2 (cell units^2)
+    // f'(r)/r inside the softening: e1 + e0 / r
+    float e0, e1;
+    float pad0, pad1;
+};
+static_assert(sizeof(BoxDev) % 16 == 0, "BoxDev must stay 16-byte aligned");
+
+// Header at the start of every workspace (256 bytes).
+struct WsHeader {
+    int status;          // nf_status bits set on the device
+    int queue;           // persistent work queue head
+    int n_items;         // number of work items
+    int max_occ;         // largest cell occupancy
+    unsigned long long pairs;       // sum over pencils of n_sink * n_src
+    unsigned long long lane_pairs;  // sink lanes issued * n_src
+    int pad[56];
+};
+static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
+
+constexpr int kMaxBoxesPerFill = 32;
+struct BoxFill {
+    int first;
+    int count;
+    BoxDev b[kMaxBoxesPerFill];
+};
+
+constexpr int kCombineChunk = 4096;  // particles per combine block (never straddles boxes)
+constexpr int kBuckets = 64;         // cost buckets of the LPT work order
+
+// Counts kernel launches (all translation units).
+void count_launches(int n);
+// Sets the dynamic shared-memory limit of a kernel once per (device, size).
+cudaError_t ensure_smem(const void* fn, int bytes);
+
+// ---- launch wrappers (nf_bin.cu) ----
+cudaError_t launch_fill_boxes(const BoxFill& f, BoxDev* boxes, cudaStream_t s);
+cudaError_t launch_shift(const float* pos, int Ntot, const BoxDev* boxes, int nboxes,
+                         int* keys, int* counts, WsHeader* hdr, cudaStream_t s);
+// Exclusive scan of n uint32 values in place; aux must hold scan_aux_words(n) words.
+size_t scan_aux_words(size_t n);
+cudaError_t launch_scan(unsigned* data, size_t n, unsigned* aux, cudaStream_t s);
+
+struct RadixPlan {
+    int passes;
+    int digit_bits;
+    int bins;
+    int tiles;
+};
+RadixPlan radix_plan(int64_t N, int64_t C);
+size_t radix_hist_words(const RadixPlan& p);
+// Stable LSD radix sort of keys (0 .. C-1), values start as the index.
+// keys_a holds the input keys; the sorted particle order lands in perm.
+cudaError_t radix_sort(const RadixPlan& p, int N, int* keys_a, int* keys_b, int* vals_a,
+                       int* vals_b, int* perm, unsigned* hist, unsigned* aux,
+                       cudaStream_t s);
+cudaError_t launch_rel(const float* pos, int Ntot, const BoxDev* boxes, int nboxes,
+                       const int* perm, float4* rel, cudaStream_t s);
+
+// ---- work list, force, adjoint, combine (nf_force.cu) ----
+struct ForceTuning {
+    int sinks_per_lane;
+    int stage;
+    int warps_per_block;
+    int blocks_per_sm;
+};
+
+cudaError_t launch_pencils(const BoxDev* boxes, int nboxes, int Ctot, const int* cell_off,
+                           int chunk, int* chunks, unsigned* bucket_count,
+                           unsigned char* bucket_of, WsHeader* hdr, cudaStream_t s);
+cudaError_t launch_items(const BoxDev* boxes, int nboxes, int Ctot, const int* chunks,
+                         const unsigned char* bucket_of, unsigned* bucket_count,
+                         int4* items, WsHeader* hdr, cudaStream_t s);
+cudaError_t launch_gather_g(const float* g, const int* perm, int Ntot, float4* gs,
+                            cudaStream_t s);
+cudaError_t launch_force(bool adjoint, const ForceTuning& t, const BoxDev* boxes,
+                         const int* cell_off, const float4* rel, const float4* gs,
+                         const int4* items, WsHeader* hdr, float* partial, int Ntot,
+                         int max_nseg, cudaStream_t s);
+cudaError_t launch_combine(bool adjoint, const BoxDev* boxes, int nboxes, int nchunks,
+                           const float* partial, const int* perm, int Ntot, float* out,
+                           double* chunk_sums, cudaStream_t s);
+cudaError_t launch_net(const BoxDev* boxes, int nboxes, const double* chunk_sums,
+                       double* net, cudaStream_t s);
+bool force_tuning_supported(const ForceTuning& t);
+int force_blocks_per_sm(bool adjoint, const ForceTuning& t, int max_nseg);
+
+}  // namespace nf
