@@ -190,6 +190,43 @@ int nf_forces_adjoint_batched(const nf_box *boxes, int nboxes, const float *pos_
                               void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* Forces without a caller-provided workspace                                */
+/* ------------------------------------------------------------------------ */
+
+/* Size of the fixed scratch array behind nf_forces_noalloc (32 MiB). */
+#define NF_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* nf_forces for callers that cannot allocate device memory.  This entry point
+ * is an addition of this library; the paper has no counterpart.
+ *
+ * Who it is for: code that may only touch the buffers it is handed and cannot
+ * call cudaMalloc to make a workspace, for example a plugin inside a host
+ * program whose device memory is owned by that program's own pool allocator,
+ * or a caller that must not allocate while other work is being captured.
+ *
+ * What it does: exactly what nf_forces does with the same arguments (pos, acc
+ * and net are still the caller's device buffers), but its scratch space is a
+ * fixed array of NF_NOALLOC_SCRATCH_BYTES compiled into the library instead
+ * of a workspace.  Every GPU that loads the library keeps that array until
+ * the process exits.  The call allocates nothing and frees nothing.
+ *
+ * Limits and rules:
+ *   - A problem whose workspace (nf_workspace_bytes with the default tuning)
+ *     is larger than the array is rejected with NF_ERR_WORKSPACE and a
+ *     message; nothing is launched.  Use nf_forces with your own workspace
+ *     for larger boxes.  Other bad arguments give NF_ERR_ARG as for nf_forces.
+ *   - The first call on a device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - All calls share the one array, and it keeps the contents of the last
+ *     call; each call clears the parts that must start at zero itself.  Calls
+ *     that can overlap on the GPU (other streams, other host threads) race on
+ *     the array and corrupt each other: order them on one stream.
+ *   - The array's device status word is not exposed; check the input for
+ *     non-finite coordinates on the caller's side if that matters. */
+int nf_forces_noalloc(const float *pos, int64_t N, double box, int K, int R, double eps,
+                      float *acc, double *net, void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* Status and statistics                                                     */
 /* ------------------------------------------------------------------------ */
 

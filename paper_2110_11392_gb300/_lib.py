@@ -80,6 +80,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         "nf_profile_enable": (i32, [i32]),
         "nf_profile_read": (i32, [i32, P]),
         "nf_kernel_launches": (i64, []),
+        "nf_forces_noalloc": (i32, [P, i64, f64, i32, i32, f64, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -94,7 +95,7 @@ def exported_symbols() -> Sequence[str]:
             "nf_bin", "nf_forces", "nf_forces_adjoint", "nf_forces_batched",
             "nf_forces_adjoint_batched", "nf_set_default_tuning", "nf_get_default_tuning",
             "nf_status_read", "nf_stats_read", "nf_profile_enable", "nf_profile_read",
-            "nf_kernel_launches")
+            "nf_kernel_launches", "nf_forces_noalloc")
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -230,3 +231,12 @@ def nf_profile_read(back: int = 0) -> dict:
 
 def nf_kernel_launches() -> int:
     return int(load().nf_kernel_launches())
+
+
+def nf_forces_noalloc(pos: torch.Tensor, box: float, K: int, R: int, eps: float, acc: torch.Tensor,
+                      net: Optional[torch.Tensor] = None, stream=None) -> None:
+    """nf_forces without a workspace: the library's fixed scratch array is used
+    instead (for callers that cannot allocate device memory; see include/nf.h)."""
+    _check(load().nf_forces_noalloc(_ptr(pos), pos.shape[0], float(box), int(K), int(R), float(eps),
+                                    _ptr(acc), _ptr(net), _stream(stream)),
+           "nf_forces_noalloc")

@@ -346,6 +346,38 @@ int forces_entry(const nf_box* boxes, int nboxes, bool adjoint, const float* pos
 }  // namespace
 }  // namespace nf
 
+namespace nf {
+namespace {
+
+// Scratch of nf_forces_noalloc: a fixed array in every loaded device image.
+// Host code must not pass this name to a kernel (on the host it is only a
+// stand-in); its device address comes from cudaGetSymbolAddress, looked up
+// once per device with that device current and then reused.
+constexpr int kMaxDevices = 64;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NF_NOALLOC_SCRATCH_BYTES];
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+int noalloc_scratch(void** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "nf_forces_noalloc: current device");
+    if (dev < 0 || dev >= kMaxDevices) return fail(NF_ERR_ARG, "nf_forces_noalloc: device %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "nf_forces_noalloc: scratch address");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return NF_OK;
+}
+
+}  // namespace
+}  // namespace nf
+
 using namespace nf;
 
 extern "C" {
@@ -434,6 +466,31 @@ void nf_get_default_tuning(nf_tuning* t)
     t->stage = g_default_tuning.stage;
     t->warps_per_block = g_default_tuning.warps_per_block;
     t->blocks_per_sm = g_default_tuning.blocks_per_sm;
+}
+
+int nf_forces_noalloc(const float* pos, int64_t N, double box, int K, int R, double eps, float* acc, double* net,
+                      void* stream)
+{
+    g_last_error.clear();
+    // Host-side checks first: nothing touches the device for a rejected call.
+    nf_box b = one_box(N, box, K, R, eps);
+    ForceTuning t;
+    int rc = check_tuning(nullptr, &t);
+    if (rc) return rc;
+    Plan p;
+    rc = make_plan(&b, 1, true, 32 * t.sinks_per_lane, &p);
+    if (rc) return rc;
+    if (!pos || !acc) return fail(NF_ERR_ARG, "null pointer argument");
+    if (p.total > (size_t)NF_NOALLOC_SCRATCH_BYTES)
+        return fail(NF_ERR_WORKSPACE,
+                    "nf_forces_noalloc: N = %lld, K = %d, R = %d needs %zu bytes of scratch, more than the "
+                    "library's fixed %u-byte array; call nf_forces with a workspace instead",
+                    (long long)N, K, R, p.total, (unsigned)NF_NOALLOC_SCRATCH_BYTES);
+    void* scratch = nullptr;
+    rc = noalloc_scratch(&scratch);
+    if (rc) return rc;
+    return forces_entry(&b, 1, false, pos, nullptr, acc, net, nullptr, scratch, NF_NOALLOC_SCRATCH_BYTES,
+                        stream);
 }
 
 int nf_status_read(void* ws, void* stream)
