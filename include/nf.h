@@ -152,8 +152,12 @@ typedef struct {
  *   stage           sources staged in shared memory per step: 64 or 128;
  *   warps_per_block 4 or 8;
  *   blocks_per_sm   resident blocks of the persistent kernel per SM, 0 = as
- *                   many as fit.
- * Unsupported combinations are rejected with NF_ERR_ARG. */
+ *                   many as fit.  Asking for 24 or more warps per SM
+ *                   (warps_per_block * blocks_per_sm) with sinks_per_lane <= 2
+ *                   selects the register-lean build of the kernel (at most
+ *                   85 registers per thread).
+ * Unsupported combinations are rejected with NF_ERR_ARG.  The built-in
+ * default is {2, 128, 8, 0}. */
 typedef struct {
     int sinks_per_lane;
     int stage;

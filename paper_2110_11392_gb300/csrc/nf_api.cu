@@ -64,7 +64,7 @@ cudaError_t prof_mark(int i, cudaStream_t s)
     }
     return cudaEventRecord(ev, s);
 }
-ForceTuning g_default_tuning = {4, 128, 8, 0};
+ForceTuning g_default_tuning = {2, 128, 8, 0};
 
 int fail(int code, const char* fmt, ...)
 {
@@ -449,7 +449,7 @@ int nf_set_default_tuning(const nf_tuning* t)
 {
     g_last_error.clear();
     if (!t) {
-        g_default_tuning = ForceTuning{4, 128, 8, 0};
+        g_default_tuning = ForceTuning{2, 128, 8, 0};
         return NF_OK;
     }
     ForceTuning f;

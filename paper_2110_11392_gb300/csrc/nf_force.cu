@@ -210,37 +210,117 @@ struct Coef {
     float eps2;
 };
 
+// Packed FP32x2 arithmetic (sm_100+ `add/mul/fma.rn.f32x2`): one instruction
+// works on the two halves of a 64-bit register pair.  The pair loops put two
+// sources side by side in each pair, so every instruction computes two
+// interactions of one sink; this halves the issue slots of the FP32 work.
+typedef unsigned long long f2;
+
+// Where r^-2 comes from in the fast paths: 1 = MUFU reciprocal, 0 = r^-1 * r^-1
+// on the FMA pipe (measured per direction on GB300).
+#ifndef NF_FWD_RCP
+#define NF_FWD_RCP 0
+#endif
+#ifndef NF_ADJ_RCP
+#define NF_ADJ_RCP 1
+#endif
+
+__device__ __forceinline__ f2 pk(float lo, float hi)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float lo(f2 v)
+{
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return a;
+}
+__device__ __forceinline__ float hi(f2 v)
+{
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return b;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b)
+{
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b)
+{
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ f2 rsqrt2(f2 v) { return pk(rsqrt_approx(lo(v)), rsqrt_approx(hi(v))); }
+// r^-2 from the MUFU reciprocal: keeps the FMA pipe (the bottleneck) for the sums
+__device__ __forceinline__ f2 rcp2(f2 v) { return pk(rcp_approx(lo(v)), rcp_approx(hi(v))); }
+
+// Per-lane sink state.  Positions and gradients are held negated and
+// duplicated in both halves ({-x, -x}), so d = source + sink is one add2.
 template <int S>
 struct SinkSet {
-    float x[S], y[S], z[S];
-    float gx[S], gy[S], gz[S];
+    f2 nx[S], ny[S], nz[S];   // -position
+    f2 ngx[S], ngy[S], ngz[S];  // -g (adjoint)
+    f2 sx[S], sy[S], sz[S];   // current stage, even/odd sources in the halves
     float ax[S], ay[S], az[S];  // running totals
-    float sx[S], sy[S], sz[S];  // current stage
 };
 
-// Forward, fast path: f = r^-3 for every pair, tracks the smallest r^2.
+// Stage buffers of one warp in shared memory: sources as structure of arrays,
+// four consecutive sources per 16-byte word.
+struct StageView {
+    const float4* X;
+    const float4* Y;
+    const float4* Z;
+    const float4* GX;
+    const float4* GY;
+    const float4* GZ;
+};
+
+// Forward, fast path: f = r^-3 for every pair; tracks the smallest r^2.
 template <int S>
-__device__ __forceinline__ void stage_fwd_fast(const float4* __restrict__ A, int cnt,
-                                               SinkSet<S>& k, float& trk)
+__device__ __forceinline__ void stage_fwd_fast(const StageView& v, int cnt, SinkSet<S>& k, float& trk)
 {
+    const f2 tiny = pk(kTiny, kTiny);
 #pragma unroll 1
     for (int q = 0; q < cnt; q += 4) {
+        const float4 xs = v.X[q >> 2], ys = v.Y[q >> 2], zs = v.Z[q >> 2];
+        const f2 px[2] = {pk(xs.x, xs.y), pk(xs.z, xs.w)};
+        const f2 py[2] = {pk(ys.x, ys.y), pk(ys.z, ys.w)};
+        const f2 pz[2] = {pk(zs.x, zs.y), pk(zs.z, zs.w)};
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const float4 sj = A[q + u];
+        for (int h = 0; h < 2; ++h) {
 #pragma unroll
             for (int s = 0; s < S; ++s) {
-                float dx = sj.x - k.x[s], dy = sj.y - k.y[s], dz = sj.z - k.z[s];
-                float r2 = fmaf(dx, dx, kTiny);
-                r2 = fmaf(dy, dy, r2);
-                r2 = fmaf(dz, dz, r2);
-                trk = fminf(trk, r2);
-                float ri = rsqrt_approx(r2);
-                float ri2 = ri * ri;
-                float f = ri2 * ri;
-                k.sx[s] = fmaf(dx, f, k.sx[s]);
-                k.sy[s] = fmaf(dy, f, k.sy[s]);
-                k.sz[s] = fmaf(dz, f, k.sz[s]);
+                const f2 dx = add2(px[h], k.nx[s]), dy = add2(py[h], k.ny[s]), dz = add2(pz[h], k.nz[s]);
+                f2 r2 = fma2(dx, dx, tiny);
+                r2 = fma2(dy, dy, r2);
+                r2 = fma2(dz, dz, r2);
+                trk = fminf(trk, fminf(lo(r2), hi(r2)));
+#if NF_FWD_RCP
+                const f2 f = mul2(rcp2(r2), rsqrt2(r2));
+#else
+                const f2 ri = rsqrt2(r2);
+                const f2 f = mul2(mul2(ri, ri), ri);
+#endif
+                k.sx[s] = fma2(dx, f, k.sx[s]);
+                k.sy[s] = fma2(dy, f, k.sy[s]);
+                k.sz[s] = fma2(dz, f, k.sz[s]);
             }
         }
     }
@@ -248,27 +328,31 @@ __device__ __forceinline__ void stage_fwd_fast(const float4* __restrict__ A, int
 
 // Forward, exact path: f = min(poly(r), r^-3) (Eq. (spline) with the min hand-off).
 template <int S>
-__device__ __forceinline__ void stage_fwd_exact(const float4* __restrict__ A, int cnt,
-                                                SinkSet<S>& k, const Coef& cf)
+__device__ __forceinline__ void stage_fwd_exact(const StageView& v, int cnt, SinkSet<S>& k, const Coef& cf)
 {
+    const f2 tiny = pk(kTiny, kTiny);
+    const f2 c0 = pk(cf.c0, cf.c0), c1 = pk(cf.c1, cf.c1), c2 = pk(cf.c2, cf.c2);
 #pragma unroll 1
     for (int q = 0; q < cnt; q += 4) {
+        const float4 xs = v.X[q >> 2], ys = v.Y[q >> 2], zs = v.Z[q >> 2];
+        const f2 px[2] = {pk(xs.x, xs.y), pk(xs.z, xs.w)};
+        const f2 py[2] = {pk(ys.x, ys.y), pk(ys.z, ys.w)};
+        const f2 pz[2] = {pk(zs.x, zs.y), pk(zs.z, zs.w)};
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const float4 sj = A[q + u];
+        for (int h = 0; h < 2; ++h) {
 #pragma unroll
             for (int s = 0; s < S; ++s) {
-                float dx = sj.x - k.x[s], dy = sj.y - k.y[s], dz = sj.z - k.z[s];
-                float r2 = fmaf(dx, dx, kTiny);
-                r2 = fmaf(dy, dy, r2);
-                r2 = fmaf(dz, dz, r2);
-                float ri = rsqrt_approx(r2);
-                float p = fmaf(r2, fmaf(cf.c1, ri, cf.c2), cf.c0);
-                float ri2 = ri * ri;
-                float f = fminf(p, ri2 * ri);
-                k.sx[s] = fmaf(dx, f, k.sx[s]);
-                k.sy[s] = fmaf(dy, f, k.sy[s]);
-                k.sz[s] = fmaf(dz, f, k.sz[s]);
+                const f2 dx = add2(px[h], k.nx[s]), dy = add2(py[h], k.ny[s]), dz = add2(pz[h], k.nz[s]);
+                f2 r2 = fma2(dx, dx, tiny);
+                r2 = fma2(dy, dy, r2);
+                r2 = fma2(dz, dz, r2);
+                const f2 ri = rsqrt2(r2);
+                const f2 p = fma2(r2, fma2(c1, ri, c2), c0);
+                const f2 r3 = mul2(mul2(ri, ri), ri);
+                const f2 f = pk(fminf(lo(p), lo(r3)), fminf(hi(p), hi(r3)));
+                k.sx[s] = fma2(dx, f, k.sx[s]);
+                k.sy[s] = fma2(dy, f, k.sy[s]);
+                k.sz[s] = fma2(dz, f, k.sz[s]);
             }
         }
     }
@@ -276,73 +360,96 @@ __device__ __forceinline__ void stage_fwd_exact(const float4* __restrict__ A, in
 
 // Adjoint, fast path: J v = r^-3 (v - 3 r^-2 (d.v) d), v = g_j - g_i.
 template <int S>
-__device__ __forceinline__ void stage_adj_fast(const float4* __restrict__ A, const float4* __restrict__ Gv,
-                                               int cnt, SinkSet<S>& k, float& trk)
+__device__ __forceinline__ void stage_adj_fast(const StageView& v, int cnt, SinkSet<S>& k, float& trk)
 {
+    const f2 tiny = pk(kTiny, kTiny);
+    const f2 m3 = pk(-3.0f, -3.0f);
 #pragma unroll 1
-    for (int q = 0; q < cnt; q += 2) {
+    for (int q = 0; q < cnt; q += 4) {
+        const float4 xs = v.X[q >> 2], ys = v.Y[q >> 2], zs = v.Z[q >> 2];
+        const float4 gxs = v.GX[q >> 2], gys = v.GY[q >> 2], gzs = v.GZ[q >> 2];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const float4 sj = A[q + u];   // x, y, z
-            const float4 sg = Gv[q + u];  // gx, gy, gz
+        for (int h = 0; h < 2; ++h) {
+            const f2 px = h ? pk(xs.z, xs.w) : pk(xs.x, xs.y);
+            const f2 py = h ? pk(ys.z, ys.w) : pk(ys.x, ys.y);
+            const f2 pz = h ? pk(zs.z, zs.w) : pk(zs.x, zs.y);
+            const f2 qx = h ? pk(gxs.z, gxs.w) : pk(gxs.x, gxs.y);
+            const f2 qy = h ? pk(gys.z, gys.w) : pk(gys.x, gys.y);
+            const f2 qz = h ? pk(gzs.z, gzs.w) : pk(gzs.x, gzs.y);
 #pragma unroll
             for (int s = 0; s < S; ++s) {
-                float dx = sj.x - k.x[s], dy = sj.y - k.y[s], dz = sj.z - k.z[s];
-                float r2 = fmaf(dx, dx, kTiny);
-                r2 = fmaf(dy, dy, r2);
-                r2 = fmaf(dz, dz, r2);
-                trk = fminf(trk, r2);
-                float ri = rsqrt_approx(r2);
-                float ri2 = ri * ri;
-                float ri3 = ri2 * ri;
-                float vx = sg.x - k.gx[s], vy = sg.y - k.gy[s], vz = sg.z - k.gz[s];
-                float dv = dx * vx;
-                dv = fmaf(dy, vy, dv);
-                dv = fmaf(dz, vz, dv);
-                float c = dv * (-3.0f * ri2);
-                float wx = fmaf(c, dx, vx), wy = fmaf(c, dy, vy), wz = fmaf(c, dz, vz);
-                k.sx[s] = fmaf(ri3, wx, k.sx[s]);
-                k.sy[s] = fmaf(ri3, wy, k.sy[s]);
-                k.sz[s] = fmaf(ri3, wz, k.sz[s]);
+                const f2 dx = add2(px, k.nx[s]), dy = add2(py, k.ny[s]), dz = add2(pz, k.nz[s]);
+                f2 r2 = fma2(dx, dx, tiny);
+                r2 = fma2(dy, dy, r2);
+                r2 = fma2(dz, dz, r2);
+                trk = fminf(trk, fminf(lo(r2), hi(r2)));
+#if NF_ADJ_RCP
+                const f2 ri2 = rcp2(r2);
+                const f2 ri3 = mul2(ri2, rsqrt2(r2));
+#else
+                const f2 ri = rsqrt2(r2);
+                const f2 ri2 = mul2(ri, ri);
+                const f2 ri3 = mul2(ri2, ri);
+#endif
+                const f2 vx = add2(qx, k.ngx[s]), vy = add2(qy, k.ngy[s]), vz = add2(qz, k.ngz[s]);
+                f2 dv = mul2(dx, vx);
+                dv = fma2(dy, vy, dv);
+                dv = fma2(dz, vz, dv);
+                const f2 c = mul2(dv, mul2(ri2, m3));
+                k.sx[s] = fma2(ri3, fma2(c, dx, vx), k.sx[s]);
+                k.sy[s] = fma2(ri3, fma2(c, dy, vy), k.sy[s]);
+                k.sz[s] = fma2(ri3, fma2(c, dz, vz), k.sz[s]);
             }
         }
     }
 }
 
-// Adjoint, exact path: J v = F (v + G (d.v) d) with F = f, G = (f'/r) / f,
-// selecting the softened branch of Eq. (spline) for r^2 < eps_s^2.
+// Adjoint, exact path: J v = F (v + G (d.v) d), F = f and G = (f'/r) / f,
+// with the softened branch of Eq. (spline) selected per pair for r^2 < eps_s^2
+// (F = poly/eps_s^3, f'/r = e1 + e0/r; outside F = r^-3, G = -3 r^-2).
 template <int S>
-__device__ __forceinline__ void stage_adj_exact(const float4* __restrict__ A, const float4* __restrict__ Gv,
-                                                int cnt, SinkSet<S>& k, const Coef& cf)
+__device__ __forceinline__ void stage_adj_exact(const StageView& v, int cnt, SinkSet<S>& k, const Coef& cf)
 {
+    const f2 tiny = pk(kTiny, kTiny);
+    const f2 m3 = pk(-3.0f, -3.0f);
+    const f2 c0 = pk(cf.c0, cf.c0), c1 = pk(cf.c1, cf.c1), c2 = pk(cf.c2, cf.c2);
+    const f2 e0 = pk(cf.e0, cf.e0), e1 = pk(cf.e1, cf.e1);
 #pragma unroll 1
-    for (int q = 0; q < cnt; ++q) {
-        const float4 sj = A[q];
-        const float4 sg = Gv[q];
+    for (int q = 0; q < cnt; q += 4) {
+        const float4 xs = v.X[q >> 2], ys = v.Y[q >> 2], zs = v.Z[q >> 2];
+        const float4 gxs = v.GX[q >> 2], gys = v.GY[q >> 2], gzs = v.GZ[q >> 2];
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-            float dx = sj.x - k.x[s], dy = sj.y - k.y[s], dz = sj.z - k.z[s];
-            float r2 = fmaf(dx, dx, kTiny);
-            r2 = fmaf(dy, dy, r2);
-            r2 = fmaf(dz, dz, r2);
-            float ri = rsqrt_approx(r2);
-            float ri2 = ri * ri;
-            float F, G;
-            if (r2 < cf.eps2) {
-                F = fmaf(r2, fmaf(cf.c1, ri, cf.c2), cf.c0);
-                G = fmaf(cf.e0, ri, cf.e1) / F;
-            } else {
-                F = ri2 * ri;
-                G = -3.0f * ri2;
+        for (int h = 0; h < 2; ++h) {
+            const f2 px = h ? pk(xs.z, xs.w) : pk(xs.x, xs.y);
+            const f2 py = h ? pk(ys.z, ys.w) : pk(ys.x, ys.y);
+            const f2 pz = h ? pk(zs.z, zs.w) : pk(zs.x, zs.y);
+            const f2 qx = h ? pk(gxs.z, gxs.w) : pk(gxs.x, gxs.y);
+            const f2 qy = h ? pk(gys.z, gys.w) : pk(gys.x, gys.y);
+            const f2 qz = h ? pk(gzs.z, gzs.w) : pk(gzs.x, gzs.y);
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const f2 dx = add2(px, k.nx[s]), dy = add2(py, k.ny[s]), dz = add2(pz, k.nz[s]);
+                f2 r2 = fma2(dx, dx, tiny);
+                r2 = fma2(dy, dy, r2);
+                r2 = fma2(dz, dz, r2);
+                const f2 ri = rsqrt2(r2);
+                const f2 ri2 = rcp2(r2);
+                const f2 Fs = fma2(r2, fma2(c1, ri, c2), c0);
+                const f2 Gs = mul2(fma2(e0, ri, e1), rcp2(Fs));
+                const f2 Fr = mul2(ri2, ri);
+                const f2 Gr = mul2(ri2, m3);
+                const bool sl = lo(r2) < cf.eps2, sh = hi(r2) < cf.eps2;
+                const f2 F = pk(sl ? lo(Fs) : lo(Fr), sh ? hi(Fs) : hi(Fr));
+                const f2 G = pk(sl ? lo(Gs) : lo(Gr), sh ? hi(Gs) : hi(Gr));
+                const f2 vx = add2(qx, k.ngx[s]), vy = add2(qy, k.ngy[s]), vz = add2(qz, k.ngz[s]);
+                f2 dv = mul2(dx, vx);
+                dv = fma2(dy, vy, dv);
+                dv = fma2(dz, vz, dv);
+                const f2 c = mul2(dv, G);
+                k.sx[s] = fma2(F, fma2(c, dx, vx), k.sx[s]);
+                k.sy[s] = fma2(F, fma2(c, dy, vy), k.sy[s]);
+                k.sz[s] = fma2(F, fma2(c, dz, vz), k.sz[s]);
             }
-            float vx = sg.x - k.gx[s], vy = sg.y - k.gy[s], vz = sg.z - k.gz[s];
-            float dv = dx * vx;
-            dv = fmaf(dy, vy, dv);
-            dv = fmaf(dz, vz, dv);
-            float c = dv * G;
-            k.sx[s] = fmaf(F, fmaf(c, dx, vx), k.sx[s]);
-            k.sy[s] = fmaf(F, fmaf(c, dy, vy), k.sy[s]);
-            k.sz[s] = fmaf(F, fmaf(c, dz, vz), k.sz[s]);
         }
     }
 }
@@ -353,16 +460,20 @@ __device__ __forceinline__ void stage_adj_exact(const float4* __restrict__ A, co
 
 template <int B, bool ADJ>
 struct WarpSmem {
-    // A[2][B] float4 sources, G[2][B] float4 source gradients (adjoint),
-    // SH[2][B] float2 (dy, dz) frame shift of each staged source, then the
-    // segment table: seg_pre[max_nseg + 1], seg_start, seg_dy, seg_dz [max_nseg].
-    static constexpr size_t a_bytes = 2ull * B * sizeof(float4);
-    static constexpr size_t g_bytes = ADJ ? 2ull * B * sizeof(float4) : 0;
+    // raw[2][B] float4 and graw[2][B] float4 (adjoint): cp.async targets;
+    // soa[3 or 6][B] floats: X, Y, Z (and GX, GY, GZ) of the stage being
+    // computed (written by the fix-up pass after the previous stage finished);
+    // sh[2][B] float2: (dy, dz) frame shift of each staged source;
+    // then the segment table: seg_pre[max_nseg + 1], seg_start, seg_dy, seg_dz.
+    static constexpr int NC = ADJ ? 6 : 3;
+    static constexpr size_t raw_bytes = 2ull * B * sizeof(float4);
+    static constexpr size_t graw_bytes = ADJ ? 2ull * B * sizeof(float4) : 0;
+    static constexpr size_t soa_bytes = 1ull * NC * B * sizeof(float);
     static constexpr size_t sh_bytes = 2ull * B * sizeof(float2);
     static size_t __host__ __device__ bytes(int max_nseg)
     {
         size_t t = (size_t)(4 * max_nseg + 1) * 4;
-        return a_bytes + g_bytes + sh_bytes + ((t + 15) & ~size_t(15));
+        return raw_bytes + graw_bytes + soa_bytes + sh_bytes + ((t + 15) & ~size_t(15));
     }
 };
 
@@ -405,13 +516,21 @@ __device__ __forceinline__ void sink_lookup(const ItemCtx& it, int p, int* at, i
     *slot = c_sel;
 }
 
+struct WarpBufs {
+    float4* raw;    // [2][B]
+    float4* graw;   // [2][B] (adjoint)
+    float* soa;     // [NC][B]
+    float2* sh;     // [2][B]
+};
+
 template <int S, int B, bool ADJ>
 __device__ __forceinline__ void run_item(const ItemCtx& it, const Coef& cf,
                                          const float4* __restrict__ rel, const float4* __restrict__ gs,
-                                         float4* bufA, float4* bufG, float2* bufSH, const int* seg_pre,
+                                         const WarpBufs& wb, const int* seg_pre,
                                          const int* seg_start, const float* seg_dy, const float* seg_dz,
                                          float* __restrict__ partial, int Ntot)
 {
+    constexpr int NC = WarpSmem<B, ADJ>::NC;
     const int lane = threadIdx.x & 31;
     SinkSet<S> k;
 #pragma unroll
@@ -421,14 +540,15 @@ __device__ __forceinline__ void run_item(const ItemCtx& it, const Coef& cf,
         sink_lookup(it, p, &at, &slot);
         const bool ok = p < it.n_sink;
         float4 r = ok ? rel[at] : make_float4(kFarSink, kFarSink, kFarSink, 0.0f);
-        k.x[s] = r.x + (float)(slot - it.R);
-        k.y[s] = r.y;
-        k.z[s] = r.z;
+        const float x = r.x + (float)(slot - it.R);
+        k.nx[s] = pk(-x, -x);
+        k.ny[s] = pk(-r.y, -r.y);
+        k.nz[s] = pk(-r.z, -r.z);
         if constexpr (ADJ) {
             float4 g = ok ? gs[at] : make_float4(0.f, 0.f, 0.f, 0.f);
-            k.gx[s] = g.x;
-            k.gy[s] = g.y;
-            k.gz[s] = g.z;
+            k.ngx[s] = pk(-g.x, -g.x);
+            k.ngy[s] = pk(-g.y, -g.y);
+            k.ngz[s] = pk(-g.z, -g.z);
         }
         k.ax[s] = k.ay[s] = k.az[s] = 0.0f;
     }
@@ -448,7 +568,7 @@ __device__ __forceinline__ void run_item(const ItemCtx& it, const Coef& cf,
         }
     };
     // Issue the asynchronous copies of stage st into buffer buf.  Each lane
-    // copies the sources it will later shift into the item's frame.
+    // copies the sources it will later shift and transpose.
     auto issue = [&](int st, int buf) {
         int beg, end;
         stage_range(st, beg, end);
@@ -459,27 +579,35 @@ __device__ __forceinline__ void run_item(const ItemCtx& it, const Coef& cf,
             if (p < end) {
                 while (p >= seg_pre[cur + 1]) ++cur;
                 const int at = seg_start[cur] + (p - seg_pre[cur]);
-                cp_async16(&bufA[slot], &rel[at]);
-                if constexpr (ADJ) cp_async16(&bufG[slot], &gs[at]);
-                bufSH[slot] = make_float2(seg_dy[cur], seg_dz[cur]);
+                cp_async16(&wb.raw[slot], &rel[at]);
+                if constexpr (ADJ) cp_async16(&wb.graw[slot], &gs[at]);
+                wb.sh[slot] = make_float2(seg_dy[cur], seg_dz[cur]);
             } else {
-                bufA[slot] = make_float4(kFarSrc, kFarSrc, kFarSrc, 0.0f);
-                if constexpr (ADJ) bufG[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
-                bufSH[slot] = make_float2(0.0f, 0.0f);
+                wb.raw[slot] = make_float4(kFarSrc, kFarSrc, kFarSrc, 0.0f);
+                if constexpr (ADJ) wb.graw[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+                wb.sh[slot] = make_float2(0.0f, 0.0f);
             }
         }
         cp_async_commit();
     };
-    // Shift this lane's own staged sources into the item's frame.
+    // Shift this lane's own staged sources into the item's frame and write
+    // them to the structure-of-arrays buffers the pair loop reads.
     auto fixup = [&](int buf) {
+        float* soa = wb.soa;
 #pragma unroll
         for (int t = 0; t < PER; ++t) {
-            const int slot = buf * B + t * 32 + lane;
-            float4 v = bufA[slot];
-            const float2 sh = bufSH[slot];
-            v.y += sh.x;
-            v.z += sh.y;
-            bufA[slot] = v;
+            const int i = t * 32 + lane;
+            const float4 v = wb.raw[buf * B + i];
+            const float2 sh = wb.sh[buf * B + i];
+            soa[0 * B + i] = v.x;
+            soa[1 * B + i] = v.y + sh.x;
+            soa[2 * B + i] = v.z + sh.y;
+            if constexpr (ADJ) {
+                const float4 g = wb.graw[buf * B + i];
+                soa[3 * B + i] = g.x;
+                soa[4 * B + i] = g.y;
+                soa[5 * B + i] = g.z;
+            }
         }
     };
 
@@ -497,28 +625,34 @@ __device__ __forceinline__ void run_item(const ItemCtx& it, const Coef& cf,
         int beg, end;
         stage_range(st, beg, end);
         const int cnt = (end - beg + 7) & ~7;
-        const float4* A = bufA + buf * B;
-        const float4* G = bufG + buf * B;
+        const float* soa = wb.soa;
+        StageView v;
+        v.X = reinterpret_cast<const float4*>(soa + 0 * B);
+        v.Y = reinterpret_cast<const float4*>(soa + 1 * B);
+        v.Z = reinterpret_cast<const float4*>(soa + 2 * B);
+        v.GX = reinterpret_cast<const float4*>(soa + (ADJ ? 3 : 0) * B);
+        v.GY = reinterpret_cast<const float4*>(soa + (ADJ ? 4 : 0) * B);
+        v.GZ = reinterpret_cast<const float4*>(soa + (ADJ ? 5 : 0) * B);
         bool exact = st < nst0;
         if (!exact) {
 #pragma unroll
-            for (int s = 0; s < S; ++s) k.sx[s] = k.sy[s] = k.sz[s] = 0.0f;
+            for (int s = 0; s < S; ++s) k.sx[s] = k.sy[s] = k.sz[s] = 0ull;
             float trk = kBig;
-            if constexpr (ADJ) stage_adj_fast<S>(A, G, cnt, k, trk);
-            else stage_fwd_fast<S>(A, cnt, k, trk);
+            if constexpr (ADJ) stage_adj_fast<S>(v, cnt, k, trk);
+            else stage_fwd_fast<S>(v, cnt, k, trk);
             exact = __any_sync(kFull, trk < cf.eps2);
         }
         if (exact) {
 #pragma unroll
-            for (int s = 0; s < S; ++s) k.sx[s] = k.sy[s] = k.sz[s] = 0.0f;
-            if constexpr (ADJ) stage_adj_exact<S>(A, G, cnt, k, cf);
-            else stage_fwd_exact<S>(A, cnt, k, cf);
+            for (int s = 0; s < S; ++s) k.sx[s] = k.sy[s] = k.sz[s] = 0ull;
+            if constexpr (ADJ) stage_adj_exact<S>(v, cnt, k, cf);
+            else stage_fwd_exact<S>(v, cnt, k, cf);
         }
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-            k.ax[s] += k.sx[s];
-            k.ay[s] += k.sy[s];
-            k.az[s] += k.sz[s];
+            k.ax[s] += lo(k.sx[s]) + hi(k.sx[s]);
+            k.ay[s] += lo(k.sy[s]) + hi(k.sy[s]);
+            k.az[s] += lo(k.sz[s]) + hi(k.sz[s]);
         }
         __syncwarp();
     }
@@ -536,8 +670,10 @@ __device__ __forceinline__ void run_item(const ItemCtx& it, const Coef& cf,
     }
 }
 
-template <int SMAX, int B, bool ADJ>
-__global__ void __launch_bounds__(256, 2)
+// MINB = 2 allows 128 registers per thread (16 resident warps per SM);
+// MINB = 3 caps them at 85 so 24 warps fit (the "lean" variant, for S <= 2).
+template <int SMAX, int B, bool ADJ, int MINB>
+__global__ void __launch_bounds__(256, MINB)
 k_force(const BoxDev* __restrict__ boxes, const int* __restrict__ off, const float4* __restrict__ rel,
         const float4* __restrict__ gs, const int4* __restrict__ items, WsHeader* hdr,
         float* __restrict__ partial, int Ntot, int max_nseg)
@@ -546,10 +682,12 @@ k_force(const BoxDev* __restrict__ boxes, const int* __restrict__ off, const flo
     using W = WarpSmem<B, ADJ>;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned char* w = smem + (size_t)wid * W::bytes(max_nseg);
-    float4* bufA = reinterpret_cast<float4*>(w);
-    float4* bufG = reinterpret_cast<float4*>(w + W::a_bytes);
-    float2* bufSH = reinterpret_cast<float2*>(w + W::a_bytes + W::g_bytes);
-    int* seg_pre = reinterpret_cast<int*>(w + W::a_bytes + W::g_bytes + W::sh_bytes);
+    WarpBufs wb;
+    wb.raw = reinterpret_cast<float4*>(w);
+    wb.graw = reinterpret_cast<float4*>(w + W::raw_bytes);
+    wb.soa = reinterpret_cast<float*>(w + W::raw_bytes + W::graw_bytes);
+    wb.sh = reinterpret_cast<float2*>(w + W::raw_bytes + W::graw_bytes + W::soa_bytes);
+    int* seg_pre = reinterpret_cast<int*>(w + W::raw_bytes + W::graw_bytes + W::soa_bytes + W::sh_bytes);
     int* seg_start = seg_pre + max_nseg + 1;
     float* seg_dy = reinterpret_cast<float*>(seg_start + max_nseg);
     float* seg_dz = seg_dy + max_nseg;
@@ -628,14 +766,13 @@ k_force(const BoxDev* __restrict__ boxes, const int* __restrict__ off, const flo
         const int n_chunk = min(CH, it.n_sink - it.chunk_begin);
         const int S = (n_chunk + 31) >> 5;
         if (SMAX >= 4 && S >= 3)
-            run_item<(SMAX >= 4 ? 4 : 1), B, ADJ>(it, cf, rel, gs, bufA, bufG, bufSH, seg_pre, seg_start,
-                                                  seg_dy, seg_dz, partial, Ntot);
+            run_item<(SMAX >= 4 ? 4 : 1), B, ADJ>(it, cf, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz,
+                                                  partial, Ntot);
         else if (SMAX >= 2 && S == 2)
-            run_item<(SMAX >= 2 ? 2 : 1), B, ADJ>(it, cf, rel, gs, bufA, bufG, bufSH, seg_pre, seg_start,
-                                                  seg_dy, seg_dz, partial, Ntot);
+            run_item<(SMAX >= 2 ? 2 : 1), B, ADJ>(it, cf, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz,
+                                                  partial, Ntot);
         else
-            run_item<1, B, ADJ>(it, cf, rel, gs, bufA, bufG, bufSH, seg_pre, seg_start, seg_dy, seg_dz,
-                                partial, Ntot);
+            run_item<1, B, ADJ>(it, cf, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz, partial, Ntot);
         __syncwarp();
     }
 }
@@ -717,17 +854,32 @@ int grid_for(size_t n, int threads)
 typedef void (*ForceKernel)(const BoxDev*, const int*, const float4*, const float4*, const int4*,
                             WsHeader*, float*, int, int);
 
+// The lean (85-register) variant is used when the tuning asks for 24 or more
+// resident warps per SM.
+bool wants_lean(const ForceTuning& t) { return t.sinks_per_lane <= 2 && t.warps_per_block * t.blocks_per_sm >= 24; }
+
 template <bool ADJ>
-ForceKernel pick_kernel(int smax, int stage)
+ForceKernel pick_kernel(const ForceTuning& t)
 {
+    const int smax = t.sinks_per_lane, stage = t.stage;
+    if (wants_lean(t)) {
+        if (stage == 128) {
+            if (smax == 2) return k_force<2, 128, ADJ, 3>;
+            if (smax == 1) return k_force<1, 128, ADJ, 3>;
+        } else if (stage == 64) {
+            if (smax == 2) return k_force<2, 64, ADJ, 3>;
+            if (smax == 1) return k_force<1, 64, ADJ, 3>;
+        }
+        return nullptr;
+    }
     if (stage == 128) {
-        if (smax == 4) return k_force<4, 128, ADJ>;
-        if (smax == 2) return k_force<2, 128, ADJ>;
-        if (smax == 1) return k_force<1, 128, ADJ>;
+        if (smax == 4) return k_force<4, 128, ADJ, 2>;
+        if (smax == 2) return k_force<2, 128, ADJ, 2>;
+        if (smax == 1) return k_force<1, 128, ADJ, 2>;
     } else if (stage == 64) {
-        if (smax == 4) return k_force<4, 64, ADJ>;
-        if (smax == 2) return k_force<2, 64, ADJ>;
-        if (smax == 1) return k_force<1, 64, ADJ>;
+        if (smax == 4) return k_force<4, 64, ADJ, 2>;
+        if (smax == 2) return k_force<2, 64, ADJ, 2>;
+        if (smax == 1) return k_force<1, 64, ADJ, 2>;
     }
     return nullptr;
 }
@@ -752,8 +904,7 @@ bool force_tuning_supported(const ForceTuning& t)
 
 int force_blocks_per_sm(bool adjoint, const ForceTuning& t, int max_nseg)
 {
-    ForceKernel kfn = adjoint ? pick_kernel<true>(t.sinks_per_lane, t.stage)
-                              : pick_kernel<false>(t.sinks_per_lane, t.stage);
+    ForceKernel kfn = adjoint ? pick_kernel<true>(t) : pick_kernel<false>(t);
     if (!kfn) return 0;
     size_t smem = force_smem_bytes(adjoint, t, max_nseg);
     if (ensure_smem((const void*)kfn, (int)smem) != cudaSuccess) return 0;
@@ -800,8 +951,7 @@ cudaError_t launch_force(bool adjoint, const ForceTuning& t, const BoxDev* boxes
                          const float4* rel, const float4* gs, const int4* items, WsHeader* hdr,
                          float* partial, int Ntot, int max_nseg, cudaStream_t s)
 {
-    ForceKernel kfn = adjoint ? pick_kernel<true>(t.sinks_per_lane, t.stage)
-                              : pick_kernel<false>(t.sinks_per_lane, t.stage);
+    ForceKernel kfn = adjoint ? pick_kernel<true>(t) : pick_kernel<false>(t);
     if (!kfn) return cudaErrorInvalidValue;
     size_t smem = force_smem_bytes(adjoint, t, max_nseg);
     cudaError_t e = ensure_smem((const void*)kfn, (int)smem);
