@@ -53,9 +53,15 @@ __device__ __forceinline__ int cell_coord(float x, double kl, int K, float* off,
     double c = floor(t);
     double frac = __dsub_rn(t, c);
     double o = __dsub_rn(frac, 0.5);
+    *off = __double2float_rn(o);
+    // c mod K into [0, K): c is an exact integer, so integer arithmetic gives
+    // the same value as an FP64 remainder (and avoids the slow FP64 one)
+    if (fabs(c) < 2147483647.0) {
+        int cm = (int)c % K;
+        return cm < 0 ? cm + K : cm;
+    }
     double cm = fmod(c, (double)K);
     if (cm < 0.0) cm = __dadd_rn(cm, (double)K);
-    *off = __double2float_rn(o);
     return (int)cm;
 }
 
@@ -196,20 +202,19 @@ __global__ void k_scan_apply(unsigned* __restrict__ d, size_t n, const unsigned*
 // ---------------------------------------------------------------------------
 
 constexpr int kRxWarps = 8;
-constexpr int kRxRounds = 64;
-constexpr int kRxSub = 32 * kRxRounds;       // elements per warp, in order
-constexpr int kRxTile = kRxWarps * kRxSub;   // elements per block
+constexpr int kRxMaxRounds = 64;            // rounds of 32 elements per warp (upper bound)
 constexpr int kRxMaxBits = 11;
 
 __global__ void __launch_bounds__(kRxWarps * 32)
-k_radix_up(const int* __restrict__ keys, int N, int shift, int mask, int bins, int tiles,
+k_radix_up(const int* __restrict__ keys, int N, int shift, int mask, int bins, int tiles, int rounds,
            unsigned* __restrict__ H)
 {
     extern __shared__ unsigned hist[];
     for (int b = threadIdx.x; b < bins; b += blockDim.x) hist[b] = 0;
     __syncthreads();
-    size_t base = (size_t)blockIdx.x * kRxTile;
-    for (int i = threadIdx.x; i < kRxTile; i += blockDim.x) {
+    const int tile = kRxWarps * 32 * rounds;
+    size_t base = (size_t)blockIdx.x * tile;
+    for (int i = threadIdx.x; i < tile; i += blockDim.x) {
         size_t e = base + i;
         if (e < (size_t)N) atomicAdd(&hist[(keys[e] >> shift) & mask], 1u);
     }
@@ -222,18 +227,18 @@ k_radix_up(const int* __restrict__ keys, int N, int shift, int mask, int bins, i
 // keys_out == nullptr skips the key write (last pass).
 __global__ void __launch_bounds__(kRxWarps * 32)
 k_radix_down(const int* __restrict__ keys_in, const int* __restrict__ vals_in, int N, int shift,
-             int mask, int bins, int tiles, const unsigned* __restrict__ H,
+             int mask, int bins, int tiles, int rounds, const unsigned* __restrict__ H,
              int* __restrict__ keys_out, int* __restrict__ vals_out)
 {
     extern __shared__ unsigned cnt[];  // [kRxWarps][bins]
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kRxWarps * bins; i += blockDim.x) cnt[i] = 0;
     __syncthreads();
-    const size_t sub = (size_t)blockIdx.x * kRxTile + (size_t)w * kRxSub;
+    const size_t sub = (size_t)blockIdx.x * (kRxWarps * 32 * rounds) + (size_t)w * (32 * rounds);
     unsigned* my = cnt + w * bins;
     const unsigned lt = (1u << lane) - 1u;
     // counts of this warp's sub-tile
-    for (int r = 0; r < kRxRounds; ++r) {
+    for (int r = 0; r < rounds; ++r) {
         size_t e0 = sub + (size_t)r * 32;
         if (e0 >= (size_t)N) break;
         size_t e = e0 + lane;
@@ -254,7 +259,7 @@ k_radix_down(const int* __restrict__ keys_in, const int* __restrict__ vals_in, i
         }
     }
     __syncthreads();
-    for (int r = 0; r < kRxRounds; ++r) {
+    for (int r = 0; r < rounds; ++r) {
         size_t e0 = sub + (size_t)r * 32;
         if (e0 >= (size_t)N) break;
         size_t e = e0 + lane;
@@ -324,7 +329,12 @@ RadixPlan radix_plan(int64_t N, int64_t C)
     p.passes = (bits + kRxMaxBits - 1) / kRxMaxBits;
     p.digit_bits = (bits + p.passes - 1) / p.passes;
     p.bins = 1 << p.digit_bits;
-    p.tiles = (int)((N + kRxTile - 1) / kRxTile);
+    // Enough tiles to fill every SM several times over (the rounds of a warp
+    // run one after another), but no more than the (bin, tile) matrix needs.
+    p.rounds = kRxMaxRounds;
+    while (p.rounds > 4 && (N + kRxWarps * 32 * p.rounds - 1) / (kRxWarps * 32 * p.rounds) < 1024) p.rounds >>= 1;
+    const int64_t tile = (int64_t)kRxWarps * 32 * p.rounds;
+    p.tiles = (int)((N + tile - 1) / tile);
     if (p.tiles < 1) p.tiles = 1;
     return p;
 }
@@ -351,12 +361,12 @@ cudaError_t radix_sort(const RadixPlan& p, int N, int* keys_a, int* keys_b, int*
         const bool last = pass == p.passes - 1;
         int* kout = last ? nullptr : kbuf[pass & 1];
         int* vout = last ? perm : vbuf[pass & 1];
-        k_radix_up<<<p.tiles, kRxWarps * 32, smem_up, s>>>(kin, N, shift, mask, p.bins, p.tiles, hist);
+        k_radix_up<<<p.tiles, kRxWarps * 32, smem_up, s>>>(kin, N, shift, mask, p.bins, p.tiles, p.rounds, hist);
         count_launches(1);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         if ((err = launch_scan(hist, radix_hist_words(p), aux, s)) != cudaSuccess) return err;
         k_radix_down<<<p.tiles, kRxWarps * 32, smem_down, s>>>(kin, vin, N, shift, mask, p.bins,
-                                                               p.tiles, hist, kout, vout);
+                                                               p.tiles, p.rounds, hist, kout, vout);
         count_launches(1);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         kin = kout;

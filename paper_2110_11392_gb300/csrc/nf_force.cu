@@ -781,6 +781,14 @@ k_force(const BoxDev* __restrict__ boxes, const int* __restrict__ off, const flo
 // Combine: sum the 2R+1 partials in FP64, scale, scatter to input order
 // ---------------------------------------------------------------------------
 
+// Error-free sum of two floats: s + e == a + b exactly (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
 __global__ void __launch_bounds__(256)
 k_combine(const BoxDev* __restrict__ boxes, int nboxes, const float* __restrict__ partial,
           const int* __restrict__ perm, int Ntot, float* __restrict__ out,
@@ -798,6 +806,9 @@ k_combine(const BoxDev* __restrict__ boxes, int nboxes, const float* __restrict_
     const BoxDev& B = boxes[lo];
     const int nslot = 2 * B.R + 1;
     const double scale = adjoint ? B.scale_grad : B.scale_acc;
+    // the scale as an unevaluated float pair: scale = s_hi + s_lo to ~2^-48
+    const float s_hi = (float)scale;
+    const float s_lo = (float)(scale - (double)s_hi);
     const double m = 1.0 / (double)B.N;
     const int s0 = B.part_base + (chunk - B.chunk_base) * kCombineChunk;
     const int s1 = min(s0 + kCombineChunk, B.part_base + B.N);
@@ -806,11 +817,20 @@ k_combine(const BoxDev* __restrict__ boxes, int nboxes, const float* __restrict_
         const int e = perm[s];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            double v = 0.0;
-            for (int q = 0; q < nslot; ++q) v += (double)partial[((size_t)q * 3 + c) * (size_t)Ntot + s];
-            float a = (float)(v * scale);
+            // the 2R+1 pencil partials, summed without rounding error into (sh, sl)
+            float sh = partial[((size_t)c) * (size_t)Ntot + s], sl = 0.0f;
+            for (int q = 1; q < nslot; ++q) {
+                float t, err;
+                two_sum(sh, partial[((size_t)q * 3 + c) * (size_t)Ntot + s], t, err);
+                sh = t;
+                sl = __fadd_rn(sl, err);
+            }
+            // (sh + sl) * (s_hi + s_lo), rounded once at the end
+            const float p = __fmul_rn(sh, s_hi);
+            const float perr = __fmaf_rn(sh, s_hi, -p);
+            const float a = __fadd_rn(p, __fmaf_rn(sh, s_lo, __fmaf_rn(sl, s_hi, perr)));
             out[3 * (size_t)e + c] = a;
-            net[c] += m * (double)a;
+            if (chunk_sums) net[c] += m * (double)a;
         }
     }
     if (chunk_sums) {

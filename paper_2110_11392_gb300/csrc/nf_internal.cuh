@@ -79,6 +79,7 @@ struct RadixPlan {
     int digit_bits;
     int bins;
     int tiles;
+    int rounds;  // rounds of 32 elements per warp in one tile (8 warps per tile)
 };
 RadixPlan radix_plan(int64_t N, int64_t C);
 size_t radix_hist_words(const RadixPlan& p);
