@@ -169,23 +169,26 @@ def oracle_sample(w, g, seconds: float, seed: int = 22):
     rng = np.random.default_rng(seed)
     order = rng.permutation(w.N)
     g64 = g.astype(np.float64)
-    # calibrate on a small sample
-    n0 = min(w.N, 256)
-    t0 = time.perf_counter()
-    oracle.forces(w.pos, w.box, w.K, w.R, w.eps, sinks=np.sort(order[:n0]))
-    oracle.adjoint(w.pos, g64, w.box, w.K, w.R, w.eps, sinks=np.sort(order[:n0]))
-    dt0 = time.perf_counter() - t0
-    pairs0 = 2 * int(S[cid[order[:n0]]].sum())
-    rate0 = pairs0 / max(dt0, 1e-6)
-    # per-call set-up (binning of all N) is part of the oracle's time as it stands
-    n = int(min(w.N, max(n0, n0 * seconds / max(dt0, 1e-3) * 0.8)))
+
+    def run(n):
+        sk = np.sort(order[:n])
+        t0 = time.perf_counter()
+        oracle.forces(w.pos, w.box, w.K, w.R, w.eps, sinks=sk)
+        oracle.adjoint(w.pos, g64, w.box, w.K, w.R, w.eps, sinks=sk)
+        return time.perf_counter() - t0
+
+    # calibrate t(n) = a + b n on two small samples (a: the oracle's own binning per call)
+    n0, n1 = min(w.N, 128), min(w.N, 1024)
+    t0, t1 = run(n0), run(n1)
+    b = max((t1 - t0) / max(n1 - n0, 1), 1e-9)
+    a = max(t0 - b * n0, 0.0)
+    n = int(min(w.N, max(n1, (seconds - a) / b)))
     sinks = np.sort(order[:n])
     t0 = time.perf_counter()
     acc_ref = oracle.forces(w.pos, w.box, w.K, w.R, w.eps, sinks=sinks)
     oracle.adjoint(w.pos, g64, w.box, w.K, w.R, w.eps, sinks=sinks)
     dt = time.perf_counter() - t0
     pairs = 2 * int(S[cid[sinks]].sum())
-    del rate0
     return ({"value": pairs / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
              "sample": f"forces + adjoint for {n} random sinks (seed {seed}) of {w.N}; "
                        f"{pairs:.3e} pair interactions in {dt:.1f} s, FP64, OpenMP"},

@@ -224,6 +224,15 @@ typedef unsigned long long f2;
 #ifndef NF_ADJ_RCP
 #define NF_ADJ_RCP 1
 #endif
+// Unroll depth of the fast pair loops over groups of four sources.
+#ifndef NF_FWD_UNROLL
+#define NF_FWD_UNROLL 1
+#endif
+#ifndef NF_ADJ_UNROLL
+#define NF_ADJ_UNROLL 1
+#endif
+constexpr int kFwdUnroll = NF_FWD_UNROLL;
+constexpr int kAdjUnroll = NF_ADJ_UNROLL;
 
 __device__ __forceinline__ f2 pk(float lo, float hi)
 {
@@ -297,7 +306,7 @@ template <int S>
 __device__ __forceinline__ void stage_fwd_fast(const StageView& v, int cnt, SinkSet<S>& k, float& trk)
 {
     const f2 tiny = pk(kTiny, kTiny);
-#pragma unroll 1
+#pragma unroll kFwdUnroll
     for (int q = 0; q < cnt; q += 4) {
         const float4 xs = v.X[q >> 2], ys = v.Y[q >> 2], zs = v.Z[q >> 2];
         const f2 px[2] = {pk(xs.x, xs.y), pk(xs.z, xs.w)};
@@ -364,7 +373,7 @@ __device__ __forceinline__ void stage_adj_fast(const StageView& v, int cnt, Sink
 {
     const f2 tiny = pk(kTiny, kTiny);
     const f2 m3 = pk(-3.0f, -3.0f);
-#pragma unroll 1
+#pragma unroll kAdjUnroll
     for (int q = 0; q < cnt; q += 4) {
         const float4 xs = v.X[q >> 2], ys = v.Y[q >> 2], zs = v.Z[q >> 2];
         const float4 gxs = v.GX[q >> 2], gys = v.GY[q >> 2], gzs = v.GZ[q >> 2];
