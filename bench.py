@@ -100,6 +100,29 @@ def stencil_sums(counts: np.ndarray, R: int) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
+# ranks (one box per GPU; the only collectives are timing and the barrier)
+# ---------------------------------------------------------------------------
+
+def aggregate_over_ranks(pairs_local: float, t_local: float, device) -> tuple:
+    """Whole-job throughput: pair interactions summed over ranks / the slowest
+    rank's time.  Returns (value, t_max, pairs_total)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return pairs_local / t_local, t_local, pairs_local
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    p = torch.tensor([pairs_local], dtype=torch.float64, device=device)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(p.item()) / float(t.item()), float(t.item()), float(p.item())
+
+
+def shard_boxes(boxes, rank: int, world: int):
+    """Round-robin share of independent boxes for one rank (no communication)."""
+    return [b for i, b in enumerate(boxes) if i % world == rank]
+
+
+# ---------------------------------------------------------------------------
 # clocks
 # ---------------------------------------------------------------------------
 
@@ -264,16 +287,7 @@ def run_native(args, rank, world, local):
     _lib.nf_profile_enable(False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_total = sum(step_ms) / 1e3
-    t_max = t_total
-    pairs_all = 2 * P * args.steps
-    if world > 1:
-        t = torch.tensor([t_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        pp = torch.tensor([pairs_all], dtype=torch.float64, device=dev)
-        dist.all_reduce(pp, op=dist.ReduceOp.SUM)
-        pairs_all = float(pp.item())
-    value = pairs_all / t_max
+    value, t_max, pairs_all = aggregate_over_ranks(2 * P * args.steps, t_total, dev)
 
     fwd_pair_ms = float(np.mean([p["pair_ms"] for p in prof_fwd]))
     adj_pair_ms = float(np.mean([p["pair_ms"] for p in prof_adj]))
@@ -326,8 +340,8 @@ def run_native(args, rank, world, local):
 
     if not args.no_e2e:
         out["e2e"] = measure_e2e(args, w, g_np, dev, P, flush)
-    if not args.no_batched and rank == 0:
-        out["batched"] = measure_batched(dev, flush)
+    if not args.no_batched:
+        out["batched"] = measure_batched(dev, flush, rank, world)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         cb, sinks, ref = oracle_sample(w, g_np, args.cpu_seconds)
         out["cpu_baseline"] = cb
@@ -382,13 +396,24 @@ def measure_e2e(args, w, g_np, dev, P, flush):
             "note": "pinned host pos and g in, acc and grad out, per step"}
 
 
-def measure_batched(dev, flush):
-    """64 boxes (batched recipe): one captured graph of nf_forces_batched vs 64 nf_forces calls."""
+def measure_batched(dev, flush, rank=0, world=1):
+    """64 boxes (batched recipe): one captured graph of nf_forces_batched vs one
+    nf_forces call per box.  With several ranks the boxes are shared round-robin
+    and the rates are summed (slowest rank's time)."""
     import torch
     import paper_2110_11392_gb300 as nf
     from paper_2110_11392_gb300 import _lib
     import workloads as W
     w = W.config_batched()
+    rows, off = [], 0
+    for b in w.boxes:
+        rows.append((off, b))
+        off += b["N"]
+    mine = shard_boxes(rows, rank, world)
+    boxes = [b for _, b in mine]
+    pos_np = np.concatenate([w.pos[o:o + b["N"]] for o, b in mine])
+    w.boxes = boxes
+    w.pos = pos_np
     run = nf.BatchedNearField(w.boxes, device=dev)
     run.pos.copy_(torch.from_numpy(w.pos).to(dev))
     run()
@@ -424,8 +449,10 @@ def measure_batched(dev, flush):
 
     separate()
     t_sep = timed(separate)
-    return {"pairs_per_s": P / t_graph, "separate_pairs_per_s": P / t_sep, "speedup": t_sep / t_graph,
-            "boxes": len(w.boxes), "N_total": w.N, "pairs": P, "graph_ms": t_graph * 1e3,
+    rate_g, t_graph, P_all = aggregate_over_ranks(float(P), t_graph, dev)
+    rate_s, t_sep, _ = aggregate_over_ranks(float(P), t_sep, dev)
+    return {"pairs_per_s": rate_g, "separate_pairs_per_s": rate_s, "speedup": t_sep / t_graph,
+            "boxes": 64, "boxes_per_rank": len(w.boxes), "pairs": P_all, "graph_ms": t_graph * 1e3,
             "separate_ms": t_sep * 1e3}
 
 

@@ -115,6 +115,21 @@ int make_box(const nf_box& in, bool need_force, BoxDev* out)
     b.R = in.R;
     b.N = (int)in.N;
     b.kl = (double)in.K / in.box;
+    {
+        // short dyadic form of kl: then x * kl is exact in FP64 for any FP32 x
+        int e = 0;
+        double f = std::frexp(b.kl, &e);                 // kl = f * 2^e, f in [0.5, 1)
+        long long m = (long long)std::ldexp(f, 53);      // exact 53-bit integer
+        int ex = e - 53;
+        while (m > 0 && (m & 1) == 0) {
+            m >>= 1;
+            ++ex;
+        }
+        if (m > 0 && m < (1LL << 29)) {
+            b.kl_mant = (int)m;
+            b.kl_exp = ex;
+        }
+    }
     const double w = in.box / in.K;
     b.scale_acc = 1.0 / ((double)in.N * w * w);
     b.scale_grad = 1.0 / ((double)in.N * w * w * w);

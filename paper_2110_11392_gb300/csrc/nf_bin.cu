@@ -39,9 +39,10 @@ __device__ __forceinline__ int find_box(const BoxDev* boxes, int nboxes, int e)
     return lo;
 }
 
-// One coordinate into cell units: returns the wrapped cell index, writes the
-// FP32 offset from the cell centre; flags non-finite input.
-__device__ __forceinline__ int cell_coord(float x, double kl, int K, float* off, bool* bad)
+// One coordinate into cell units, in FP64 as defined: t = x * kl, c = floor(t),
+// offset = fp32((t - c) - 1/2), cell = c mod K.  Returns the cell, writes the
+// offset; flags non-finite input.
+__device__ __forceinline__ int cell_coord_fp64(float x, double kl, int K, float* off, bool* bad)
 {
     double xd = (double)x;
     if (!isfinite(xd)) {
@@ -65,6 +66,41 @@ __device__ __forceinline__ int cell_coord(float x, double kl, int K, float* off,
     return (int)cm;
 }
 
+// The same function in integer arithmetic, used when kl = kl_mant * 2^kl_exp
+// with a short odd mantissa (the unit box: kl = K).  Then t = x * kl, floor(t),
+// t - c and (t - c) - 1/2 are all exact in FP64 for 2^-29 <= |x| < 2^30, so the
+// FP64 definition reduces to one rounding of an exact value, which this path
+// computes with 64-bit integers (the GPU's FP64 pipe is slow).  Other inputs
+// take the FP64 path; both give identical results.
+__device__ __forceinline__ int cell_coord(float x, const BoxDev& B, float* off, bool* bad)
+{
+    const unsigned bits = __float_as_uint(x);
+    const int E = (int)((bits >> 23) & 0xFF);
+    if (B.kl_mant > 0 && E >= 127 - 29 && E < 127 + 30) {
+        const long long P = (long long)((bits & 0x7FFFFFu) | 0x800000u) * (long long)B.kl_mant;
+        const int s = 150 - E - B.kl_exp;  // t = +-P * 2^-s
+        if (s >= 1 && s <= 53) {
+            const long long one = 1LL << s;
+            const long long low = P & (one - 1);
+            long long c;
+            long long frac;  // (t - c) * 2^s, in [0, 2^s)
+            if ((int)(bits >> 31) == 0) {
+                c = P >> s;
+                frac = low;
+            } else {
+                c = -(P >> s) - (low != 0);
+                frac = low ? one - low : 0;
+            }
+            const long long o = frac - (one >> 1);
+            // exact scaling of the rounded integer by 2^-s
+            *off = __ll2float_rn(o) * __int_as_float((127 - s) << 23);
+            long long cm = c % B.K;
+            return (int)(cm < 0 ? cm + B.K : cm);
+        }
+    }
+    return cell_coord_fp64(x, B.kl, B.K, off, bad);
+}
+
 __global__ void k_fill_boxes(BoxFill f, BoxDev* boxes)
 {
     int i = threadIdx.x;
@@ -79,9 +115,9 @@ __global__ void k_shift(const float* __restrict__ pos, int Ntot, const BoxDev* _
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Ntot; e += gridDim.x * blockDim.x) {
         const BoxDev& B = boxes[find_box(boxes, nboxes, e)];
         float o;
-        int cx = cell_coord(pos[3 * (size_t)e + 0], B.kl, B.K, &o, &bad);
-        int cy = cell_coord(pos[3 * (size_t)e + 1], B.kl, B.K, &o, &bad);
-        int cz = cell_coord(pos[3 * (size_t)e + 2], B.kl, B.K, &o, &bad);
+        int cx = cell_coord(pos[3 * (size_t)e + 0], B, &o, &bad);
+        int cy = cell_coord(pos[3 * (size_t)e + 1], B, &o, &bad);
+        int cz = cell_coord(pos[3 * (size_t)e + 2], B, &o, &bad);
         int key = B.cell_base + (cx * B.K + cy) * B.K + cz;
         keys[e] = key;
         atomicAdd(&counts[key], 1);
@@ -97,9 +133,9 @@ __global__ void k_rel(const float* __restrict__ pos, int Ntot, const BoxDev* __r
         const BoxDev& B = boxes[find_box(boxes, nboxes, e)];
         bool bad = false;
         float4 r;
-        cell_coord(pos[3 * (size_t)e + 0], B.kl, B.K, &r.x, &bad);
-        cell_coord(pos[3 * (size_t)e + 1], B.kl, B.K, &r.y, &bad);
-        cell_coord(pos[3 * (size_t)e + 2], B.kl, B.K, &r.z, &bad);
+        cell_coord(pos[3 * (size_t)e + 0], B, &r.x, &bad);
+        cell_coord(pos[3 * (size_t)e + 1], B, &r.y, &bad);
+        cell_coord(pos[3 * (size_t)e + 2], B, &r.z, &bad);
         r.w = __int_as_float(e);
         rel[s] = r;
     }
@@ -214,6 +250,7 @@ k_radix_up(const int* __restrict__ keys, int N, int shift, int mask, int bins, i
     __syncthreads();
     const int tile = kRxWarps * 32 * rounds;
     size_t base = (size_t)blockIdx.x * tile;
+#pragma unroll 4
     for (int i = threadIdx.x; i < tile; i += blockDim.x) {
         size_t e = base + i;
         if (e < (size_t)N) atomicAdd(&hist[(keys[e] >> shift) & mask], 1u);
@@ -237,16 +274,25 @@ k_radix_down(const int* __restrict__ keys_in, const int* __restrict__ vals_in, i
     const size_t sub = (size_t)blockIdx.x * (kRxWarps * 32 * rounds) + (size_t)w * (32 * rounds);
     unsigned* my = cnt + w * bins;
     const unsigned lt = (1u << lane) - 1u;
-    // counts of this warp's sub-tile
-    for (int r = 0; r < rounds; ++r) {
-        size_t e0 = sub + (size_t)r * 32;
-        if (e0 >= (size_t)N) break;
-        size_t e = e0 + lane;
-        bool valid = e < (size_t)N;
-        int d = valid ? ((keys_in[e] >> shift) & mask) : bins;
-        unsigned peers = __match_any_sync(kFull, d);
-        if (valid && lane == __ffs(peers) - 1) my[d] += __popc(peers);
-        __syncwarp();
+    // counts of this warp's sub-tile; keys are loaded four rounds at a time so
+    // the loads overlap (rounds is a multiple of 4)
+    constexpr int G = 4;
+    for (int r0 = 0; r0 < rounds; r0 += G) {
+        if (sub + (size_t)r0 * 32 >= (size_t)N) break;
+        int kv[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const size_t e = sub + (size_t)(r0 + g) * 32 + lane;
+            kv[g] = e < (size_t)N ? keys_in[e] : -1;
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const bool valid = kv[g] >= 0;
+            const int d = valid ? ((kv[g] >> shift) & mask) : bins;
+            const unsigned peers = __match_any_sync(kFull, d);
+            if (valid && lane == __ffs(peers) - 1) my[d] += __popc(peers);
+            __syncwarp();
+        }
     }
     __syncthreads();
     // global offsets: bins of earlier tiles and earlier warps of this tile
@@ -259,23 +305,30 @@ k_radix_down(const int* __restrict__ keys_in, const int* __restrict__ vals_in, i
         }
     }
     __syncthreads();
-    for (int r = 0; r < rounds; ++r) {
-        size_t e0 = sub + (size_t)r * 32;
-        if (e0 >= (size_t)N) break;
-        size_t e = e0 + lane;
-        bool valid = e < (size_t)N;
-        int key = valid ? keys_in[e] : 0;
-        int val = valid ? (vals_in ? vals_in[e] : (int)e) : 0;
-        int d = valid ? ((key >> shift) & mask) : bins;
-        unsigned peers = __match_any_sync(kFull, d);
-        unsigned base = valid ? my[d] : 0u;
-        __syncwarp();
-        if (valid && lane == __ffs(peers) - 1) my[d] = base + __popc(peers);
-        __syncwarp();
-        if (valid) {
-            unsigned p = base + __popc(peers & lt);
-            if (keys_out) keys_out[p] = key;
-            vals_out[p] = val;
+    for (int r0 = 0; r0 < rounds; r0 += G) {
+        if (sub + (size_t)r0 * 32 >= (size_t)N) break;
+        int kv[G], vv[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const size_t e = sub + (size_t)(r0 + g) * 32 + lane;
+            const bool valid = e < (size_t)N;
+            kv[g] = valid ? keys_in[e] : -1;
+            vv[g] = valid ? (vals_in ? vals_in[e] : (int)e) : 0;
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const bool valid = kv[g] >= 0;
+            const int d = valid ? ((kv[g] >> shift) & mask) : bins;
+            const unsigned peers = __match_any_sync(kFull, d);
+            const unsigned base = valid ? my[d] : 0u;
+            __syncwarp();
+            if (valid && lane == __ffs(peers) - 1) my[d] = base + __popc(peers);
+            __syncwarp();
+            if (valid) {
+                const unsigned p = base + __popc(peers & lt);
+                if (keys_out) keys_out[p] = kv[g];
+                vals_out[p] = vv[g];
+            }
         }
     }
 }

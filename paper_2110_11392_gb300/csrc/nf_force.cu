@@ -822,17 +822,28 @@ k_combine(const BoxDev* __restrict__ boxes, int nboxes, const float* __restrict_
     const int s0 = B.part_base + (chunk - B.chunk_base) * kCombineChunk;
     const int s1 = min(s0 + kCombineChunk, B.part_base + B.N);
     double net[3] = {0.0, 0.0, 0.0};
+    constexpr int kMaxSlots = 2 * NF_MAX_R + 1;
     for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
         const int e = perm[s];
+        // issue every partial load first (they are independent), then sum
+        float v[3][kMaxSlots];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int q = 0; q < kMaxSlots; ++q)
+                v[c][q] = q < nslot ? partial[((size_t)q * 3 + c) * (size_t)Ntot + s] : 0.0f;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             // the 2R+1 pencil partials, summed without rounding error into (sh, sl)
-            float sh = partial[((size_t)c) * (size_t)Ntot + s], sl = 0.0f;
-            for (int q = 1; q < nslot; ++q) {
-                float t, err;
-                two_sum(sh, partial[((size_t)q * 3 + c) * (size_t)Ntot + s], t, err);
-                sh = t;
-                sl = __fadd_rn(sl, err);
+            float sh = v[c][0], sl = 0.0f;
+#pragma unroll
+            for (int q = 1; q < kMaxSlots; ++q) {
+                if (q < nslot) {
+                    float t, err;
+                    two_sum(sh, v[c][q], t, err);
+                    sh = t;
+                    sl = __fadd_rn(sl, err);
+                }
             }
             // (sh + sl) * (s_hi + s_lo), rounded once at the end
             const float p = __fmul_rn(sh, s_hi);

@@ -35,7 +35,9 @@ struct BoxDev {
     float eps2;      // eps_s^2 (cell units^2)
     // f'(r)/r inside the softening: e1 + e0 / r
     float e0, e1;
-    float pad0, pad1;
+    // K / box = kl_mant * 2^kl_exp with an odd kl_mant < 2^29, or kl_mant = 0
+    // when no such short form exists (then the shift stays in FP64)
+    int kl_mant, kl_exp;
 };
 static_assert(sizeof(BoxDev) % 16 == 0, "BoxDev must stay 16-byte aligned");
 

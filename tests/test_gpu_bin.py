@@ -37,6 +37,9 @@ def test_bin_configs_bit_exact(name):
     (70001, 11, 1.0, 3),      # ragged tiles
     (300000, 24, 2.5, 4),     # two passes
     (1 << 20, 128, 1.0, 5),   # 21-bit keys: two 11-bit passes, many tiles
+    (200000, 24, 2.0, 6),     # K / box = 12: dyadic, integer shift path
+    (200000, 10, 0.625, 7),   # K / box = 16
+    (200000, 13, 1.3, 8),     # K / box = 10 (box not dyadic): FP64 shift path
 ])
 def test_bin_uniform_sizes(N, K, box, seed):
     _assert_bit_exact(uniform_positions(N, seed, box), box, K)
@@ -50,8 +53,10 @@ def test_bin_adversarial_positions():
     edge = np.full((500, 3), one_minus, np.float32)
     dup = np.repeat(rng.random((10, 3)).astype(np.float32), 50, axis=0)        # duplicates keep order
     outside = (rng.random((500, 3)) * 5 - 2).astype(np.float32)               # wrapped periodically
+    negative = -(rng.random((500, 3)) * np.float32(1e-3)).astype(np.float32)  # just below 0
+    huge = (rng.random((50, 3)) * 4e9 - 2e9).astype(np.float32)               # |x| >= 2^30: FP64 path
     tiny = (rng.random((500, 3)) * 1e-30).astype(np.float32)                  # offsets that round
-    pos = np.concatenate([faces, edge, dup, outside, tiny])
+    pos = np.concatenate([faces, edge, dup, outside, negative, huge, tiny])
     pos = pos[rng.permutation(len(pos))]
     _assert_bit_exact(pos, 1.0, K)
 
