@@ -20,6 +20,9 @@ binning's rounding.  Each function below cites what it follows in the paper
   derivative of the sum above).
 * :func:`local_energy` - the part of L that depends on one particle, for
   finite differences with frozen cell assignment.
+* :func:`density` - the apodized top-hat density estimate the paper's kernel
+  accumulates as a 4th component, sum over near-field j with r < b of
+  (1 - r^2/b^2) (Sec. "Force Kernel").
 
 Every function has at least one pin in ``tests/test_oracle_pins.py`` against
 closed forms, brute force, symmetry or the paper's printed values.
@@ -67,6 +70,8 @@ def _load():
     lib.oracle_adjoint.argtypes = [P, P, i64, f64, i32, i32, f64, P, i64, P, i32]
     lib.oracle_local_energy.restype = i32
     lib.oracle_local_energy.argtypes = [P, P, i64, f64, i32, i32, f64, P, i64, P, P]
+    lib.oracle_density.restype = i32
+    lib.oracle_density.argtypes = [P, i64, f64, i32, i32, f64, P, i64, P, i32]
     lib.oracle_wrapped_positions.restype = i32
     lib.oracle_wrapped_positions.argtypes = [P, i64, f64, i32, P]
     lib.oracle_num_threads.restype = i32
@@ -148,6 +153,22 @@ def adjoint(pos, g, box: float, K: int, R: int, eps: float,
     n = N if s is None else s.shape[0]
     out = np.zeros((max(n, 1), 3), np.float64)
     rc = _load().oracle_adjoint(_p(pos), _p(gg), N, float(box), int(K), int(R), float(eps),
+                                None if s is None else _p(s), n, _p(out), int(threads))
+    if rc:
+        raise ValueError("non-finite coordinates")
+    return out[:n]
+
+
+def density(pos, box: float, K: int, R: int, b: float,
+            sinks: Optional[np.ndarray] = None, threads: int = 0) -> np.ndarray:
+    """Top-hat density estimate, FP64 [N] (or [len(sinks)]): sum over the
+    near-field neighbours j (self included) with r_ij < b of 1 - r_ij^2/b^2."""
+    pos = _pos(pos)
+    N = pos.shape[0]
+    s = None if sinks is None else np.ascontiguousarray(np.asarray(sinks, np.int64))
+    n = N if s is None else s.shape[0]
+    out = np.zeros(max(n, 1), np.float64)
+    rc = _load().oracle_density(_p(pos), N, float(box), int(K), int(R), float(b),
                                 None if s is None else _p(s), n, _p(out), int(threads))
     if rc:
         raise ValueError("non-finite coordinates")

@@ -26,6 +26,11 @@
  *     with eps_s = 2.16 eps_p (same section), eps_p the Plummer-equivalent
  *     softening the caller passes.  G = 1 and every particle has mass 1/N.
  *     The force is attractive: the acceleration of i points towards j.
+ *   - The apodized top-hat density estimate the paper's kernel accumulates as
+ *     a 4th component (Sec. "Force Kernel"): rho_i = sum over near-field j
+ *     with r_ij < b of (1 - r_ij^2 / b^2), the particle itself included
+ *     (it contributes 1).  The kernel accumulates b^2 - r^2; this is that sum
+ *     divided by b^2.
  *   - The adjoint (the gradient of L = sum_i g_i . a_i with respect to the
  *     positions), which the paper does not give; it is the derivative of the
  *     sum above: dL/dx_i = m sum_j J(d_ij) (g_j - g_i) with J(d) the Jacobian
@@ -336,6 +341,48 @@ int oracle_adjoint(const float *pos, const double *gvec, int64_t N, double box, 
         }
         visit_neighbours(&g, &g.cell[3 * i], &g.xw[3 * i], adj_visit, &ctx);
         for (int k = 0; k < 3; ++k) out[3 * q + k] = g.m * ctx.out[k];
+    }
+    oracle_grid_free(&g);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Top-hat density estimate                                                   */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    double b;
+    double rho;
+} dens_ctx;
+
+static void dens_visit(void *vctx, int64_t j, const double d[3])
+{
+    (void)j;
+    dens_ctx *ctx = (dens_ctx *)vctx;
+    double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    if (r < ctx->b) ctx->rho += 1.0 - (r * r) / (ctx->b * ctx->b);
+}
+
+/* rho_i = sum_{j in N(i), r_ij < b} (1 - r_ij^2/b^2) at the listed particles
+ * (or all), FP64 out[nsinks].  b in box units. */
+int oracle_density(const float *pos, int64_t N, double box, int K, int R, double b,
+                   const int64_t *sinks, int64_t nsinks, double *out, int nthreads)
+{
+    oracle_grid g;
+    if (oracle_grid_init(&g, pos, N, box, K, R, 1.0)) {
+        oracle_grid_free(&g);
+        return 1;
+    }
+    int64_t n = sinks ? nsinks : N;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t q = 0; q < n; ++q) {
+        int64_t i = sinks ? sinks[q] : q;
+        dens_ctx ctx = {b, 0.0};
+        visit_neighbours(&g, &g.cell[3 * i], &g.xw[3 * i], dens_visit, &ctx);
+        out[q] = ctx.rho;
     }
     oracle_grid_free(&g);
     return 0;

@@ -381,3 +381,55 @@ def test_adjoint_of_coincident_pair_is_central_jacobian():
     expect = 0.5 * 10.0 / eps_s ** 3 * (g[1] - g[0])
     assert np.allclose(grad[0], expect, rtol=1e-12)
     assert np.allclose(grad[1], -expect, rtol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# top-hat density estimate (Sec. "Force Kernel": b^2 - r^2 for r < b)
+# --------------------------------------------------------------------------
+
+def test_density_isolated_and_pair():
+    one = oracle.density(np.array([[0.3, 0.4, 0.5]], np.float32), 1.0, 8, 2, 0.05)
+    assert one[0] == 1.0          # the particle itself
+    b = 2.0 ** -5
+    pos = np.array([[0.5, 0.5, 0.5], [0.5 + b / 2, 0.5, 0.5]], np.float32)
+    assert np.allclose(oracle.density(pos, 1.0, 8, 2, b), 1.75, rtol=1e-15, atol=0)
+    pos[1, 0] = 0.5 + b            # r = b is outside the top hat
+    assert np.array_equal(oracle.density(pos, 1.0, 8, 2, b), [1.0, 1.0])
+
+
+def test_density_lattice_closed_form():
+    """Unit lattice, b = 1.5: self 1, 6 faces at r = 1 (5/9 each), 12 edges at
+    sqrt 2 (1/9 each), corners at sqrt 3 > b: rho = 17/3 for every particle."""
+    K = 8
+    g = np.arange(K) + 0.5
+    x = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3).astype(np.float32)
+    rho = oracle.density(x, float(K), K, 2, 1.5)
+    assert np.allclose(rho, 17.0 / 3.0, rtol=1e-14, atol=0)
+
+
+def test_density_brute_force_minimum_image():
+    rng = np.random.default_rng(31)
+    K, w = 5, 0.2
+    cells = rng.integers(0, K, size=(400, 3))
+    x = ((cells + 0.5) * w + rng.uniform(-0.24 * w, 0.24 * w, size=(400, 3))).astype(np.float32)
+    b = 0.15
+    rho = oracle.density(x, 1.0, K, 2, b)
+    xd = x.astype(np.float64)
+    d = xd[None, :, :] - xd[:, None, :]
+    d -= np.round(d)
+    r2 = (d * d).sum(axis=2)
+    ref = np.where(r2 < b * b, 1.0 - r2 / (b * b), 0.0).sum(axis=1)
+    assert np.allclose(rho, ref, rtol=1e-13, atol=0)
+
+
+def test_density_mean_matches_the_top_hat_volume():
+    """Uniform particles: E[rho] = 1 + n (8 pi / 15) b^3, the integral of
+    1 - r^2/b^2 over the ball of radius b times the number density n."""
+    rng = np.random.default_rng(32)
+    N = 60000
+    x = rng.random((N, 3)).astype(np.float32)
+    b = 0.02
+    rho = oracle.density(x, 1.0, 10, 2, b, sinks=np.arange(0, N, 7))
+    expect = 1.0 + (N - 1) * 8.0 * np.pi / 15.0 * b ** 3
+    sem = rho.std() / np.sqrt(rho.size)
+    assert abs(rho.mean() - expect) < 5 * sem
