@@ -338,6 +338,7 @@ def run_native(args, rank, world, local):
                   "lane_utilisation": st["pairs"] / max(st["lane_pairs"], 1)},
     }
 
+    out["density"] = measure_density(w, pos, ws, acc, fwd_pair_ms, flush)
     if not args.no_e2e:
         out["e2e"] = measure_e2e(args, w, g_np, dev, P, flush)
     if not args.no_batched:
@@ -358,6 +359,26 @@ def run_native(args, rank, world, local):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out))
+
+
+def measure_density(w, pos, ws, acc, fwd_pair_ms, flush):
+    """The forward with the fused top-hat density estimate (b = half a cell):
+    its pair kernel time against the plain forward pair kernel."""
+    import torch
+    from paper_2110_11392_gb300 import _lib
+    b = 0.5 * w.box / w.K
+    rho = torch.empty(w.N, dtype=torch.float32, device=pos.device)
+    _lib.nf_forces_density(pos, w.box, w.K, w.R, w.eps, b, acc, rho, ws)
+    _lib.nf_profile_enable(True)
+    ms = []
+    for _ in range(3):
+        flush.zero_()
+        _lib.nf_forces_density(pos, w.box, w.K, w.R, w.eps, b, acc, rho, ws)
+        ms.append(_lib.nf_profile_read(0)["pair_ms"])
+    _lib.nf_profile_enable(False)
+    t = float(np.mean(ms))
+    return {"b_cells": 0.5, "pair_kernel_ms": t, "over_fwd_pair_kernel": t / fwd_pair_ms,
+            "mean_rho": float(rho.mean().item())}
 
 
 def measure_e2e(args, w, g_np, dev, P, flush):

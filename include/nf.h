@@ -116,6 +116,18 @@ int nf_bin(const float *pos, int64_t N, double box, int K,
 int nf_forces(const float *pos, int64_t N, double box, int K, int R, double eps,
               float *acc, double *net, void *ws, size_t ws_bytes, void *stream);
 
+/* nf_forces plus the top-hat density estimate the paper's kernel accumulates
+ * as a 4th component of the acceleration (Sec. "Force Kernel": b^2 - r^2 for
+ * r < b, "nearly for free" next to the distances the force needs).
+ *   b    top-hat radius in box units, 0 < b <= R w (the ball must lie inside
+ *        the near field; checked, NF_ERR_ARG otherwise);
+ *   acc  as nf_forces (bit-identical to nf_forces for the same inputs);
+ *   rho  [N] FP32 (output), original order:
+ *        rho_i = sum_{j in N(i), |x_j - x_i| < b} (1 - |x_j - x_i|^2 / b^2),
+ *        the particle itself included (it contributes 1). */
+int nf_forces_density(const float *pos, int64_t N, double box, int K, int R, double eps,
+                      double b, float *acc, float *rho, void *ws, size_t ws_bytes, void *stream);
+
 /* Adjoint of nf_forces: for a loss L with g = dL/da,
  *   g     [N][3] FP32 (input), original order;
  *   grad  [N][3] FP32 (output), original order:
@@ -147,7 +159,7 @@ typedef struct {
 } nf_box;
 
 /* Shape of the force kernel's work (picked by the autotuner or by hand).
- *   sinks_per_lane  sinks each lane keeps in registers: 1, 2 or 4
+ *   sinks_per_lane  sinks each lane keeps in registers: 1 to 4
  *                   (a sink chunk is 32 * sinks_per_lane particles);
  *   stage           sources staged in shared memory per step: 64 or 128;
  *   warps_per_block 4 or 8;

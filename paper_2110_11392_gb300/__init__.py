@@ -12,6 +12,7 @@ from .nearfield import (
     bin_particles,
     forces,
     forces_adjoint,
+    forces_density,
     near_field,
     stats,
     status,
@@ -29,6 +30,7 @@ __all__ = [
     "bin_particles",
     "forces",
     "forces_adjoint",
+    "forces_density",
     "near_field",
     "stats",
     "status",

@@ -81,6 +81,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         "nf_profile_read": (i32, [i32, P]),
         "nf_kernel_launches": (i64, []),
         "nf_forces_noalloc": (i32, [P, i64, f64, i32, i32, f64, P, P, P]),
+        "nf_forces_density": (i32, [P, i64, f64, i32, i32, f64, f64, P, P, P, sz, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -95,7 +96,7 @@ def exported_symbols() -> Sequence[str]:
             "nf_bin", "nf_forces", "nf_forces_adjoint", "nf_forces_batched",
             "nf_forces_adjoint_batched", "nf_set_default_tuning", "nf_get_default_tuning",
             "nf_status_read", "nf_stats_read", "nf_profile_enable", "nf_profile_read",
-            "nf_kernel_launches", "nf_forces_noalloc")
+            "nf_kernel_launches", "nf_forces_noalloc", "nf_forces_density")
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -167,6 +168,14 @@ def nf_forces(pos: torch.Tensor, box: float, K: int, R: int, eps: float, acc: to
     _check(load().nf_forces(_ptr(pos), pos.shape[0], float(box), int(K), int(R), float(eps), _ptr(acc),
                             _ptr(net), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)),
            "nf_forces")
+
+
+def nf_forces_density(pos: torch.Tensor, box: float, K: int, R: int, eps: float, b: float,
+                      acc: torch.Tensor, rho: torch.Tensor, ws: torch.Tensor, stream=None) -> None:
+    _check(load().nf_forces_density(_ptr(pos), pos.shape[0], float(box), int(K), int(R), float(eps), float(b),
+                                    _ptr(acc), _ptr(rho), _ptr(ws), ws.numel() * ws.element_size(),
+                                    _stream(stream)),
+           "nf_forces_density")
 
 
 def nf_forces_adjoint(pos: torch.Tensor, g: torch.Tensor, box: float, K: int, R: int, eps: float,

@@ -20,7 +20,7 @@ from . import _lib
 Tuning = Tuple[int, int, int, int]
 
 CANDIDATES: List[Tuning] = [
-    (2, 128, 8, 0), (2, 64, 8, 0), (2, 128, 4, 0), (4, 128, 8, 0), (4, 64, 8, 0),
+    (2, 128, 8, 0), (2, 64, 8, 0), (2, 128, 4, 0), (3, 128, 8, 0), (3, 64, 8, 0), (4, 128, 8, 0), (4, 64, 8, 0),
     (2, 128, 8, 3), (2, 64, 8, 3), (1, 128, 8, 3), (1, 64, 8, 3), (1, 128, 8, 0),
 ]
 

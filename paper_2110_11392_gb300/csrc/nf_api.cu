@@ -219,7 +219,7 @@ int make_plan(const nf_box* boxes, int nboxes, bool need_force, int chunk_lanes,
         p->o_bucket_count = take(4 * kBuckets);
         p->o_items = take(16 * (size_t)items);
         p->o_gs = take(16 * (size_t)N);
-        p->o_partial = take(4 * 3 * (size_t)(2 * max_R + 1) * (size_t)N);
+        p->o_partial = take(4 * 4 * (size_t)(2 * max_R + 1) * (size_t)N);
         p->o_chunk_sums = take(8 * 3 * (size_t)nchunks);
     } else {
         p->o_chunks = p->o_bucket_of = p->o_bucket_count = p->o_items = p->o_gs = p->o_partial =
@@ -283,7 +283,7 @@ int run_binning(const Plan& p, const float* pos, void* ws, int32_t* cell_off, fl
 }
 
 int run_forces(const Plan& p, bool adjoint, const ForceTuning& t, const float* pos, const float* g, float* out,
-               double* net, void* ws, cudaStream_t s)
+               double* net, float* rho, void* ws, cudaStream_t s)
 {
     WsHeader* hdr = at<WsHeader>(ws, 0);
     BoxDev* boxes = at<BoxDev>(ws, p.o_boxes);
@@ -307,12 +307,12 @@ int run_forces(const Plan& p, bool adjoint, const ForceTuning& t, const float* p
     if (adjoint) NF_CUDA(launch_gather_g(g, perm, (int)p.N, gs, s), "gather g");
     float* partial = at<float>(ws, p.o_partial);
     NF_CUDA(prof_mark(2, s), "profile");
-    NF_CUDA(launch_force(adjoint, t, boxes, off, rel, gs, at<int4>(ws, p.o_items), hdr, partial, (int)p.N,
-                         p.max_nseg, s),
+    NF_CUDA(launch_force(adjoint, rho != nullptr, t, boxes, off, rel, gs, at<int4>(ws, p.o_items), hdr, partial,
+                         (int)p.N, p.max_nseg, s),
             adjoint ? "adjoint kernel" : "force kernel");
     NF_CUDA(prof_mark(3, s), "profile");
     double* chunk_sums = net ? at<double>(ws, p.o_chunk_sums) : nullptr;
-    NF_CUDA(launch_combine(adjoint, boxes, p.nboxes, p.nchunks, partial, perm, (int)p.N, out, chunk_sums, s),
+    NF_CUDA(launch_combine(adjoint, boxes, p.nboxes, p.nchunks, partial, perm, (int)p.N, out, rho, chunk_sums, s),
             "combine");
     if (net) NF_CUDA(launch_net(boxes, p.nboxes, chunk_sums, net, s), "net force");
     NF_CUDA(prof_mark(4, s), "profile");
@@ -343,7 +343,8 @@ nf_box one_box(int64_t N, double box, int K, int R, double eps)
 }
 
 int forces_entry(const nf_box* boxes, int nboxes, bool adjoint, const float* pos, const float* g, float* out,
-                 double* net, const nf_tuning* tune, void* ws, size_t ws_bytes, void* stream)
+                 double* net, const nf_tuning* tune, void* ws, size_t ws_bytes, void* stream,
+                 double dens_b = 0.0, float* rho = nullptr)
 {
     g_last_error.clear();
     ForceTuning t;
@@ -353,9 +354,20 @@ int forces_entry(const nf_box* boxes, int nboxes, bool adjoint, const float* pos
     rc = make_plan(boxes, nboxes, true, 32 * t.sinks_per_lane, &p);
     if (rc) return rc;
     if (!pos || !out || (adjoint && !g)) return fail(NF_ERR_ARG, "null pointer argument");
+    if (rho) {
+        for (int b = 0; b < nboxes; ++b) {
+            const double w = boxes[b].box / boxes[b].K;
+            if (!(dens_b > 0.0) || !std::isfinite(dens_b) || dens_b > boxes[b].R * w)
+                return fail(NF_ERR_ARG, "density radius b = %g must be in (0, R w = %g]: the top hat must lie in the near field",
+                            dens_b, boxes[b].R * w);
+            const double bc = dens_b / w;
+            p.boxes[b].dens_b2 = (float)(bc * bc);
+            p.boxes[b].dens_inv_b2 = (float)(1.0 / (bc * bc));
+        }
+    }
     rc = check_ws(p, ws, ws_bytes);
     if (rc) return rc;
-    return run_forces(p, adjoint, t, pos, g, out, net, ws, static_cast<cudaStream_t>(stream));
+    return run_forces(p, adjoint, t, pos, g, out, net, rho, ws, static_cast<cudaStream_t>(stream));
 }
 
 }  // namespace
@@ -439,6 +451,17 @@ int nf_forces(const float* pos, int64_t N, double box, int K, int R, double eps,
 {
     nf_box b = one_box(N, box, K, R, eps);
     return forces_entry(&b, 1, false, pos, nullptr, acc, net, nullptr, ws, ws_bytes, stream);
+}
+
+int nf_forces_density(const float* pos, int64_t N, double box, int K, int R, double eps, double b, float* acc,
+                      float* rho, void* ws, size_t ws_bytes, void* stream)
+{
+    if (!rho) {
+        g_last_error.clear();
+        return fail(NF_ERR_ARG, "null pointer argument");
+    }
+    nf_box bx = one_box(N, box, K, R, eps);
+    return forces_entry(&bx, 1, false, pos, nullptr, acc, nullptr, nullptr, ws, ws_bytes, stream, b, rho);
 }
 
 int nf_forces_adjoint(const float* pos, const float* g, int64_t N, double box, int K, int R, double eps, float* grad,

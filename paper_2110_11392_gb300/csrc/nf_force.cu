@@ -287,7 +287,9 @@ struct SinkSet {
     f2 nx[S], ny[S], nz[S];   // -position
     f2 ngx[S], ngy[S], ngz[S];  // -g (adjoint)
     f2 sx[S], sy[S], sz[S];   // current stage, even/odd sources in the halves
+    f2 sw[S];                 // current stage, density estimate
     float ax[S], ay[S], az[S];  // running totals
+    float aw[S];              // running density estimate
 };
 
 // Stage buffers of one warp in shared memory: sources as structure of arrays,
@@ -301,9 +303,17 @@ struct StageView {
     const float4* GZ;
 };
 
+// Top-hat density term of one packed pair (Sec. "Force Kernel"): b^2 - r^2 where positive.
+__device__ __forceinline__ f2 tophat2(f2 r2, f2 b2)
+{
+    const f2 t = fma2(r2, pk(-1.0f, -1.0f), b2);
+    return pk(fmaxf(lo(t), 0.0f), fmaxf(hi(t), 0.0f));
+}
+
 // Forward, fast path: f = r^-3 for every pair; tracks the smallest r^2.
-template <int S>
-__device__ __forceinline__ void stage_fwd_fast(const StageView& v, int cnt, SinkSet<S>& k, float& trk)
+// DENS adds the top-hat density estimate as a 4th sum.
+template <int S, bool DENS>
+__device__ __forceinline__ void stage_fwd_fast(const StageView& v, int cnt, SinkSet<S>& k, float& trk, f2 b2)
 {
     const f2 tiny = pk(kTiny, kTiny);
 #pragma unroll kFwdUnroll
@@ -321,6 +331,7 @@ __device__ __forceinline__ void stage_fwd_fast(const StageView& v, int cnt, Sink
                 r2 = fma2(dy, dy, r2);
                 r2 = fma2(dz, dz, r2);
                 trk = fminf(trk, fminf(lo(r2), hi(r2)));
+                if constexpr (DENS) k.sw[s] = add2(k.sw[s], tophat2(r2, b2));
 #if NF_FWD_RCP
                 const f2 f = mul2(rcp2(r2), rsqrt2(r2));
 #else
@@ -336,8 +347,8 @@ __device__ __forceinline__ void stage_fwd_fast(const StageView& v, int cnt, Sink
 }
 
 // Forward, exact path: f = min(poly(r), r^-3) (Eq. (spline) with the min hand-off).
-template <int S>
-__device__ __forceinline__ void stage_fwd_exact(const StageView& v, int cnt, SinkSet<S>& k, const Coef& cf)
+template <int S, bool DENS>
+__device__ __forceinline__ void stage_fwd_exact(const StageView& v, int cnt, SinkSet<S>& k, const Coef& cf, f2 b2)
 {
     const f2 tiny = pk(kTiny, kTiny);
     const f2 c0 = pk(cf.c0, cf.c0), c1 = pk(cf.c1, cf.c1), c2 = pk(cf.c2, cf.c2);
@@ -355,6 +366,7 @@ __device__ __forceinline__ void stage_fwd_exact(const StageView& v, int cnt, Sin
                 f2 r2 = fma2(dx, dx, tiny);
                 r2 = fma2(dy, dy, r2);
                 r2 = fma2(dz, dz, r2);
+                if constexpr (DENS) k.sw[s] = add2(k.sw[s], tophat2(r2, b2));
                 const f2 ri = rsqrt2(r2);
                 const f2 p = fma2(r2, fma2(c1, ri, c2), c0);
                 const f2 r3 = mul2(mul2(ri, ri), ri);
@@ -532,8 +544,8 @@ struct WarpBufs {
     float2* sh;     // [2][B]
 };
 
-template <int S, int B, bool ADJ>
-__device__ __forceinline__ void run_item(const ItemCtx& it, const Coef& cf,
+template <int S, int B, bool ADJ, bool DENS>
+__device__ __forceinline__ void run_item(const ItemCtx& it, const Coef& cf, f2 b2,
                                          const float4* __restrict__ rel, const float4* __restrict__ gs,
                                          const WarpBufs& wb, const int* seg_pre,
                                          const int* seg_start, const float* seg_dy, const float* seg_dz,
@@ -560,6 +572,7 @@ __device__ __forceinline__ void run_item(const ItemCtx& it, const Coef& cf,
             k.ngz[s] = pk(-g.z, -g.z);
         }
         k.ax[s] = k.ay[s] = k.az[s] = 0.0f;
+        k.aw[s] = 0.0f;
     }
 
     constexpr int PER = B / 32;
@@ -645,23 +658,24 @@ __device__ __forceinline__ void run_item(const ItemCtx& it, const Coef& cf,
         bool exact = st < nst0;
         if (!exact) {
 #pragma unroll
-            for (int s = 0; s < S; ++s) k.sx[s] = k.sy[s] = k.sz[s] = 0ull;
+            for (int s = 0; s < S; ++s) k.sx[s] = k.sy[s] = k.sz[s] = k.sw[s] = 0ull;
             float trk = kBig;
             if constexpr (ADJ) stage_adj_fast<S>(v, cnt, k, trk);
-            else stage_fwd_fast<S>(v, cnt, k, trk);
+            else stage_fwd_fast<S, DENS>(v, cnt, k, trk, b2);
             exact = __any_sync(kFull, trk < cf.eps2);
         }
         if (exact) {
 #pragma unroll
-            for (int s = 0; s < S; ++s) k.sx[s] = k.sy[s] = k.sz[s] = 0ull;
+            for (int s = 0; s < S; ++s) k.sx[s] = k.sy[s] = k.sz[s] = k.sw[s] = 0ull;
             if constexpr (ADJ) stage_adj_exact<S>(v, cnt, k, cf);
-            else stage_fwd_exact<S>(v, cnt, k, cf);
+            else stage_fwd_exact<S, DENS>(v, cnt, k, cf, b2);
         }
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             k.ax[s] += lo(k.sx[s]) + hi(k.sx[s]);
             k.ay[s] += lo(k.sy[s]) + hi(k.sy[s]);
             k.az[s] += lo(k.sz[s]) + hi(k.sz[s]);
+            if constexpr (DENS) k.aw[s] += lo(k.sw[s]) + hi(k.sw[s]);
         }
         __syncwarp();
     }
@@ -671,17 +685,18 @@ __device__ __forceinline__ void run_item(const ItemCtx& it, const Coef& cf,
         int at, slot;
         sink_lookup(it, p, &at, &slot);
         if (p < it.n_sink) {
-            const size_t base = (size_t)slot * 3 * (size_t)Ntot + (size_t)at;
+            const size_t base = (size_t)slot * 4 * (size_t)Ntot + (size_t)at;
             partial[base] = k.ax[s];
             partial[base + (size_t)Ntot] = k.ay[s];
             partial[base + 2 * (size_t)Ntot] = k.az[s];
+            if constexpr (DENS) partial[base + 3 * (size_t)Ntot] = k.aw[s];
         }
     }
 }
 
 // MINB = 2 allows 128 registers per thread (16 resident warps per SM);
 // MINB = 3 caps them at 85 so 24 warps fit (the "lean" variant, for S <= 2).
-template <int SMAX, int B, bool ADJ, int MINB>
+template <int SMAX, int B, bool ADJ, int MINB, bool DENS>
 __global__ void __launch_bounds__(256, MINB)
 k_force(const BoxDev* __restrict__ boxes, const int* __restrict__ off, const float4* __restrict__ rel,
         const float4* __restrict__ gs, const int4* __restrict__ items, WsHeader* hdr,
@@ -721,6 +736,7 @@ k_force(const BoxDev* __restrict__ boxes, const int* __restrict__ off, const flo
         cf.e0 = Bx.e0;
         cf.e1 = Bx.e1;
         cf.eps2 = Bx.eps2;
+        const f2 b2 = pk(Bx.dens_b2, Bx.dens_b2);
         const int K = it.K, R = it.R;
         const int l = item.x - it.cb;
         it.i = l / (K * K);
@@ -774,14 +790,17 @@ k_force(const BoxDev* __restrict__ boxes, const int* __restrict__ off, const flo
         it.n_c0 = seg_pre[1];
         const int n_chunk = min(CH, it.n_sink - it.chunk_begin);
         const int S = (n_chunk + 31) >> 5;
-        if (SMAX >= 4 && S >= 3)
-            run_item<(SMAX >= 4 ? 4 : 1), B, ADJ>(it, cf, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz,
+        if (SMAX >= 4 && S >= 4)
+            run_item<(SMAX >= 4 ? 4 : 1), B, ADJ, DENS>(it, cf, b2, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz,
+                                                  partial, Ntot);
+        else if (SMAX >= 3 && S == 3)
+            run_item<(SMAX >= 3 ? 3 : 1), B, ADJ, DENS>(it, cf, b2, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz,
                                                   partial, Ntot);
         else if (SMAX >= 2 && S == 2)
-            run_item<(SMAX >= 2 ? 2 : 1), B, ADJ>(it, cf, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz,
+            run_item<(SMAX >= 2 ? 2 : 1), B, ADJ, DENS>(it, cf, b2, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz,
                                                   partial, Ntot);
         else
-            run_item<1, B, ADJ>(it, cf, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz, partial, Ntot);
+            run_item<1, B, ADJ, DENS>(it, cf, b2, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz, partial, Ntot);
         __syncwarp();
     }
 }
@@ -800,7 +819,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
 
 __global__ void __launch_bounds__(256)
 k_combine(const BoxDev* __restrict__ boxes, int nboxes, const float* __restrict__ partial,
-          const int* __restrict__ perm, int Ntot, float* __restrict__ out,
+          const int* __restrict__ perm, int Ntot, float* __restrict__ out, float* __restrict__ rho,
           double* __restrict__ chunk_sums, bool adjoint)
 {
     // block = one chunk of kCombineChunk sorted slots of a single box
@@ -831,7 +850,7 @@ k_combine(const BoxDev* __restrict__ boxes, int nboxes, const float* __restrict_
         for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int q = 0; q < kMaxSlots; ++q)
-                v[c][q] = q < nslot ? partial[((size_t)q * 3 + c) * (size_t)Ntot + s] : 0.0f;
+                v[c][q] = q < nslot ? partial[((size_t)q * 4 + c) * (size_t)Ntot + s] : 0.0f;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             // the 2R+1 pencil partials, summed without rounding error into (sh, sl)
@@ -851,6 +870,17 @@ k_combine(const BoxDev* __restrict__ boxes, int nboxes, const float* __restrict_
             const float a = __fadd_rn(p, __fmaf_rn(sh, s_lo, __fmaf_rn(sl, s_hi, perr)));
             out[3 * (size_t)e + c] = a;
             if (chunk_sums) net[c] += m * (double)a;
+        }
+        if (rho) {
+            // density partials (b^2 - r^2 sums), compensated, times 1/b^2
+            float sh = partial[(size_t)3 * (size_t)Ntot + s], sl = 0.0f;
+            for (int q = 1; q < nslot; ++q) {
+                float t, err;
+                two_sum(sh, partial[((size_t)q * 4 + 3) * (size_t)Ntot + s], t, err);
+                sh = t;
+                sl = __fadd_rn(sl, err);
+            }
+            rho[e] = __fmul_rn(__fadd_rn(sh, sl), B.dens_inv_b2);
         }
     }
     if (chunk_sums) {
@@ -898,30 +928,38 @@ typedef void (*ForceKernel)(const BoxDev*, const int*, const float4*, const floa
 // resident warps per SM.
 bool wants_lean(const ForceTuning& t) { return t.sinks_per_lane <= 2 && t.warps_per_block * t.blocks_per_sm >= 24; }
 
-template <bool ADJ>
+template <bool ADJ, bool DENS>
 ForceKernel pick_kernel(const ForceTuning& t)
 {
     const int smax = t.sinks_per_lane, stage = t.stage;
     if (wants_lean(t)) {
         if (stage == 128) {
-            if (smax == 2) return k_force<2, 128, ADJ, 3>;
-            if (smax == 1) return k_force<1, 128, ADJ, 3>;
+            if (smax == 2) return k_force<2, 128, ADJ, 3, DENS>;
+            if (smax == 1) return k_force<1, 128, ADJ, 3, DENS>;
         } else if (stage == 64) {
-            if (smax == 2) return k_force<2, 64, ADJ, 3>;
-            if (smax == 1) return k_force<1, 64, ADJ, 3>;
+            if (smax == 2) return k_force<2, 64, ADJ, 3, DENS>;
+            if (smax == 1) return k_force<1, 64, ADJ, 3, DENS>;
         }
         return nullptr;
     }
     if (stage == 128) {
-        if (smax == 4) return k_force<4, 128, ADJ, 2>;
-        if (smax == 2) return k_force<2, 128, ADJ, 2>;
-        if (smax == 1) return k_force<1, 128, ADJ, 2>;
+        if (smax == 4) return k_force<4, 128, ADJ, 2, DENS>;
+        if (smax == 3) return k_force<3, 128, ADJ, 2, DENS>;
+        if (smax == 2) return k_force<2, 128, ADJ, 2, DENS>;
+        if (smax == 1) return k_force<1, 128, ADJ, 2, DENS>;
     } else if (stage == 64) {
-        if (smax == 4) return k_force<4, 64, ADJ, 2>;
-        if (smax == 2) return k_force<2, 64, ADJ, 2>;
-        if (smax == 1) return k_force<1, 64, ADJ, 2>;
+        if (smax == 4) return k_force<4, 64, ADJ, 2, DENS>;
+        if (smax == 3) return k_force<3, 64, ADJ, 2, DENS>;
+        if (smax == 2) return k_force<2, 64, ADJ, 2, DENS>;
+        if (smax == 1) return k_force<1, 64, ADJ, 2, DENS>;
     }
     return nullptr;
+}
+
+ForceKernel pick(bool adjoint, bool density, const ForceTuning& t)
+{
+    if (adjoint) return pick_kernel<true, false>(t);
+    return density ? pick_kernel<false, true>(t) : pick_kernel<false, false>(t);
 }
 
 size_t force_smem_bytes(bool adjoint, const ForceTuning& t, int max_nseg)
@@ -936,15 +974,15 @@ size_t force_smem_bytes(bool adjoint, const ForceTuning& t, int max_nseg)
 
 bool force_tuning_supported(const ForceTuning& t)
 {
-    bool s_ok = t.sinks_per_lane == 1 || t.sinks_per_lane == 2 || t.sinks_per_lane == 4;
+    bool s_ok = t.sinks_per_lane >= 1 && t.sinks_per_lane <= 4;
     bool b_ok = t.stage == 64 || t.stage == 128;
     bool w_ok = t.warps_per_block == 4 || t.warps_per_block == 8;
     return s_ok && b_ok && w_ok && t.blocks_per_sm >= 0 && t.blocks_per_sm <= 8;
 }
 
-int force_blocks_per_sm(bool adjoint, const ForceTuning& t, int max_nseg)
+int force_blocks_per_sm(bool adjoint, bool density, const ForceTuning& t, int max_nseg)
 {
-    ForceKernel kfn = adjoint ? pick_kernel<true>(t) : pick_kernel<false>(t);
+    ForceKernel kfn = pick(adjoint, density, t);
     if (!kfn) return 0;
     size_t smem = force_smem_bytes(adjoint, t, max_nseg);
     if (ensure_smem((const void*)kfn, (int)smem) != cudaSuccess) return 0;
@@ -987,11 +1025,11 @@ cudaError_t launch_gather_g(const float* g, const int* perm, int Ntot, float4* g
     return cudaGetLastError();
 }
 
-cudaError_t launch_force(bool adjoint, const ForceTuning& t, const BoxDev* boxes, const int* cell_off,
-                         const float4* rel, const float4* gs, const int4* items, WsHeader* hdr,
-                         float* partial, int Ntot, int max_nseg, cudaStream_t s)
+cudaError_t launch_force(bool adjoint, bool density, const ForceTuning& t, const BoxDev* boxes,
+                         const int* cell_off, const float4* rel, const float4* gs, const int4* items,
+                         WsHeader* hdr, float* partial, int Ntot, int max_nseg, cudaStream_t s)
 {
-    ForceKernel kfn = adjoint ? pick_kernel<true>(t) : pick_kernel<false>(t);
+    ForceKernel kfn = pick(adjoint, density, t);
     if (!kfn) return cudaErrorInvalidValue;
     size_t smem = force_smem_bytes(adjoint, t, max_nseg);
     cudaError_t e = ensure_smem((const void*)kfn, (int)smem);
@@ -1011,10 +1049,10 @@ cudaError_t launch_force(bool adjoint, const ForceTuning& t, const BoxDev* boxes
 }
 
 cudaError_t launch_combine(bool adjoint, const BoxDev* boxes, int nboxes, int nchunks, const float* partial,
-                           const int* perm, int Ntot, float* out, double* chunk_sums, cudaStream_t s)
+                           const int* perm, int Ntot, float* out, float* rho, double* chunk_sums, cudaStream_t s)
 {
     if (nchunks <= 0) return cudaSuccess;
-    k_combine<<<nchunks, 256, 0, s>>>(boxes, nboxes, partial, perm, Ntot, out, chunk_sums, adjoint);
+    k_combine<<<nchunks, 256, 0, s>>>(boxes, nboxes, partial, perm, Ntot, out, rho, chunk_sums, adjoint);
     count_launches(1);
     return cudaGetLastError();
 }

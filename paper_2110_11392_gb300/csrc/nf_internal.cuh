@@ -7,7 +7,8 @@
 //   rel         float4 [N]      sorted cell-centred offsets, .w = index bits
 //   perm        int32 [N]       sorted slot -> particle (global index)
 //   items       int4 [<= M]     work items: (global centre cell, chunk, box, -)
-//   partial     float [(2R+1)*3][N]  per-pencil partial sums, sorted order
+//   partial     float [(2R+1)*4][N]  per-pencil partial sums (ax, ay, az, density),
+//                                    sorted order
 // A "global cell" numbers the cells of all boxes of a batch back to back:
 // box b owns cells [cell_base_b, cell_base_b + K_b^3).
 #pragma once
@@ -38,6 +39,9 @@ struct BoxDev {
     // K / box = kl_mant * 2^kl_exp with an odd kl_mant < 2^29, or kl_mant = 0
     // when no such short form exists (then the shift stays in FP64)
     int kl_mant, kl_exp;
+    // top-hat density estimate (Sec. "Force Kernel"): b^2 and 1/b^2 in cell units
+    float dens_b2, dens_inv_b2;
+    float pad0, pad1;
 };
 static_assert(sizeof(BoxDev) % 16 == 0, "BoxDev must stay 16-byte aligned");
 
@@ -109,16 +113,16 @@ cudaError_t launch_items(const BoxDev* boxes, int nboxes, int Ctot, const int* c
                          int4* items, WsHeader* hdr, cudaStream_t s);
 cudaError_t launch_gather_g(const float* g, const int* perm, int Ntot, float4* gs,
                             cudaStream_t s);
-cudaError_t launch_force(bool adjoint, const ForceTuning& t, const BoxDev* boxes,
+cudaError_t launch_force(bool adjoint, bool density, const ForceTuning& t, const BoxDev* boxes,
                          const int* cell_off, const float4* rel, const float4* gs,
                          const int4* items, WsHeader* hdr, float* partial, int Ntot,
                          int max_nseg, cudaStream_t s);
 cudaError_t launch_combine(bool adjoint, const BoxDev* boxes, int nboxes, int nchunks,
                            const float* partial, const int* perm, int Ntot, float* out,
-                           double* chunk_sums, cudaStream_t s);
+                           float* rho, double* chunk_sums, cudaStream_t s);
 cudaError_t launch_net(const BoxDev* boxes, int nboxes, const double* chunk_sums,
                        double* net, cudaStream_t s);
 bool force_tuning_supported(const ForceTuning& t);
-int force_blocks_per_sm(bool adjoint, const ForceTuning& t, int max_nseg);
+int force_blocks_per_sm(bool adjoint, bool density, const ForceTuning& t, int max_nseg);
 
 }  // namespace nf

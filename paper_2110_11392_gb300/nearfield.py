@@ -70,6 +70,20 @@ def forces(pos: torch.Tensor, box: float, K: int, R: int, eps: float,
     return (acc, net_t) if net else acc
 
 
+def forces_density(pos: torch.Tensor, box: float, K: int, R: int, eps: float, b: float,
+                   ws: Optional[torch.Tensor] = None):
+    """Accelerations and the top-hat density estimate (nf_forces_density):
+    (acc float32 [N, 3], rho float32 [N]), rho_i = sum_{r_ij < b} (1 - r_ij^2/b^2)."""
+    pos = _check_pos(pos)
+    N = pos.shape[0]
+    if ws is None:
+        ws = workspace(_lib.nf_workspace_bytes(N, K, R), pos.device)
+    acc = torch.empty_like(pos)
+    rho = torch.empty(N, dtype=torch.float32, device=pos.device)
+    _lib.nf_forces_density(pos, box, K, R, eps, b, acc, rho, ws)
+    return acc, rho
+
+
 def forces_adjoint(pos: torch.Tensor, g: torch.Tensor, box: float, K: int, R: int, eps: float,
                    ws: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None):
     """dL/dx for upstream g = dL/da (nf_forces_adjoint), float32 [N, 3]."""

@@ -99,7 +99,7 @@ def test_batched_rejects_bad_packing_and_tuning():
     assert lib.nf_forces_batched(arr, 2, FAKE, FAKE, None, None, FAKE_WS, 1 << 40, None) == _lib.NF_ERR_ARG
     assert "packed" in _lib.nf_last_error()
     arr = _lib.make_boxes(boxes)
-    bad = _lib.nf_tuning(3, 128, 8, 0)
+    bad = _lib.nf_tuning(5, 128, 8, 0)
     assert lib.nf_forces_batched(arr, 2, FAKE, FAKE, None, ctypes.byref(bad), FAKE_WS, 1 << 40,
                                  None) == _lib.NF_ERR_ARG
     assert lib.nf_forces_batched(arr, 0, FAKE, FAKE, None, None, FAKE_WS, 1 << 40, None) == _lib.NF_ERR_ARG
