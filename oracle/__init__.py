@@ -20,6 +20,12 @@ binning's rounding.  Each function below cites what it follows in the paper
   derivative of the sum above).
 * :func:`local_energy` - the part of L that depends on one particle, for
   finite differences with frozen cell assignment.
+* :func:`timestep` - the global time step of Eq. (timestep), Sec. "Time
+  Stepping": per-cell v_rms / a_max (v_rms without subtracting the cell's
+  mean velocity), the most conservative cell, guarded by the global ratio
+  and limited by the Hubble term.
+* :func:`kdk_step` - one Kick-Drift-Kick leapfrog step (Sec. "Time
+  Stepping") with the near-field accelerations of :func:`forces`.
 * :func:`density` - the apodized top-hat density estimate the paper's kernel
   accumulates as a 4th component, sum over near-field j with r < b of
   (1 - r^2/b^2) (Sec. "Force Kernel").
@@ -173,6 +179,46 @@ def density(pos, box: float, K: int, R: int, b: float,
     if rc:
         raise ValueError("non-finite coordinates")
     return out[:n]
+
+
+def timestep(vel, acc, cell, eta_acc: float, eta_h: float = 0.0, hubble: float = 0.0) -> float:
+    """dt = min(eta_H / H, eta_acc * max(min_c v_rms,c / a_max,c, v_rms / a_max)) in FP64.
+
+    Eq. (timestep) written for dt with a = 1 (dt = da / (a H)); cell[i] is the
+    cell of particle i.  Cells whose largest acceleration is zero are skipped;
+    with H = 0 there is no Hubble limit.  Returns +inf if nothing limits dt.
+    """
+    v2 = (np.asarray(vel, np.float64) ** 2).sum(axis=1)
+    a = np.sqrt((np.asarray(acc, np.float64) ** 2).sum(axis=1))
+    cell = np.asarray(cell)
+    best = np.inf
+    for c in np.unique(cell):
+        sel = cell == c
+        amax = a[sel].max()
+        if amax > 0.0:
+            best = min(best, np.sqrt(v2[sel].mean()) / amax)
+    amax_g = a.max()
+    glob = np.sqrt(v2.mean()) / amax_g if amax_g > 0.0 else np.inf
+    dt = eta_acc * max(best, glob) if np.isfinite(max(best, glob)) else np.inf
+    if hubble > 0.0:
+        dt = min(dt, eta_h / hubble)
+    return float(dt)
+
+
+def kdk_step(pos, vel, acc, dt: float, box: float, K: int, R: int, eps: float):
+    """One leapfrog step: v += a dt/2; x += v dt (wrapped into [0, box)); a = F(x);
+    v += a dt/2.  State stored as the API stores it (FP32 positions and
+    velocities); arithmetic in FP64.  Returns (pos, vel, acc_FP64)."""
+    pos = np.asarray(pos, np.float32)
+    v = np.asarray(vel, np.float32).astype(np.float64)
+    a = np.asarray(acc, np.float64)
+    v_half = (v + 0.5 * dt * a).astype(np.float32)
+    x = pos.astype(np.float64) + dt * v_half.astype(np.float64)
+    x = np.mod(x, box).astype(np.float32)
+    x[x >= np.float32(box)] = np.float32(0.0)
+    a_new = forces(x, box, K, R, eps)
+    v_new = (v_half.astype(np.float64) + 0.5 * dt * a_new).astype(np.float32)
+    return x, v_new, a_new
 
 
 def local_energy(pos, g, box: float, K: int, R: int, eps: float,

@@ -433,3 +433,66 @@ def test_density_mean_matches_the_top_hat_volume():
     expect = 1.0 + (N - 1) * 8.0 * np.pi / 15.0 * b ** 3
     sem = rho.std() / np.sqrt(rho.size)
     assert abs(rho.mean() - expect) < 5 * sem
+
+
+# --------------------------------------------------------------------------
+# time stepping (Sec. "Time Stepping": KDK leapfrog, Eq. (timestep))
+# --------------------------------------------------------------------------
+
+def test_timestep_hand_computed():
+    """Two occupied cells: cell 0 has v_rms = sqrt((1 + 9)/2) = sqrt 5 and
+    a_max = 2; cell 1 has v_rms = 4, a_max = 8.  min_c = 0.5 (cell 1); global:
+    v_rms = sqrt((1 + 9 + 16)/3), a_max = 8."""
+    vel = np.array([[1.0, 0, 0], [0, 3.0, 0], [0, 0, 4.0]])
+    acc = np.array([[2.0, 0, 0], [0, 1.0, 0], [0, 8.0, 0]])
+    cell = np.array([0, 0, 1])
+    glob = np.sqrt(26.0 / 3.0) / 8.0
+    assert glob < 0.5
+    assert oracle.timestep(vel, acc, cell, 0.25) == pytest.approx(0.25 * 0.5, rel=1e-15)
+    # a cell that is much colder than the box is overruled by the global ratio
+    vel2 = vel.copy()
+    vel2[2] = [0, 0, 0.01]
+    glob2 = np.sqrt((1 + 9 + 1e-4) / 3.0) / 8.0
+    assert oracle.timestep(vel2, acc, cell, 0.25) == pytest.approx(0.25 * glob2, rel=1e-14)
+    # the Hubble limit eta_H / H
+    assert oracle.timestep(vel, acc, cell, 0.25, eta_h=0.01, hubble=1.0) == pytest.approx(0.01)
+
+
+def _kdk_box(seed=3, N=600, K=5):
+    rng = np.random.default_rng(seed)
+    x = rng.random((N, 3)).astype(np.float32)
+    v = (0.05 * rng.standard_normal((N, 3))).astype(np.float32)
+    return x, v, K
+
+
+def test_kdk_reversible():
+    """Leapfrog is time-symmetric: a step with dt then one with -dt returns
+    to the start (up to FP32 storage of the state)."""
+    x, v, K = _kdk_box()
+    eps = 0.004
+    a = oracle.forces(x, 1.0, K, 2, eps)
+    x1, v1, a1 = oracle.kdk_step(x, v, a, 1e-3, 1.0, K, 2, eps)
+    x2, v2, _ = oracle.kdk_step(x1, v1, a1, -1e-3, 1.0, K, 2, eps)
+    dx = (x2.astype(np.float64) - x + 0.5) % 1.0 - 0.5
+    assert np.abs(dx).max() < 1e-6
+    assert np.abs(v2 - v).max() < 1e-5 * np.abs(v).max()
+    assert np.abs(x1 - x).max() > 1e-5   # it did move
+
+
+def test_kdk_conserves_momentum_and_moves_free_particles_straight():
+    x, v, K = _kdk_box(seed=4)
+    eps = 0.004
+    a = oracle.forces(x, 1.0, K, 2, eps)
+    p0 = v.astype(np.float64).sum(axis=0)
+    xs, vs, as_ = x, v, a
+    for _ in range(3):
+        xs, vs, as_ = oracle.kdk_step(xs, vs, as_, 1e-3, 1.0, K, 2, eps)
+    # Newton III: forces cancel pairwise, so the total momentum changes only by
+    # the FP32 rounding of the stored velocities (~1e-8 of sum |v| here)
+    assert np.abs(vs.astype(np.float64).sum(axis=0) - p0).max() < 1e-6 * np.abs(v).sum()
+    # a lone particle (no neighbour in its near field) drifts at constant velocity
+    lone = np.array([[0.1, 0.2, 0.3]], np.float32)
+    vl = np.array([[0.5, -0.25, 0.125]], np.float32)
+    xl, vl2, _ = oracle.kdk_step(lone, vl, np.zeros((1, 3)), 0.25, 1.0, 5, 2, 0.004)
+    assert np.array_equal(vl2, vl)
+    assert np.allclose(xl, [[0.225, 0.1375, 0.33125]], rtol=0, atol=1e-7)
