@@ -339,6 +339,7 @@ def run_native(args, rank, world, local):
     }
 
     out["density"] = measure_density(w, pos, ws, acc, fwd_pair_ms, flush)
+    out["kdk"] = measure_kdk(w, dev, flush)
     if not args.no_e2e:
         out["e2e"] = measure_e2e(args, w, g_np, dev, P, flush)
     if not args.no_batched:
@@ -379,6 +380,35 @@ def measure_density(w, pos, ws, acc, fwd_pair_ms, flush):
     t = float(np.mean(ms))
     return {"b_cells": 0.5, "pair_kernel_ms": t, "over_fwd_pair_kernel": t / fwd_pair_ms,
             "mean_rho": float(rho.mean().item())}
+
+
+def measure_kdk(w, dev, flush, steps=5):
+    """Leapfrog steps with the adaptive global time step, all on the device:
+    kick, drift, near-field forces, kick and Eq. (timestep) per step."""
+    import torch
+    import paper_2110_11392_gb300 as nf
+    from paper_2110_11392_gb300 import _lib
+    rng = np.random.default_rng(9)
+    pos = torch.from_numpy(w.pos).to(dev)
+    vel = torch.from_numpy((0.01 * rng.standard_normal((w.N, 3))).astype(np.float32)).to(dev)
+    ws = torch.empty(_lib.nf_workspace_bytes(w.N, w.K, w.R), dtype=torch.uint8, device=dev)
+    acc = nf.forces(pos, w.box, w.K, w.R, w.eps, ws=ws)
+    dt = torch.zeros(1, dtype=torch.float64, device=dev)
+    prm = _lib.make_step_params(0.25)
+    _lib.nf_timestep(pos, vel, acc, w.box, w.K, prm, dt, ws)
+    stream = torch.cuda.current_stream(dev)
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _lib.nf_kdk_step(pos, vel, acc, w.box, w.K, w.R, w.eps, dt, prm, ws)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = float(np.mean(ms))
+    return {"ms_per_step": t, "particle_updates_per_s": w.N / (t / 1e3), "last_dt": float(dt.item()),
+            "steps": steps, "note": "kick + drift + nf_forces + kick + Eq. (timestep), near field only"}
 
 
 def measure_e2e(args, w, g_np, dev, P, flush):

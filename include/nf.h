@@ -243,6 +243,42 @@ int nf_forces_noalloc(const float *pos, int64_t N, double box, int K, int R, dou
                       float *acc, double *net, void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* Time stepping (Sec. "Time Stepping": Kick-Drift-Kick leapfrog with a      */
+/* global time step, Eq. (timestep))                                         */
+/* ------------------------------------------------------------------------ */
+
+/* Parameters of the time-step criterion, Eq. (timestep), written for the time
+ * step dt at scale factor a = 1 (da = a H dt):
+ *     dt = min(eta_h / hubble, eta_acc * max(min_c [v_rms / a_max]_c,
+ *                                            v_rms,global / a_max,global)),
+ * v_rms per cell without subtracting the cell's mean velocity (as the paper
+ * specifies), a_max the largest |a| in the cell; cells with a_max = 0 are
+ * skipped; hubble = 0 drops the Hubble limit.  eta_acc > 0 is required. */
+typedef struct {
+    double eta_acc;
+    double eta_h;
+    double hubble;
+} nf_step_params;
+
+/* Global time step of the particles (host array prm; dt is ONE double in device
+ * memory, written).  Bins pos (same rule as nf_bin) to group the particles by
+ * cell, then reduces vel and acc ([N][3] FP32, original order) per cell.
+ * If nothing limits the step (all accelerations zero and hubble = 0) dt = +inf. */
+int nf_timestep(const float *pos, const float *vel, const float *acc, int64_t N, double box, int K,
+                const nf_step_params *prm, double *dt, void *ws, size_t ws_bytes, void *stream);
+
+/* One leapfrog step in place, all on the device:
+ *     vel += acc dt/2;  pos = wrap(pos + vel dt) into [0, box);
+ *     acc = nf_forces(pos);  vel += acc dt/2;
+ * acc must hold the accelerations at the input positions (from nf_forces or
+ * the previous step).  dt is ONE double in device memory: it is read for this
+ * step and, when prm != NULL, overwritten with the next step's dt from
+ * Eq. (timestep) at the new state; so a loop of steps needs no host round trip
+ * and can be captured in a CUDA graph.  Arguments as nf_forces otherwise. */
+int nf_kdk_step(float *pos, float *vel, float *acc, int64_t N, double box, int K, int R, double eps,
+                double *dt, const nf_step_params *prm, void *ws, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* Status and statistics                                                     */
 /* ------------------------------------------------------------------------ */
 

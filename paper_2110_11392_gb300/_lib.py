@@ -37,6 +37,10 @@ class nf_profile(ctypes.Structure):
                 ("combine_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
 
 
+class nf_step_params(ctypes.Structure):
+    _fields_ = [("eta_acc", ctypes.c_double), ("eta_h", ctypes.c_double), ("hubble", ctypes.c_double)]
+
+
 class nf_tuning(ctypes.Structure):
     _fields_ = [("sinks_per_lane", ctypes.c_int), ("stage", ctypes.c_int),
                 ("warps_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int)]
@@ -82,6 +86,8 @@ def load(build: bool = True) -> ctypes.CDLL:
         "nf_kernel_launches": (i64, []),
         "nf_forces_noalloc": (i32, [P, i64, f64, i32, i32, f64, P, P, P]),
         "nf_forces_density": (i32, [P, i64, f64, i32, i32, f64, f64, P, P, P, sz, P]),
+        "nf_timestep": (i32, [P, P, P, i64, f64, i32, P, P, P, sz, P]),
+        "nf_kdk_step": (i32, [P, P, P, i64, f64, i32, i32, f64, P, P, P, sz, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -96,7 +102,8 @@ def exported_symbols() -> Sequence[str]:
             "nf_bin", "nf_forces", "nf_forces_adjoint", "nf_forces_batched",
             "nf_forces_adjoint_batched", "nf_set_default_tuning", "nf_get_default_tuning",
             "nf_status_read", "nf_stats_read", "nf_profile_enable", "nf_profile_read",
-            "nf_kernel_launches", "nf_forces_noalloc", "nf_forces_density")
+            "nf_kernel_launches", "nf_forces_noalloc", "nf_forces_density", "nf_timestep",
+            "nf_kdk_step")
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -249,3 +256,23 @@ def nf_forces_noalloc(pos: torch.Tensor, box: float, K: int, R: int, eps: float,
     _check(load().nf_forces_noalloc(_ptr(pos), pos.shape[0], float(box), int(K), int(R), float(eps),
                                     _ptr(acc), _ptr(net), _stream(stream)),
            "nf_forces_noalloc")
+
+
+def make_step_params(eta_acc: float, eta_h: float = 0.0, hubble: float = 0.0) -> nf_step_params:
+    return nf_step_params(float(eta_acc), float(eta_h), float(hubble))
+
+
+def nf_timestep(pos: torch.Tensor, vel: torch.Tensor, acc: torch.Tensor, box: float, K: int, prm,
+                dt: torch.Tensor, ws: torch.Tensor, stream=None) -> None:
+    _check(load().nf_timestep(_ptr(pos), _ptr(vel), _ptr(acc), pos.shape[0], float(box), int(K),
+                              ctypes.byref(prm), _ptr(dt), _ptr(ws), ws.numel() * ws.element_size(),
+                              _stream(stream)),
+           "nf_timestep")
+
+
+def nf_kdk_step(pos: torch.Tensor, vel: torch.Tensor, acc: torch.Tensor, box: float, K: int, R: int, eps: float,
+                dt: torch.Tensor, prm, ws: torch.Tensor, stream=None) -> None:
+    _check(load().nf_kdk_step(_ptr(pos), _ptr(vel), _ptr(acc), pos.shape[0], float(box), int(K), int(R),
+                              float(eps), _ptr(dt), ctypes.byref(prm) if prm is not None else None, _ptr(ws),
+                              ws.numel() * ws.element_size(), _stream(stream)),
+           "nf_kdk_step")

@@ -99,7 +99,7 @@ struct Plan {
     std::vector<BoxDev> boxes;
     // region offsets (bytes from ws)
     size_t o_boxes, o_keys_a, o_keys_b, o_vals_a, o_vals_b, o_off, o_hist, o_aux, o_rel, o_perm,
-        o_chunks, o_bucket_of, o_bucket_count, o_items, o_gs, o_partial, o_chunk_sums, total;
+        o_chunks, o_bucket_of, o_bucket_count, o_items, o_gs, o_partial, o_chunk_sums, o_step, total;
 };
 
 // Validates one box; fills the device constants.
@@ -213,6 +213,7 @@ int make_plan(const nf_box* boxes, int nboxes, bool need_force, int chunk_lanes,
     p->o_aux = take(4 * (aux > aux2 ? aux : aux2));
     p->o_rel = take(16 * (size_t)N);
     p->o_perm = take(4 * (size_t)N);
+    p->o_step = take(sizeof(StepScratch));
     if (need_force) {
         p->o_chunks = take(4 * (size_t)C);
         p->o_bucket_of = take((size_t)C);
@@ -529,6 +530,59 @@ int nf_forces_noalloc(const float* pos, int64_t N, double box, int K, int R, dou
     if (rc) return rc;
     return forces_entry(&b, 1, false, pos, nullptr, acc, net, nullptr, scratch, NF_NOALLOC_SCRATCH_BYTES,
                         stream);
+}
+
+int nf_timestep(const float* pos, const float* vel, const float* acc, int64_t N, double box, int K,
+                const nf_step_params* prm, double* dt, void* ws, size_t ws_bytes, void* stream)
+{
+    g_last_error.clear();
+    nf_box b = one_box(N, box, K, 0, 0.0);
+    Plan p;
+    int rc = make_plan(&b, 1, false, 32, &p);
+    if (rc) return rc;
+    if (!pos || !vel || !acc || !dt || !prm) return fail(NF_ERR_ARG, "null pointer argument");
+    if (!(prm->eta_acc > 0.0) || !(prm->hubble >= 0.0) || (prm->hubble > 0.0 && !(prm->eta_h > 0.0)))
+        return fail(NF_ERR_ARG, "step parameters need eta_acc > 0, hubble >= 0 and eta_h > 0 when hubble > 0");
+    rc = check_ws(p, ws, ws_bytes);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int32_t* off = at<int32_t>(ws, p.o_off);
+    int32_t* perm = at<int32_t>(ws, p.o_perm);
+    rc = run_binning(p, pos, ws, off, at<float4>(ws, p.o_rel), perm, s);
+    if (rc) return rc;
+    NF_CUDA(launch_timestep(off, perm, vel, acc, (int)p.C, (long long)N, prm->eta_acc, prm->eta_h, prm->hubble,
+                            at<StepScratch>(ws, p.o_step), dt, s),
+            "time step");
+    return NF_OK;
+}
+
+int nf_kdk_step(float* pos, float* vel, float* acc, int64_t N, double box, int K, int R, double eps, double* dt,
+                const nf_step_params* prm, void* ws, size_t ws_bytes, void* stream)
+{
+    g_last_error.clear();
+    nf_box b = one_box(N, box, K, R, eps);
+    ForceTuning t;
+    int rc = check_tuning(nullptr, &t);
+    if (rc) return rc;
+    Plan p;
+    rc = make_plan(&b, 1, true, 32 * t.sinks_per_lane, &p);
+    if (rc) return rc;
+    if (!pos || !vel || !acc || !dt) return fail(NF_ERR_ARG, "null pointer argument");
+    if (prm && (!(prm->eta_acc > 0.0) || !(prm->hubble >= 0.0) || (prm->hubble > 0.0 && !(prm->eta_h > 0.0))))
+        return fail(NF_ERR_ARG, "step parameters need eta_acc > 0, hubble >= 0 and eta_h > 0 when hubble > 0");
+    rc = check_ws(p, ws, ws_bytes);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    NF_CUDA(launch_kick(vel, acc, (int)N, dt, 0.5, s), "kick");
+    NF_CUDA(launch_drift(pos, vel, (int)N, dt, (float)box, s), "drift");
+    rc = run_forces(p, false, t, pos, nullptr, acc, nullptr, nullptr, ws, s);
+    if (rc) return rc;
+    NF_CUDA(launch_kick(vel, acc, (int)N, dt, 0.5, s), "kick");
+    if (prm)
+        NF_CUDA(launch_timestep(at<int32_t>(ws, p.o_off), at<int32_t>(ws, p.o_perm), vel, acc, (int)p.C, (long long)N,
+                                prm->eta_acc, prm->eta_h, prm->hubble, at<StepScratch>(ws, p.o_step), dt, s),
+                "time step");
+    return NF_OK;
 }
 
 int nf_status_read(void* ws, void* stream)

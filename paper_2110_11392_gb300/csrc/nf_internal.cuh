@@ -67,6 +67,15 @@ struct BoxFill {
 constexpr int kCombineChunk = 4096;  // particles per combine block (never straddles boxes)
 constexpr int kBuckets = 64;         // cost buckets of the LPT work order
 
+// Scratch of the time-step reduction (nf_step.cu).
+constexpr int kStepBlocks = 256;
+struct StepScratch {
+    unsigned min_ratio_bits;  // smallest per-cell v_rms / a_max (bits of a positive float)
+    unsigned max_a2_bits;     // largest |a|^2 (bits of a positive float)
+    unsigned pad[62];
+    double v2_block[kStepBlocks];  // per-block FP64 sums of |v|^2
+};
+
 // Counts kernel launches (all translation units).
 void count_launches(int n);
 // Sets the dynamic shared-memory limit of a kernel once per (device, size).
@@ -123,6 +132,13 @@ cudaError_t launch_combine(bool adjoint, const BoxDev* boxes, int nboxes, int nc
 cudaError_t launch_net(const BoxDev* boxes, int nboxes, const double* chunk_sums,
                        double* net, cudaStream_t s);
 bool force_tuning_supported(const ForceTuning& t);
+
+// ---- time stepping (nf_step.cu) ----
+cudaError_t launch_kick(float* vel, const float* acc, int N, const double* dt, double factor, cudaStream_t s);
+cudaError_t launch_drift(float* pos, const float* vel, int N, const double* dt, float box, cudaStream_t s);
+cudaError_t launch_timestep(const int* off, const int* perm, const float* vel, const float* acc, int C, long long N,
+                            double eta_acc, double eta_h, double hubble, StepScratch* st, double* dt,
+                            cudaStream_t s);
 int force_blocks_per_sm(bool adjoint, bool density, const ForceTuning& t, int max_nseg);
 
 }  // namespace nf
