@@ -26,6 +26,8 @@ binning's rounding.  Each function below cites what it follows in the paper
   and limited by the Hubble term.
 * :func:`kdk_step` - one Kick-Drift-Kick leapfrog step (Sec. "Time
   Stepping") with the near-field accelerations of :func:`forces`.
+* :func:`multipoles` - cell multipoles in the complete basis, Eq. (multipoles)
+  (Sec. "Computation of the Cell Multipoles"), about the cell centres.
 * :func:`density` - the apodized top-hat density estimate the paper's kernel
   accumulates as a 4th component, sum over near-field j with r < b of
   (1 - r^2/b^2) (Sec. "Force Kernel").
@@ -78,6 +80,10 @@ def _load():
     lib.oracle_local_energy.argtypes = [P, P, i64, f64, i32, i32, f64, P, i64, P, P]
     lib.oracle_density.restype = i32
     lib.oracle_density.argtypes = [P, i64, f64, i32, i32, f64, P, i64, P, i32]
+    lib.oracle_multipoles.restype = i32
+    lib.oracle_multipoles.argtypes = [P, i64, f64, i32, i32, P]
+    lib.oracle_multipole_terms.restype = i64
+    lib.oracle_multipole_terms.argtypes = [i32]
     lib.oracle_wrapped_positions.restype = i32
     lib.oracle_wrapped_positions.argtypes = [P, i64, f64, i32, P]
     lib.oracle_num_threads.restype = i32
@@ -163,6 +169,28 @@ def adjoint(pos, g, box: float, K: int, R: int, eps: float,
     if rc:
         raise ValueError("non-finite coordinates")
     return out[:n]
+
+
+def multipole_terms(p: int) -> int:
+    return int(_load().oracle_multipole_terms(int(p)))
+
+
+def multipole_index(p: int):
+    """(a, b, c) of every complete-basis term, in the order of the output."""
+    return [(a, b, c) for a in range(p + 1) for b in range(p + 1 - a) for c in range(p + 1 - a - b)]
+
+
+def multipoles(pos, box: float, K: int, p: int) -> np.ndarray:
+    """M[cell, term] = sum over the cell's particles of x^a y^b z^c, FP64, with
+    (x, y, z) the displacement from the cell centre in box units; terms in the
+    order of multipole_index(p)."""
+    pos = _pos(pos)
+    N = pos.shape[0]
+    nt = multipole_terms(p)
+    M = np.zeros((K ** 3, nt), np.float64)
+    if _load().oracle_multipoles(_p(pos), N, float(box), int(K), int(p), _p(M)):
+        raise ValueError("non-finite coordinates")
+    return M
 
 
 def density(pos, box: float, K: int, R: int, b: float,

@@ -31,6 +31,10 @@
  *     with r_ij < b of (1 - r_ij^2 / b^2), the particle itself included
  *     (it contributes 1).  The kernel accumulates b^2 - r^2; this is that sum
  *     divided by b^2.
+ *   - Cell multipoles in the complete basis, Eq. (multipoles) in Sec.
+ *     "Computation of the Cell Multipoles": M^{abc} = sum_q x_q^a y_q^b z_q^c
+ *     over the particles of a cell, a + b + c <= p, with (x, y, z) the
+ *     displacement from the cell centre in box units (unit masses).
  *   - The adjoint (the gradient of L = sum_i g_i . a_i with respect to the
  *     positions), which the paper does not give; it is the derivative of the
  *     sum above: dL/dx_i = m sum_j J(d_ij) (g_j - g_i) with J(d) the Jacobian
@@ -385,6 +389,53 @@ int oracle_density(const float *pos, int64_t N, double box, int K, int R, double
         out[q] = ctx.rho;
     }
     oracle_grid_free(&g);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Cell multipoles (complete basis)                                           */
+/* ------------------------------------------------------------------------- */
+
+/* Number of complete-basis terms of order p: (p+3)(p+2)(p+1)/6. */
+int64_t oracle_multipole_terms(int p)
+{
+    return (int64_t)(p + 3) * (p + 2) * (p + 1) / 6;
+}
+
+/* M[cell][term] for every cell, terms ordered a (0..p), then b (0..p-a), then
+ * c (0..p-a-b).  The displacement of a particle from its cell centre is
+ * x_wrapped - (cell + 1/2) * box / K per axis, in FP64. */
+int oracle_multipoles(const float *pos, int64_t N, double box, int K, int p, double *M)
+{
+    const int64_t nt = oracle_multipole_terms(p);
+    const int64_t ncell = (int64_t)K * K * K;
+    memset(M, 0, sizeof(double) * (size_t)(ncell * nt));
+    const double kl = (double)K / box;
+    const double w = box / (double)K;
+    for (int64_t i = 0; i < N; ++i) {
+        int cell[3];
+        double disp[3];
+        for (int d = 0; d < 3; ++d) {
+            int c = 0;
+            float o = 0.0f;
+            double wrap = 0.0;
+            if (oracle_coord(pos[3 * i + d], kl, K, &c, &o, &wrap)) return 1;
+            double xw = (double)pos[3 * i + d] - wrap * box;
+            cell[d] = c;
+            disp[d] = xw - ((double)c + 0.5) * w;
+        }
+        double *m = &M[(((int64_t)cell[0] * K + cell[1]) * K + cell[2]) * nt];
+        int64_t t = 0;
+        for (int a = 0; a <= p; ++a)
+            for (int b = 0; b <= p - a; ++b)
+                for (int c = 0; c <= p - a - b; ++c) {
+                    double v = 1.0;
+                    for (int e = 0; e < a; ++e) v *= disp[0];
+                    for (int e = 0; e < b; ++e) v *= disp[1];
+                    for (int e = 0; e < c; ++e) v *= disp[2];
+                    m[t++] += v;
+                }
+    }
     return 0;
 }
 

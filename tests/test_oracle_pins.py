@@ -496,3 +496,57 @@ def test_kdk_conserves_momentum_and_moves_free_particles_straight():
     xl, vl2, _ = oracle.kdk_step(lone, vl, np.zeros((1, 3)), 0.25, 1.0, 5, 2, 0.004)
     assert np.array_equal(vl2, vl)
     assert np.allclose(xl, [[0.225, 0.1375, 0.33125]], rtol=0, atol=1e-7)
+
+
+# --------------------------------------------------------------------------
+# cell multipoles, Eq. (multipoles) (complete basis about the cell centre)
+# --------------------------------------------------------------------------
+
+def test_multipole_term_count_and_order():
+    for p in (0, 1, 4, 8, 16):
+        assert oracle.multipole_terms(p) == (p + 3) * (p + 2) * (p + 1) // 6 == len(oracle.multipole_index(p))
+    idx = oracle.multipole_index(2)
+    assert idx[:4] == [(0, 0, 0), (0, 0, 1), (0, 0, 2), (0, 1, 0)]
+
+
+def test_multipoles_single_particle_exact():
+    """One particle at a dyadic displacement (1/64, -1/32, 3/128) from the centre
+    of cell (2, 5, 1) on K = 8: every term is an exact product of powers."""
+    K, p = 8, 6
+    d = np.array([1 / 64, -1 / 32, 3 / 128])
+    x = ((np.array([2, 5, 1]) + 0.5) / K + d).astype(np.float32)
+    M = oracle.multipoles(x[None, :], 1.0, K, p)
+    cell = (2 * K + 5) * K + 1
+    for t, (a, b, c) in enumerate(oracle.multipole_index(p)):
+        assert M[cell, t] == d[0] ** a * d[1] ** b * d[2] ** c
+    assert np.count_nonzero(M.sum(axis=1)) == 1
+
+
+def test_multipoles_monopole_is_the_count_and_trace_is_r2():
+    rng = np.random.default_rng(41)
+    K, p = 5, 4
+    x = rng.random((3000, 3)).astype(np.float32)
+    M = oracle.multipoles(x, 1.0, K, p)
+    idx = oracle.multipole_index(p)
+    c = np.floor(x.astype(np.float64) * K).astype(int)
+    cid = (c[:, 0] * K + c[:, 1]) * K + c[:, 2]
+    assert np.array_equal(M[:, idx.index((0, 0, 0))], np.bincount(cid, minlength=K ** 3).astype(float))
+    disp = x.astype(np.float64) - (c + 0.5) / K
+    r2 = np.bincount(cid, weights=(disp ** 2).sum(axis=1), minlength=K ** 3)
+    tr = M[:, idx.index((2, 0, 0))] + M[:, idx.index((0, 2, 0))] + M[:, idx.index((0, 0, 2))]
+    assert np.allclose(tr, r2, rtol=1e-13, atol=0)
+
+
+def test_multipoles_match_numpy_powers():
+    rng = np.random.default_rng(42)
+    K, p = 4, 8
+    x = rng.random((500, 3)).astype(np.float32)
+    M = oracle.multipoles(x, 1.0, K, p)
+    c = np.floor(x.astype(np.float64) * K).astype(int)
+    cid = (c[:, 0] * K + c[:, 1]) * K + c[:, 2]
+    disp = x.astype(np.float64) - (c + 0.5) / K
+    for t, (a, b, cc) in enumerate(oracle.multipole_index(p)):
+        mono = np.power(disp[:, 0], a) * np.power(disp[:, 1], b) * np.power(disp[:, 2], cc)
+        ref = np.bincount(cid, weights=mono, minlength=K ** 3)
+        scale = np.bincount(cid, weights=np.abs(mono), minlength=K ** 3) + 1e-300
+        assert np.all(np.abs(M[:, t] - ref) <= 1e-13 * scale)
