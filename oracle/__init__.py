@@ -182,8 +182,9 @@ def multipole_index(p: int):
 
 def multipoles(pos, box: float, K: int, p: int) -> np.ndarray:
     """M[cell, term] = sum over the cell's particles of x^a y^b z^c, FP64, with
-    (x, y, z) the displacement from the cell centre in box units; terms in the
-    order of multipole_index(p)."""
+    (x, y, z) the displacement from the cell centre in box units (the stored
+    FP32 cell-centred offset times the cell width); terms in the order of
+    multipole_index(p)."""
     pos = _pos(pos)
     N = pos.shape[0]
     nt = multipole_terms(p)

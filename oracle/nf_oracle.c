@@ -34,7 +34,10 @@
  *   - Cell multipoles in the complete basis, Eq. (multipoles) in Sec.
  *     "Computation of the Cell Multipoles": M^{abc} = sum_q x_q^a y_q^b z_q^c
  *     over the particles of a cell, a + b + c <= p, with (x, y, z) the
- *     displacement from the cell centre in box units (unit masses).
+ *     displacement from the cell centre in box units (unit masses), taken
+ *     from the particle's stored FP32 cell-centred offset times the cell
+ *     width: the paper's particle state is that offset (Sec. "Force
+ *     Accuracy", overview).
  *   - The adjoint (the gradient of L = sum_i g_i . a_i with respect to the
  *     positions), which the paper does not give; it is the derivative of the
  *     sum above: dL/dx_i = m sum_j J(d_ij) (g_j - g_i) with J(d) the Jacobian
@@ -403,8 +406,8 @@ int64_t oracle_multipole_terms(int p)
 }
 
 /* M[cell][term] for every cell, terms ordered a (0..p), then b (0..p-a), then
- * c (0..p-a-b).  The displacement of a particle from its cell centre is
- * x_wrapped - (cell + 1/2) * box / K per axis, in FP64. */
+ * c (0..p-a-b).  The displacement of a particle from its cell centre is its
+ * FP32 cell-centred offset (the binning above) times box / K, in FP64. */
 int oracle_multipoles(const float *pos, int64_t N, double box, int K, int p, double *M)
 {
     const int64_t nt = oracle_multipole_terms(p);
@@ -420,9 +423,8 @@ int oracle_multipoles(const float *pos, int64_t N, double box, int K, int p, dou
             float o = 0.0f;
             double wrap = 0.0;
             if (oracle_coord(pos[3 * i + d], kl, K, &c, &o, &wrap)) return 1;
-            double xw = (double)pos[3 * i + d] - wrap * box;
             cell[d] = c;
-            disp[d] = xw - ((double)c + 0.5) * w;
+            disp[d] = (double)o * w;
         }
         double *m = &M[(((int64_t)cell[0] * K + cell[1]) * K + cell[2]) * nt];
         int64_t t = 0;

@@ -522,10 +522,16 @@ def test_multipoles_single_particle_exact():
     assert np.count_nonzero(M.sum(axis=1)) == 1
 
 
+def _dyadic_positions(rng, n):
+    """Positions on a 2^-20 grid: their cell offsets are exact in FP32, so the
+    stored offset and the exact displacement from the centre coincide."""
+    return (rng.integers(0, 1 << 20, size=(n, 3)) / float(1 << 20)).astype(np.float32)
+
+
 def test_multipoles_monopole_is_the_count_and_trace_is_r2():
     rng = np.random.default_rng(41)
-    K, p = 5, 4
-    x = rng.random((3000, 3)).astype(np.float32)
+    K, p = 4, 4
+    x = _dyadic_positions(rng, 3000)
     M = oracle.multipoles(x, 1.0, K, p)
     idx = oracle.multipole_index(p)
     c = np.floor(x.astype(np.float64) * K).astype(int)
@@ -540,7 +546,7 @@ def test_multipoles_monopole_is_the_count_and_trace_is_r2():
 def test_multipoles_match_numpy_powers():
     rng = np.random.default_rng(42)
     K, p = 4, 8
-    x = rng.random((500, 3)).astype(np.float32)
+    x = _dyadic_positions(rng, 500)
     M = oracle.multipoles(x, 1.0, K, p)
     c = np.floor(x.astype(np.float64) * K).astype(int)
     cid = (c[:, 0] * K + c[:, 1]) * K + c[:, 2]
