@@ -340,6 +340,7 @@ def run_native(args, rank, world, local):
 
     out["density"] = measure_density(w, pos, ws, acc, fwd_pair_ms, flush)
     out["kdk"] = measure_kdk(w, dev, flush)
+    out["multipoles"] = measure_multipoles(w, pos, dev, flush)
     if not args.no_e2e:
         out["e2e"] = measure_e2e(args, w, g_np, dev, P, flush)
     if not args.no_batched:
@@ -409,6 +410,30 @@ def measure_kdk(w, dev, flush, steps=5):
     t = float(np.mean(ms))
     return {"ms_per_step": t, "particle_updates_per_s": w.N / (t / 1e3), "last_dt": float(dt.item()),
             "steps": steps, "note": "kick + drift + nf_forces + kick + Eq. (timestep), near field only"}
+
+
+def measure_multipoles(w, pos, dev, flush, p=8, reps=3):
+    """Complete-basis cell multipoles at order p (FP64): binning + nf_multipoles."""
+    import torch
+    from paper_2110_11392_gb300 import _lib
+    nt = (p + 3) * (p + 2) * (p + 1) // 6
+    M = torch.empty((w.K ** 3, nt), dtype=torch.float64, device=dev)
+    ws = torch.empty(_lib.nf_workspace_bytes(w.N, w.K, w.R), dtype=torch.uint8, device=dev)
+    _lib.nf_multipoles(pos, w.box, w.K, p, M, ws)
+    stream = torch.cuda.current_stream(dev)
+    ms = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _lib.nf_multipoles(pos, w.box, w.K, p, M, ws)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = float(np.mean(ms)) / 1e3
+    flop = w.N * (3 * p + 3 * nt)  # powers, then a multiply and an FMA per term
+    return {"order": p, "terms": nt, "ms": t * 1e3, "particles_per_s": w.N / t,
+            "fp64_tflops": flop / t / 1e12, "note": "includes binning; FP64 throughout"}
 
 
 def measure_e2e(args, w, g_np, dev, P, flush):

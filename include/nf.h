@@ -243,6 +243,23 @@ int nf_forces_noalloc(const float *pos, int64_t N, double box, int K, int R, dou
                       float *acc, double *net, void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* Cell multipoles (Sec. "Computation of the Cell Multipoles")               */
+/* ------------------------------------------------------------------------ */
+
+#define NF_MAX_MULTIPOLE_ORDER 16
+
+/* Complete-basis multipoles of every cell, Eq. (multipoles), in FP64:
+ *     M[cell][t] = sum over the particles q of the cell of x_q^a y_q^b z_q^c,
+ * (x, y, z) the displacement of q from the centre of its cell in box units
+ * (unit masses; multiply by the particle mass for mass moments).  Terms t run
+ * over a = 0..p, then b = 0..p-a, then c = 0..p-a-b; there are
+ * (p+3)(p+2)(p+1)/6 of them.  The particles are binned first (as nf_bin);
+ * cells are numbered (cx*K + cy)*K + cz.  M is [K^3][(p+3)(p+2)(p+1)/6]
+ * doubles in device memory; 0 <= p <= NF_MAX_MULTIPOLE_ORDER. */
+int nf_multipoles(const float *pos, int64_t N, double box, int K, int p, double *M,
+                  void *ws, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* Time stepping (Sec. "Time Stepping": Kick-Drift-Kick leapfrog with a      */
 /* global time step, Eq. (timestep))                                         */
 /* ------------------------------------------------------------------------ */

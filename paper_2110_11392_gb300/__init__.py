@@ -13,6 +13,7 @@ from .nearfield import (
     forces,
     forces_adjoint,
     forces_density,
+    multipoles,
     near_field,
     stats,
     status,
@@ -31,6 +32,7 @@ __all__ = [
     "forces",
     "forces_adjoint",
     "forces_density",
+    "multipoles",
     "near_field",
     "stats",
     "status",

@@ -88,6 +88,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         "nf_forces_density": (i32, [P, i64, f64, i32, i32, f64, f64, P, P, P, sz, P]),
         "nf_timestep": (i32, [P, P, P, i64, f64, i32, P, P, P, sz, P]),
         "nf_kdk_step": (i32, [P, P, P, i64, f64, i32, i32, f64, P, P, P, sz, P]),
+        "nf_multipoles": (i32, [P, i64, f64, i32, i32, P, P, sz, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -103,7 +104,7 @@ def exported_symbols() -> Sequence[str]:
             "nf_forces_adjoint_batched", "nf_set_default_tuning", "nf_get_default_tuning",
             "nf_status_read", "nf_stats_read", "nf_profile_enable", "nf_profile_read",
             "nf_kernel_launches", "nf_forces_noalloc", "nf_forces_density", "nf_timestep",
-            "nf_kdk_step")
+            "nf_kdk_step", "nf_multipoles")
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -276,3 +277,10 @@ def nf_kdk_step(pos: torch.Tensor, vel: torch.Tensor, acc: torch.Tensor, box: fl
                               float(eps), _ptr(dt), ctypes.byref(prm) if prm is not None else None, _ptr(ws),
                               ws.numel() * ws.element_size(), _stream(stream)),
            "nf_kdk_step")
+
+
+def nf_multipoles(pos: torch.Tensor, box: float, K: int, p: int, M: torch.Tensor, ws: torch.Tensor,
+                  stream=None) -> None:
+    _check(load().nf_multipoles(_ptr(pos), pos.shape[0], float(box), int(K), int(p), _ptr(M), _ptr(ws),
+                                ws.numel() * ws.element_size(), _stream(stream)),
+           "nf_multipoles")

@@ -585,6 +585,27 @@ int nf_kdk_step(float* pos, float* vel, float* acc, int64_t N, double box, int K
     return NF_OK;
 }
 
+int nf_multipoles(const float* pos, int64_t N, double box, int K, int p, double* M, void* ws, size_t ws_bytes,
+                  void* stream)
+{
+    g_last_error.clear();
+    nf_box b = one_box(N, box, K, 0, 0.0);
+    Plan pl;
+    int rc = make_plan(&b, 1, false, 32, &pl);
+    if (rc) return rc;
+    if (p < 0 || p > NF_MAX_MULTIPOLE_ORDER) return fail(NF_ERR_ARG, "multipole order p = %d out of [0, %d]", p, NF_MAX_MULTIPOLE_ORDER);
+    if (!pos || !M) return fail(NF_ERR_ARG, "null pointer argument");
+    rc = check_ws(pl, ws, ws_bytes);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int32_t* off = at<int32_t>(ws, pl.o_off);
+    float4* rel = at<float4>(ws, pl.o_rel);
+    rc = run_binning(pl, pos, ws, off, rel, at<int32_t>(ws, pl.o_perm), s);
+    if (rc) return rc;
+    NF_CUDA(launch_multipoles(off, rel, (int)pl.C, box / K, p, M, s), "multipoles");
+    return NF_OK;
+}
+
 int nf_status_read(void* ws, void* stream)
 {
     g_last_error.clear();

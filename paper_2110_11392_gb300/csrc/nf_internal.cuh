@@ -133,6 +133,10 @@ cudaError_t launch_net(const BoxDev* boxes, int nboxes, const double* chunk_sums
                        double* net, cudaStream_t s);
 bool force_tuning_supported(const ForceTuning& t);
 
+// ---- cell multipoles (nf_multipole.cu) ----
+int multipole_terms(int p);
+cudaError_t launch_multipoles(const int* off, const float4* rel, int C, double w, int p, double* M, cudaStream_t s);
+
 // ---- time stepping (nf_step.cu) ----
 cudaError_t launch_kick(float* vel, const float* acc, int N, const double* dt, double factor, cudaStream_t s);
 cudaError_t launch_drift(float* pos, const float* vel, int N, const double* dt, float box, cudaStream_t s);

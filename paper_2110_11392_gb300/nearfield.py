@@ -99,6 +99,17 @@ def forces_adjoint(pos: torch.Tensor, g: torch.Tensor, box: float, K: int, R: in
     return grad
 
 
+def multipoles(pos: torch.Tensor, box: float, K: int, p: int, ws: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Complete-basis cell multipoles (nf_multipoles): float64 [K^3, (p+3)(p+2)(p+1)/6]."""
+    pos = _check_pos(pos)
+    N = pos.shape[0]
+    if ws is None:
+        ws = workspace(_lib.nf_workspace_bytes(N, max(K, 5), 2), pos.device)
+    M = torch.empty((K ** 3, (p + 3) * (p + 2) * (p + 1) // 6), dtype=torch.float64, device=pos.device)
+    _lib.nf_multipoles(pos, box, K, p, M, ws)
+    return M
+
+
 def status(ws: Optional[torch.Tensor] = None, N: int = 1, K: int = 5, R: int = 2) -> int:
     """Device status of the last call on the default workspace (synchronises)."""
     if ws is None:
