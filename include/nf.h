@@ -60,7 +60,8 @@ typedef enum {
     NF_ERR_CUDA = 2,       /* a CUDA runtime call failed */
     NF_ERR_WORKSPACE = 3,  /* ws is NULL or ws_bytes is below the required size */
     NF_ERR_NONFINITE = 4,  /* device status: a coordinate was NaN or infinite */
-    NF_ERR_TIMEOUT = 5     /* device status: a bounded device-side wait gave up */
+    NF_ERR_TIMEOUT = 5,    /* device status: a bounded device-side wait gave up */
+    NF_ERR_CORRUPT = 6     /* device status (debug mode): a workspace guard block was overwritten */
 } nf_status;
 
 /* Message for the last non-OK return on the calling thread ("" if none). */
@@ -299,9 +300,22 @@ int nf_kdk_step(float *pos, float *vel, float *acc, int64_t N, double box, int K
 /* Status and statistics                                                     */
 /* ------------------------------------------------------------------------ */
 
+/* Debug mode (process-wide, off by default): every workspace region is
+ * followed by a 256-byte guard block, so workspace sizes grow - size
+ * workspaces after switching it.  Each call fills the guards when it starts
+ * and checks them when it ends; an overwritten guard (an out-of-bounds write
+ * by a kernel, or by anyone else) sets NF_ERR_CORRUPT in the status word.
+ * This stands in for a memory checker where none can run. */
+int nf_set_debug(int on);
+
+/* Debug mode: checks the guard blocks of `ws` now (enqueued on `stream`);
+ * read the result with nf_status_read.  NF_ERR_ARG if debug mode is off. */
+int nf_debug_check(void *ws, void *stream);
+
 /* Synchronises `stream`, then returns the device status word of the last call
- * that used `ws` (NF_OK, NF_ERR_NONFINITE or NF_ERR_TIMEOUT), or NF_ERR_CUDA
- * if synchronisation failed.  Every call clears the word when it starts. */
+ * that used `ws` (NF_OK, NF_ERR_NONFINITE, NF_ERR_TIMEOUT or NF_ERR_CORRUPT),
+ * or NF_ERR_CUDA if synchronisation failed.  Every call clears the word when
+ * it starts. */
 int nf_status_read(void *ws, void *stream);
 
 /* Statistics of the last call that used `ws`, copied to the host after a

@@ -15,10 +15,10 @@ import torch
 
 from . import _build
 
-NF_OK, NF_ERR_ARG, NF_ERR_CUDA, NF_ERR_WORKSPACE, NF_ERR_NONFINITE, NF_ERR_TIMEOUT = range(6)
+NF_OK, NF_ERR_ARG, NF_ERR_CUDA, NF_ERR_WORKSPACE, NF_ERR_NONFINITE, NF_ERR_TIMEOUT, NF_ERR_CORRUPT = range(7)
 NF_MAX_R = 4
 STATUS_NAMES = {0: "NF_OK", 1: "NF_ERR_ARG", 2: "NF_ERR_CUDA", 3: "NF_ERR_WORKSPACE",
-                4: "NF_ERR_NONFINITE", 5: "NF_ERR_TIMEOUT"}
+                4: "NF_ERR_NONFINITE", 5: "NF_ERR_TIMEOUT", 6: "NF_ERR_CORRUPT"}
 
 
 class NFError(RuntimeError):
@@ -89,6 +89,8 @@ def load(build: bool = True) -> ctypes.CDLL:
         "nf_timestep": (i32, [P, P, P, i64, f64, i32, P, P, P, sz, P]),
         "nf_kdk_step": (i32, [P, P, P, i64, f64, i32, i32, f64, P, P, P, sz, P]),
         "nf_multipoles": (i32, [P, i64, f64, i32, i32, P, P, sz, P]),
+        "nf_set_debug": (i32, [i32]),
+        "nf_debug_check": (i32, [P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -104,7 +106,7 @@ def exported_symbols() -> Sequence[str]:
             "nf_forces_adjoint_batched", "nf_set_default_tuning", "nf_get_default_tuning",
             "nf_status_read", "nf_stats_read", "nf_profile_enable", "nf_profile_read",
             "nf_kernel_launches", "nf_forces_noalloc", "nf_forces_density", "nf_timestep",
-            "nf_kdk_step", "nf_multipoles")
+            "nf_kdk_step", "nf_multipoles", "nf_set_debug", "nf_debug_check")
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -284,3 +286,11 @@ def nf_multipoles(pos: torch.Tensor, box: float, K: int, p: int, M: torch.Tensor
     _check(load().nf_multipoles(_ptr(pos), pos.shape[0], float(box), int(K), int(p), _ptr(M), _ptr(ws),
                                 ws.numel() * ws.element_size(), _stream(stream)),
            "nf_multipoles")
+
+
+def nf_set_debug(on: bool) -> None:
+    _check(load().nf_set_debug(1 if on else 0), "nf_set_debug")
+
+
+def nf_debug_check(ws: torch.Tensor, stream=None) -> None:
+    _check(load().nf_debug_check(_ptr(ws), _stream(stream)), "nf_debug_check")

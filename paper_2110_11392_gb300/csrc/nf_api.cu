@@ -48,6 +48,41 @@ namespace {
 
 thread_local std::string g_last_error;
 
+// Debug mode: guard blocks after every workspace region, filled when a call
+// starts and checked when it ends (process-wide; off by default).
+bool g_debug = false;
+
+struct GuardList {
+    int count;
+    long long off[24];
+};
+
+__global__ void k_guard_setup(void* ws, GuardList gl)
+{
+    WsHeader* h = static_cast<WsHeader*>(ws);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        h->guard_count = gl.count;
+        for (int i = 0; i < gl.count; ++i) h->guard_off[i] = gl.off[i];
+    }
+    const int g = blockIdx.x;
+    if (g < gl.count) {
+        unsigned* w = reinterpret_cast<unsigned*>(static_cast<char*>(ws) + gl.off[g]);
+        for (int i = threadIdx.x; i < kGuardBytes / 4; i += blockDim.x) w[i] = kGuardWord;
+    }
+}
+
+__global__ void k_guard_check(void* ws)
+{
+    WsHeader* h = static_cast<WsHeader*>(ws);
+    const int n = h->guard_count;
+    const int g = blockIdx.x;
+    if (g >= n) return;
+    const unsigned* w = reinterpret_cast<const unsigned*>(static_cast<const char*>(ws) + h->guard_off[g]);
+    bool bad = false;
+    for (int i = threadIdx.x; i < kGuardBytes / 4; i += blockDim.x) bad |= w[i] != kGuardWord;
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&h->status, 1 << NF_ERR_CORRUPT);
+}
+
 // Per-stage profiling events of the last NF_PROFILE_RING calls (process-wide;
 // off by default).  g_prof_count counts completed profiled calls.
 bool g_profile_on = false;
@@ -100,6 +135,7 @@ struct Plan {
     // region offsets (bytes from ws)
     size_t o_boxes, o_keys_a, o_keys_b, o_vals_a, o_vals_b, o_off, o_hist, o_aux, o_rel, o_perm,
         o_chunks, o_bucket_of, o_bucket_count, o_items, o_gs, o_partial, o_chunk_sums, o_step, total;
+    std::vector<size_t> guards;  // debug mode: guard block after each region
 };
 
 // Validates one box; fills the device constants.
@@ -195,9 +231,14 @@ int make_plan(const nf_box* boxes, int nboxes, bool need_force, int chunk_lanes,
     p->rx = radix_plan(N, C);
 
     size_t o = 0;
+    p->guards.clear();
     auto take = [&](size_t bytes) {
         size_t at = o;
         o = align_up(o + bytes);
+        if (g_debug) {
+            p->guards.push_back(o);
+            o = align_up(o + kGuardBytes);
+        }
         return at;
     };
     take(sizeof(WsHeader));
@@ -257,12 +298,31 @@ int check_tuning(const nf_tuning* t, ForceTuning* out)
     } while (0)
 
 // Clears the header, uploads the box table, bins every particle.
+// Debug mode: check every guard block of the workspace at the end of a call.
+int finish_call(void* ws, cudaStream_t s)
+{
+    if (!g_debug) return NF_OK;
+    k_guard_check<<<24, 64, 0, s>>>(ws);
+    count_launches(1);
+    NF_CUDA(cudaGetLastError(), "guard check");
+    return NF_OK;
+}
+
 int run_binning(const Plan& p, const float* pos, void* ws, int32_t* cell_off, float4* rel, int32_t* perm,
                 cudaStream_t s)
 {
     WsHeader* hdr = at<WsHeader>(ws, 0);
     BoxDev* boxes = at<BoxDev>(ws, p.o_boxes);
     NF_CUDA(cudaMemsetAsync(hdr, 0, sizeof(WsHeader), s), "clear header");
+    if (g_debug && !p.guards.empty()) {
+        GuardList gl;
+        std::memset(&gl, 0, sizeof gl);
+        gl.count = (int)std::min<size_t>(p.guards.size(), 24);
+        for (int i = 0; i < gl.count; ++i) gl.off[i] = (long long)p.guards[i];
+        k_guard_setup<<<gl.count, 64, 0, s>>>(ws, gl);
+        count_launches(1);
+        NF_CUDA(cudaGetLastError(), "guard setup");
+    }
     NF_CUDA(cudaMemsetAsync(cell_off, 0, 4 * (size_t)(p.C + 1), s), "clear counts");
     for (int first = 0; first < p.nboxes; first += kMaxBoxesPerFill) {
         BoxFill f;
@@ -318,7 +378,7 @@ int run_forces(const Plan& p, bool adjoint, const ForceTuning& t, const float* p
     if (net) NF_CUDA(launch_net(boxes, p.nboxes, chunk_sums, net, s), "net force");
     NF_CUDA(prof_mark(4, s), "profile");
     if (g_profile_on) ++g_prof_count;
-    return NF_OK;
+    return finish_call(ws, s);
 }
 
 int check_ws(const Plan& p, void* ws, size_t ws_bytes)
@@ -443,8 +503,9 @@ int nf_bin(const float* pos, int64_t N, double box, int K, int32_t* cell_offsets
     // nf_bin needs only the binning regions, which precede the force regions
     rc = check_ws(p, ws, ws_bytes);
     if (rc) return rc;
-    return run_binning(p, pos, ws, cell_offsets, reinterpret_cast<float4*>(rel), perm,
-                       static_cast<cudaStream_t>(stream));
+    rc = run_binning(p, pos, ws, cell_offsets, reinterpret_cast<float4*>(rel), perm, static_cast<cudaStream_t>(stream));
+    if (rc) return rc;
+    return finish_call(ws, static_cast<cudaStream_t>(stream));
 }
 
 int nf_forces(const float* pos, int64_t N, double box, int K, int R, double eps, float* acc, double* net, void* ws,
@@ -553,7 +614,7 @@ int nf_timestep(const float* pos, const float* vel, const float* acc, int64_t N,
     NF_CUDA(launch_timestep(off, perm, vel, acc, (int)p.C, (long long)N, prm->eta_acc, prm->eta_h, prm->hubble,
                             at<StepScratch>(ws, p.o_step), dt, s),
             "time step");
-    return NF_OK;
+    return finish_call(ws, s);
 }
 
 int nf_kdk_step(float* pos, float* vel, float* acc, int64_t N, double box, int K, int R, double eps, double* dt,
@@ -582,7 +643,7 @@ int nf_kdk_step(float* pos, float* vel, float* acc, int64_t N, double box, int K
         NF_CUDA(launch_timestep(at<int32_t>(ws, p.o_off), at<int32_t>(ws, p.o_perm), vel, acc, (int)p.C, (long long)N,
                                 prm->eta_acc, prm->eta_h, prm->hubble, at<StepScratch>(ws, p.o_step), dt, s),
                 "time step");
-    return NF_OK;
+    return finish_call(ws, s);
 }
 
 int nf_multipoles(const float* pos, int64_t N, double box, int K, int p, double* M, void* ws, size_t ws_bytes,
@@ -603,7 +664,21 @@ int nf_multipoles(const float* pos, int64_t N, double box, int K, int p, double*
     rc = run_binning(pl, pos, ws, off, rel, at<int32_t>(ws, pl.o_perm), s);
     if (rc) return rc;
     NF_CUDA(launch_multipoles(off, rel, (int)pl.C, box / K, p, M, s), "multipoles");
+    return finish_call(ws, s);
+}
+
+int nf_set_debug(int on)
+{
+    g_debug = on != 0;
     return NF_OK;
+}
+
+int nf_debug_check(void* ws, void* stream)
+{
+    g_last_error.clear();
+    if (!ws) return fail(NF_ERR_WORKSPACE, "workspace is NULL");
+    if (!g_debug) return fail(NF_ERR_ARG, "debug mode is off: the workspace has no guard blocks");
+    return finish_call(ws, static_cast<cudaStream_t>(stream));
 }
 
 int nf_status_read(void* ws, void* stream)
@@ -617,6 +692,7 @@ int nf_status_read(void* ws, void* stream)
     if (e != cudaSuccess) return cuda_fail(e, "status read");
     if (bits & (1 << NF_ERR_NONFINITE)) return fail(NF_ERR_NONFINITE, "non-finite coordinates in the input");
     if (bits & (1 << NF_ERR_TIMEOUT)) return fail(NF_ERR_TIMEOUT, "a device-side wait timed out");
+    if (bits & (1 << NF_ERR_CORRUPT)) return fail(NF_ERR_CORRUPT, "a workspace guard block was overwritten");
     return NF_OK;
 }
 

@@ -53,9 +53,16 @@ struct WsHeader {
     int max_occ;         // largest cell occupancy
     unsigned long long pairs;       // sum over pencils of n_sink * n_src
     unsigned long long lane_pairs;  // sink lanes issued * n_src
-    int pad[56];
+    // debug mode: byte offsets of the guard blocks that follow each workspace region
+    int guard_count;
+    int pad0;
+    long long guard_off[24];
+    int pad1[6];
 };
 static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
+
+constexpr int kGuardBytes = 256;       // one guard block (debug mode)
+constexpr unsigned kGuardWord = 0xA5C3A5C3u;
 
 constexpr int kMaxBoxesPerFill = 32;
 struct BoxFill {
