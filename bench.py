@@ -306,7 +306,7 @@ def run_native(args, rank, world, local):
     max_mhz = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
     fp32_peak = sms * 128 * 2 * max_mhz * 1e6 / 1e12  # TFLOP/s, 128 FP32 lanes/SM, FMA = 2 flop
     achieved = FLOP_PER_PAIR * P / (fwd_pair_ms / 1e3) / 1e12
-    traffic = kernel_traffic("force")
+    traffic = kernel_traffic("force", args.workload)
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": traffic,
                 "kernel": "k_force (forward pair loop)",
@@ -317,7 +317,7 @@ def run_native(args, rank, world, local):
     hbm = peaks.get("hbm_gbs", 6786.2)
     bin_bytes = 32.0 * N + 8.0 * (w.K ** 3 + 1)
     bin_roof = {"bound": "hbm", "achieved": bin_bytes / (bin_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
-                "frac": bin_bytes / (bin_ms / 1e3) / 1e9 / hbm, "traffic": kernel_traffic("bin"),
+                "frac": bin_bytes / (bin_ms / 1e3) / 1e9 / hbm, "traffic": kernel_traffic("bin", args.workload),
                 "bytes_per_particle": 32, "note": "algorithmic bytes: pos 12 + rel 16 + perm 4 per particle + offsets"}
 
     out = {
@@ -532,13 +532,13 @@ def measure_batched(dev, flush, rank=0, world=1):
             "separate_ms": t_sep * 1e3}
 
 
-def kernel_traffic(which: str):
-    """DRAM bytes per launch from a committed ncu summary, if it matches the current source."""
+def kernel_traffic(which: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary of this workload, if it matches the current source."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        rec = json.load(open(path))[which]
-    except (OSError, ValueError, KeyError):
+        rec = json.load(open(path))[workload][which]
+    except (OSError, ValueError, KeyError, TypeError):
         return None
     src = os.path.join(ROOT, "paper_2110_11392_gb300", "csrc", rec.get("source", ""))
     try:
