@@ -212,9 +212,21 @@ def oracle_sample(w, g, seconds: float, seed: int = 22):
     oracle.adjoint(w.pos, g64, w.box, w.K, w.R, w.eps, sinks=sinks)
     dt = time.perf_counter() - t0
     pairs = 2 * int(S[cid[sinks]].sum())
-    return ({"value": pairs / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    cores = oracle.num_threads()
+    # the same oracle on one host core, on a smaller sample (about 3 s)
+    n1c = int(min(n, max(16, 3.0 / (b * max(cores, 1)))))
+    sk1 = np.sort(order[n:n + n1c]) if n + n1c <= w.N else np.sort(order[:n1c])
+    t0 = time.perf_counter()
+    oracle.forces(w.pos, w.box, w.K, w.R, w.eps, sinks=sk1, threads=1)
+    oracle.adjoint(w.pos, g64, w.box, w.K, w.R, w.eps, sinks=sk1, threads=1)
+    dt1 = time.perf_counter() - t0
+    pairs1 = 2 * int(S[cid[sk1]].sum())
+    return ({"value": pairs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
              "sample": f"forces + adjoint for {n} random sinks (seed {seed}) of {w.N}; "
-                       f"{pairs:.3e} pair interactions in {dt:.1f} s, FP64, OpenMP"},
+                       f"{pairs:.3e} pair interactions in {dt:.1f} s, FP64, OpenMP",
+             "one_core": {"value": pairs1 / dt1, "unit": UNIT, "cores": 1,
+                          "sample": f"forces + adjoint for {n1c} random sinks; "
+                                    f"{pairs1:.3e} pair interactions in {dt1:.1f} s"}},
             sinks, acc_ref)
 
 
@@ -306,6 +318,7 @@ def run_native(args, rank, world, local):
     max_mhz = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
     fp32_peak = sms * 128 * 2 * max_mhz * 1e6 / 1e12  # TFLOP/s, 128 FP32 lanes/SM, FMA = 2 flop
     achieved = FLOP_PER_PAIR * P / (fwd_pair_ms / 1e3) / 1e12
+    fma = measure_fma_peak(dev)
     traffic = kernel_traffic("force", args.workload)
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": traffic,
@@ -313,7 +326,9 @@ def run_native(args, rank, world, local):
                 "peak_basis": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x {max_mhz:.0f} MHz max SM clock",
                 "frac_at_sampled_clock": (achieved / (sms * 256 * clk["sm_mhz"] * 1e6 / 1e12)
                                           if clk.get("sm_mhz") else None),
-                "flop_per_pair": FLOP_PER_PAIR}
+                "flop_per_pair": FLOP_PER_PAIR,
+                "measured_fma_peak": fma,
+                "frac_of_measured_fma": achieved / max(fma["scalar_tflops"], fma["packed_tflops"])}
     hbm = peaks.get("hbm_gbs", 6786.2)
     bin_bytes = 32.0 * N + 8.0 * (w.K ** 3 + 1)
     bin_roof = {"bound": "hbm", "achieved": bin_bytes / (bin_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
@@ -361,6 +376,36 @@ def run_native(args, rank, world, local):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out))
+
+
+def measure_fma_peak(dev, target_ms=40.0, reps=3):
+    """FP32 multiply-add throughput of this GPU (nf_fma_probe), scalar and packed
+    f32x2, timed with events on the launching stream: the measured denominator
+    beside the derived FP32 peak."""
+    import torch
+    from paper_2110_11392_gb300 import _lib
+    sink = torch.empty(_lib.nf_fma_probe_sink_floats(), dtype=torch.float32, device=dev)
+    s = torch.cuda.current_stream(dev)
+    out = {}
+    for packed in (False, True):
+        def timed(iters):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            flop = _lib.nf_fma_probe(sink, iters, packed, s)
+            e1.record(s)
+            e1.synchronize()
+            return flop, e0.elapsed_time(e1)
+        timed(256)
+        flop, ms = timed(2048)
+        iters = int(min(1 << 24, max(2048, 2048 * target_ms / max(ms, 1e-3))))
+        best = 0.0
+        for _ in range(reps):
+            flop, ms = timed(iters)
+            best = max(best, flop / (ms / 1e3) / 1e12)
+        out["packed_tflops" if packed else "scalar_tflops"] = best
+    out["unit"] = "TFLOP/s"
+    out["probe"] = "nf_fma_probe: 4 x 256 threads per SM, 8 independent multiply-add chains per thread, best of 3"
+    return out
 
 
 def measure_density(w, pos, ws, acc, fwd_pair_ms, flush):

@@ -363,6 +363,23 @@ int nf_profile_read(int back, nf_profile *out);
 /* Number of kernels libnf has launched in this process (all entry points). */
 int64_t nf_kernel_launches(void);
 
+/* ---- Measurement aid (no counterpart in the paper) ----------------------
+ * FP32 multiply-add throughput probe, the measured denominator beside the
+ * derived FP32 peak (SMs x 128 lanes x 2 flop x clock) of the pair kernels'
+ * roofline.  Launches one kernel of 4 blocks of 256 threads per SM; every
+ * thread runs 8 independent multiply-add chains for iters x 16 trips, as
+ * scalar fma.rn.f32 (packed = 0) or packed fma.rn.f32x2 (packed != 0).
+ *   sink   device float buffer of at least nf_fma_probe_sink_floats() values,
+ *          caller-owned; receives one value per thread (keeps the work live)
+ *   iters  1 .. 2^24
+ *   flop   host double; receives the floating-point operations the launch
+ *          performs (2 per multiply-add and lane)
+ * The call is asynchronous on `stream`; time it with events on that stream.
+ * Returns NF_ERR_ARG for NULL pointers or iters out of range, NF_ERR_CUDA if
+ * the launch fails. */
+size_t nf_fma_probe_sink_floats(void);
+int nf_fma_probe(float *sink, int iters, int packed, double *flop, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -286,8 +286,7 @@ int oracle_forces(const float *pos, int64_t N, double box, int K, int R, double 
     }
     int64_t n = sinks ? nsinks : N;
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 16)
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
 #endif
     for (int64_t q = 0; q < n; ++q) {
         int64_t i = sinks ? sinks[q] : q;
@@ -334,8 +333,7 @@ int oracle_adjoint(const float *pos, const double *gvec, int64_t N, double box, 
     }
     int64_t n = sinks ? nsinks : N;
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 16)
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
 #endif
     for (int64_t q = 0; q < n; ++q) {
         int64_t i = sinks ? sinks[q] : q;
@@ -382,8 +380,7 @@ int oracle_density(const float *pos, int64_t N, double box, int K, int R, double
     }
     int64_t n = sinks ? nsinks : N;
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 16)
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
 #endif
     for (int64_t q = 0; q < n; ++q) {
         int64_t i = sinks ? sinks[q] : q;

@@ -1,6 +1,6 @@
 """Builds libnf.so in-tree with nvcc for sm_103a (GB300).
 
-The three translation units are compiled in parallel and linked into
+The translation units are compiled in parallel and linked into
 ``paper_2110_11392_gb300/libnf.so`` (static CUDA runtime, C ABI only).  The
 build is skipped when the library is newer than every source.
 """
@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libnf.so")
-SOURCES = ["nf_bin.cu", "nf_force.cu", "nf_step.cu", "nf_multipole.cu", "nf_api.cu"]
+SOURCES = ["nf_bin.cu", "nf_force.cu", "nf_step.cu", "nf_multipole.cu", "nf_probe.cu", "nf_api.cu"]
 HEADERS = ["nf_internal.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

@@ -91,6 +91,8 @@ def load(build: bool = True) -> ctypes.CDLL:
         "nf_multipoles": (i32, [P, i64, f64, i32, i32, P, P, sz, P]),
         "nf_set_debug": (i32, [i32]),
         "nf_debug_check": (i32, [P, P]),
+        "nf_fma_probe_sink_floats": (sz, []),
+        "nf_fma_probe": (i32, [P, i32, i32, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -106,7 +108,8 @@ def exported_symbols() -> Sequence[str]:
             "nf_forces_adjoint_batched", "nf_set_default_tuning", "nf_get_default_tuning",
             "nf_status_read", "nf_stats_read", "nf_profile_enable", "nf_profile_read",
             "nf_kernel_launches", "nf_forces_noalloc", "nf_forces_density", "nf_timestep",
-            "nf_kdk_step", "nf_multipoles", "nf_set_debug", "nf_debug_check")
+            "nf_kdk_step", "nf_multipoles", "nf_set_debug", "nf_debug_check",
+            "nf_fma_probe_sink_floats", "nf_fma_probe")
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -250,6 +253,20 @@ def nf_profile_read(back: int = 0) -> dict:
 
 def nf_kernel_launches() -> int:
     return int(load().nf_kernel_launches())
+
+
+def nf_fma_probe_sink_floats() -> int:
+    return int(load().nf_fma_probe_sink_floats())
+
+
+def nf_fma_probe(sink: torch.Tensor, iters: int, packed: bool, stream=None) -> float:
+    """Launches the FP32 multiply-add probe; returns the flop count of the launch."""
+    if sink.dtype != torch.float32 or not sink.is_cuda or sink.numel() < nf_fma_probe_sink_floats():
+        raise ValueError("sink must be a CUDA float32 tensor of nf_fma_probe_sink_floats() values")
+    flop = ctypes.c_double(0.0)
+    _check(load().nf_fma_probe(_ptr(sink), int(iters), int(bool(packed)), ctypes.byref(flop), _stream(stream)),
+           "nf_fma_probe")
+    return flop.value
 
 
 def nf_forces_noalloc(pos: torch.Tensor, box: float, K: int, R: int, eps: float, acc: torch.Tensor,

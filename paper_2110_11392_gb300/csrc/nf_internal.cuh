@@ -84,6 +84,9 @@ struct StepScratch {
 };
 
 // Counts kernel launches (all translation units).
+// FP32 multiply-add throughput probe (measurement aid)
+size_t fma_probe_sink_floats();
+cudaError_t launch_fma_probe(float* sink, int iters, bool packed, double* flop, cudaStream_t s);
 void count_launches(int n);
 // Sets the dynamic shared-memory limit of a kernel once per (device, size).
 cudaError_t ensure_smem(const void* fn, int bytes);

@@ -1,0 +1,103 @@
+// FP32 fused multiply-add throughput probe: a measurement aid for the roofline
+// of the pair kernels, not part of the paper's method.  Every thread runs
+// kChains independent multiply-add chains (scalar FFMA, or packed .f32x2
+// pairs) so the FMA pipe, not latency, limits the rate.  The chain constants
+// keep every value normal and finite: x -> x * 0.999 + 0.001 converges to 1.
+#include <cuda_runtime.h>
+
+#include "nf_internal.cuh"
+
+namespace nf {
+
+namespace {
+
+constexpr int kProbeThreads = 256;
+constexpr int kProbeBlocksPerSm = 4;
+constexpr int kChains = 8;
+constexpr int kUnroll = 16;
+
+typedef unsigned long long p2;
+
+__device__ __forceinline__ p2 pack2(float a, float b)
+{
+    p2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void unpack2(p2 v, float& a, float& b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ p2 ffma2(p2 a, p2 b, p2 c)
+{
+    p2 d;
+    asm volatile("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+template <bool PACKED>
+__global__ void __launch_bounds__(kProbeThreads) k_fma_probe(float* __restrict__ sink, int iters, float m, float a)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    float s = 0.0f;
+    if constexpr (PACKED) {
+        p2 x[kChains];
+        const p2 mm = pack2(m, m), aa = pack2(a, a);
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) x[c] = pack2(0.5f + 1e-3f * c, 0.25f + 1e-3f * t);
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+#pragma unroll
+                for (int c = 0; c < kChains; ++c) x[c] = ffma2(x[c], mm, aa);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) {
+            float lo, hi;
+            unpack2(x[c], lo, hi);
+            s += lo + hi;
+        }
+    } else {
+        float x[kChains];
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) x[c] = 0.5f + 1e-3f * c + 1e-6f * t;
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+#pragma unroll
+                for (int c = 0; c < kChains; ++c) x[c] = fmaf(x[c], m, a);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) s += x[c];
+    }
+    sink[t] = s;
+}
+
+int probe_blocks()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms * kProbeBlocksPerSm;
+}
+
+}  // namespace
+
+size_t fma_probe_sink_floats() { return (size_t)probe_blocks() * kProbeThreads; }
+
+cudaError_t launch_fma_probe(float* sink, int iters, bool packed, double* flop, cudaStream_t s)
+{
+    const int blocks = probe_blocks();
+    if (packed)
+        k_fma_probe<true><<<blocks, kProbeThreads, 0, s>>>(sink, iters, 0.999f, 0.001f);
+    else
+        k_fma_probe<false><<<blocks, kProbeThreads, 0, s>>>(sink, iters, 0.999f, 0.001f);
+    count_launches(1);
+    // lanes x multiply-adds per lane x 2 flop
+    *flop = (double)blocks * kProbeThreads * iters * kUnroll * kChains * (packed ? 2 : 1) * 2.0;
+    return cudaGetLastError();
+}
+
+}  // namespace nf
