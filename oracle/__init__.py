@@ -28,6 +28,14 @@ binning's rounding.  Each function below cites what it follows in the paper
   Stepping") with the near-field accelerations of :func:`forces`.
 * :func:`multipoles` - cell multipoles in the complete basis, Eq. (multipoles)
   (Sec. "Computation of the Cell Multipoles"), about the cell centres.
+* :func:`derivatives`, :func:`taylors_fft`, :func:`taylor_forces`,
+  :func:`far_field` - the far field of Sec. "Far-field Computation": the
+  derivatives tensor (all periodic images by Ewald's split, minus the image
+  the near field computes), the Taylors as the convolution of derivatives and
+  multipoles (by FFT; :func:`convolve_direct` is the plain cyclic sum), and
+  the acceleration from the Taylors.  The arithmetic is in ``nf_oracle_far.c``.
+* :func:`ewald_forces` - plain Ewald summation over every pair, the reference
+  the paper's Sec. "Force Accuracy" compares the total force against.
 * :func:`density` - the apodized top-hat density estimate the paper's kernel
   accumulates as a 4th component, sum over near-field j with r < b of
   (1 - r^2/b^2) (Sec. "Force Kernel").
@@ -46,6 +54,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "nf_oracle.c")
+_SRC_FAR = os.path.join(_HERE, "nf_oracle_far.c")
 _LIB_PATH = os.path.join(_HERE, "_nf_oracle.so")
 _lib = None
 
@@ -53,10 +62,10 @@ _lib = None
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (-O2 -fopenmp -ffp-contract=off)."""
     if force or not os.path.exists(_LIB_PATH) or \
-            os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+            os.path.getmtime(_LIB_PATH) < max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_FAR)):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
         cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-               "-std=c11", "-o", tmp, _SRC, "-lm"]
+               "-std=c11", "-o", tmp, _SRC, _SRC_FAR, "-lm"]
         subprocess.check_call(cmd)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -88,6 +97,16 @@ def _load():
     lib.oracle_wrapped_positions.argtypes = [P, i64, f64, i32, P]
     lib.oracle_num_threads.restype = i32
     lib.oracle_num_threads.argtypes = []
+    lib.oracle_derivatives.restype = i32
+    lib.oracle_derivatives.argtypes = [i32, i32, i32, f64, f64, i32, i32, P]
+    lib.oracle_coulomb_derivatives.restype = None
+    lib.oracle_coulomb_derivatives.argtypes = [i32, f64, f64, f64, P]
+    lib.oracle_convolve_direct.restype = i32
+    lib.oracle_convolve_direct.argtypes = [i32, i32, P, P, P]
+    lib.oracle_taylor_forces.restype = i32
+    lib.oracle_taylor_forces.argtypes = [P, i64, f64, i32, i32, P, P]
+    lib.oracle_ewald_forces.restype = i32
+    lib.oracle_ewald_forces.argtypes = [P, i64, f64, f64, i32, i32, P, i64, P]
     _lib = lib
     return lib
 
@@ -297,3 +316,111 @@ def frac_error(a: np.ndarray, ref: np.ndarray) -> np.ndarray:
     a = np.asarray(a, np.float64)
     ref = np.asarray(ref, np.float64)
     return np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
+
+
+# ---------------------------------------------------------------------------
+# far field (Sec. "Far-field Computation") and the Ewald reference
+# ---------------------------------------------------------------------------
+
+EWALD_ALPHA_L = 3.5   # alpha * box of the default Ewald split
+EWALD_NIMG = 2        # real-space images n in [-2, 2]^3
+EWALD_HMAX = 9        # reciprocal vectors h in [-9, 9]^3
+
+
+def derivatives(K: int, R: int, p: int, box: float = 1.0, alpha: Optional[float] = None,
+                nimg: int = EWALD_NIMG, hmax: int = EWALD_HMAX) -> np.ndarray:
+    """Derivatives tensor D[g, term] (g = (gx*K + gy)*K + gz the sink-minus-source
+    cell offset mod K; terms in multipole_index(p) order): Cartesian derivatives
+    of the periodic unit-mass potential over all images, minus the near-field
+    image, at the cell-centre separation.  alpha defaults to 3.5 / box."""
+    a = EWALD_ALPHA_L / box if alpha is None else float(alpha)
+    D = np.zeros((K ** 3, multipole_terms(p)), np.float64)
+    _load().oracle_derivatives(int(K), int(R), int(p), float(box), a, int(nimg), int(hmax), _p(D))
+    return D
+
+
+def coulomb_derivatives(p: int, r) -> np.ndarray:
+    """Cartesian derivatives of 1/|r| at r != 0, every term of order <= p."""
+    out = np.zeros(multipole_terms(p), np.float64)
+    _load().oracle_coulomb_derivatives(int(p), float(r[0]), float(r[1]), float(r[2]), _p(out))
+    return out
+
+
+def taylor_coefficients(p: int):
+    """(n, k, n+k) term indices and (-1)^|k| / (n! k!) for every |n| + |k| <= p."""
+    from math import factorial
+    idx = multipole_index(p)
+    where = {t: q for q, t in enumerate(idx)}
+    out = []
+    for qn, n in enumerate(idx):
+        for qk, k in enumerate(idx):
+            if sum(n) + sum(k) > p:
+                continue
+            j = (n[0] + k[0], n[1] + k[1], n[2] + k[2])
+            coef = (-1.0) ** sum(k) / float(factorial(n[0]) * factorial(n[1]) * factorial(n[2]) *
+                                          factorial(k[0]) * factorial(k[1]) * factorial(k[2]))
+            out.append((qn, qk, where[j], coef))
+    return out
+
+
+def convolve_direct(K: int, p: int, D: np.ndarray, M: np.ndarray) -> np.ndarray:
+    """Taylors T[cell, term] by the plain cyclic sum over every (sink, source) cell pair."""
+    T = np.zeros((K ** 3, multipole_terms(p)), np.float64)
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    _load().oracle_convolve_direct(int(K), int(p), _p(D), _p(M), _p(T))
+    return T
+
+
+def taylors_fft(K: int, p: int, D: np.ndarray, M: np.ndarray) -> np.ndarray:
+    """Taylors T[cell, term]: the same convolution through numpy's 3-D FFT."""
+    nt = multipole_terms(p)
+    Dh = np.fft.fftn(D.reshape(K, K, K, nt), axes=(0, 1, 2))
+    Mh = np.fft.fftn(M.reshape(K, K, K, nt), axes=(0, 1, 2))
+    Th = np.zeros_like(Dh)
+    for qn, qk, qj, coef in taylor_coefficients(p):
+        Th[..., qn] += coef * Dh[..., qj] * Mh[..., qk]
+    return np.fft.ifftn(Th, axes=(0, 1, 2)).real.reshape(K ** 3, nt)
+
+
+def taylor_forces(pos, box: float, K: int, p: int, T: np.ndarray) -> np.ndarray:
+    """sum_n T^n grad(x^n) at every particle (unit masses), input order."""
+    pos = _pos(pos)
+    out = np.zeros((pos.shape[0], 3), np.float64)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    if _load().oracle_taylor_forces(_p(pos), pos.shape[0], float(box), int(K), int(p), _p(T), _p(out)):
+        raise ValueError("non-finite coordinates")
+    return out
+
+
+def far_field(pos, box: float, K: int, R: int, p: int, D: Optional[np.ndarray] = None,
+              return_taylors: bool = False):
+    """Far-field accelerations (m = 1/N, G = 1): multipoles, convolution with the
+    derivatives tensor, Taylor evaluation."""
+    pos = _pos(pos)
+    N = pos.shape[0]
+    if D is None:
+        D = derivatives(K, R, p, box)
+    M = multipoles(pos, box, K, p)
+    T = taylors_fft(K, p, D, M)
+    a = taylor_forces(pos, box, K, p, T) / N
+    return (a, T) if return_taylors else a
+
+
+def ewald_forces(pos, box: float, sinks: Optional[np.ndarray] = None, alpha: Optional[float] = None,
+                 nimg: int = 1, hmax: int = EWALD_HMAX) -> np.ndarray:
+    """Plain Ewald accelerations (m = 1/N, G = 1, unsoftened) on the sinks (all by default).
+
+    Pair separations are first reduced to the minimum image, so with
+    alpha * box = 3.5 the images n in [-1, 1]^3 leave out only terms below
+    erfc(5.25) ~ 1e-13 of a unit pair force."""
+    pos = _pos(pos)
+    N = pos.shape[0]
+    a = EWALD_ALPHA_L / box if alpha is None else float(alpha)
+    s = None if sinks is None else np.ascontiguousarray(sinks, dtype=np.int64)
+    n = N if s is None else len(s)
+    out = np.zeros((n, 3), np.float64)
+    if _load().oracle_ewald_forces(_p(pos), N, float(box), a, int(nimg), int(hmax),
+                                   None if s is None else _p(s), n, _p(out)):
+        raise ValueError("non-finite coordinates")
+    return out / N

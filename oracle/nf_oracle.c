@@ -64,7 +64,7 @@
  * centre of cell c in cell units is (t - c) - 0.5, rounded once to FP32; the
  * cell index wraps periodically, c mod K in [0, K).  `wrap` returns the number
  * of whole boxes between the input coordinate and its image in [0, box). */
-static int oracle_coord(float x, double kl, int K, int *cell, float *offset,
+int oracle_coord(float x, double kl, int K, int *cell, float *offset,
                         double *wrap)
 {
     double xd = (double)x;
