@@ -261,6 +261,64 @@ int nf_multipoles(const float *pos, int64_t N, double box, int K, int p, double 
                   void *ws, size_t ws_bytes, void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* Far field (Sec. "Far-field Computation")                                  */
+/* ------------------------------------------------------------------------ */
+
+/* The far field of the paper's near/far split: cell multipoles (Eq.
+ * (multipoles)), their convolution over the K^3 grid with the derivatives
+ * tensor (by FFT), and the acceleration from the resulting Taylor series of
+ * the potential in every cell.  The derivatives include every periodic image
+ * of the box, the images of the central and near-field cells included, minus
+ * the one image per cell pair that nf_forces computes directly, so
+ * nf_forces + nf_far_forces is the periodic (Ewald-summed) force up to the
+ * multipole order (same section).  Expansions are truncated at total order p:
+ * Taylor index n and multipole index k with |n| + |k| <= p, both in the
+ * complete basis of (p+3)(p+2)(p+1)/6 terms (ordered as in nf_multipoles).
+ * The uniform background of Ewald summation is included (the mean density
+ * exerts no force).  Arithmetic is FP64; the FFTs are cuFFT's. */
+#define NF_MAX_FAR_ORDER 12
+
+/* Bytes of a derivatives buffer for grid K and order p (0 if out of range):
+ * a 256-byte header, the convolution's coefficient table and the transformed
+ * derivatives, (p+3)(p+2)(p+1)/6 complex FP64 fields of K*K*(K/2+1) values. */
+size_t nf_derivatives_bytes(int K, int p);
+
+/* Workspace bytes of nf_far_forces (N particles) and of nf_derivatives (any
+ * N >= 1 will do): the binning, the multipoles, two complex spectra and the
+ * cuFFT work area.  0 if the arguments are out of range. */
+size_t nf_far_workspace_bytes(int64_t N, int K, int p);
+
+/* Precomputes the derivatives tensor of grid K, near-field radius R, order p
+ * and box side box into `derivs` (device memory, caller-owned, 256-byte
+ * aligned, at least nf_derivatives_bytes(K, p) bytes); ws is a device
+ * workspace of nf_far_workspace_bytes(1, K, p) bytes.  Asynchronous on
+ * `stream`.  The first call for a (K, p) on a device creates its cuFFT plans
+ * (cuFFT keeps its own small tables); make it before any graph capture.
+ * Errors: NF_ERR_ARG for K < 2R+1, R outside 1..NF_MAX_R, p outside
+ * 0..NF_MAX_FAR_ORDER, box <= 0 or NULL pointers; NF_ERR_WORKSPACE for a
+ * short or misaligned buffer; NF_ERR_CUDA if a launch or transform fails. */
+int nf_derivatives(int K, int R, int p, double box, void *derivs, size_t derivs_bytes,
+                   void *ws, size_t ws_bytes, void *stream);
+
+/* Far-field accelerations (m = 1/N, G = 1) of N particles (pos FP32 [N][3],
+ * box units, wrapped into [0, box) like nf_forces) from a derivatives buffer
+ * made by nf_derivatives for the same K, R, p and box:
+ *   acc_far  FP64 [N][3] in input order, or NULL;
+ *   acc_add  FP32 [N][3] in input order, or NULL: the far acceleration is
+ *            added to it (e.g. to the output of nf_forces for the total);
+ *   taylors  FP64 [K^3][(p+3)(p+2)(p+1)/6] Taylor coefficients, or NULL:
+ *            the potential in cell c is -m sum_t taylors[c][t] x^a y^b z^c,
+ *            x the displacement from the cell centre in box units.
+ * All device memory, caller-owned; ws holds nf_far_workspace_bytes(N, K, p)
+ * bytes.  Asynchronous on `stream` and graph-capturable once the cuFFT plans
+ * exist (after the first call for this (K, p)).  Errors: as nf_derivatives;
+ * NF_ERR_ARG also when `derivs` was made for another (K, R, p, box) by this
+ * process. */
+int nf_far_forces(const float *pos, int64_t N, double box, int K, int R, int p,
+                  const void *derivs, size_t derivs_bytes, double *acc_far, float *acc_add,
+                  double *taylors, void *ws, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* Time stepping (Sec. "Time Stepping": Kick-Drift-Kick leapfrog with a      */
 /* global time step, Eq. (timestep))                                         */
 /* ------------------------------------------------------------------------ */

@@ -1,4 +1,5 @@
-"""GB300-native near-field force of the Abacus N-body method (Garrison et al.).
+"""GB300-native force of the Abacus N-body method (Garrison et al.): the
+near-field pair sums, their adjoint, and the multipole/Taylor far field.
 
 The hot path is libnf (CUDA, sm_103a) behind a C ABI (``include/nf.h``);
 this package is its Python binding.  Importing it loads the library and
@@ -8,6 +9,7 @@ from . import _lib
 from ._lib import NFError, nf_version
 from .nearfield import (
     BatchedNearField,
+    FarField,
     NearField,
     bin_particles,
     forces,
@@ -27,6 +29,7 @@ __all__ = [
     "NFError",
     "nf_version",
     "BatchedNearField",
+    "FarField",
     "NearField",
     "bin_particles",
     "forces",

@@ -16,9 +16,10 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libnf.so")
-SOURCES = ["nf_bin.cu", "nf_force.cu", "nf_step.cu", "nf_multipole.cu", "nf_probe.cu", "nf_api.cu"]
+SOURCES = ["nf_bin.cu", "nf_force.cu", "nf_step.cu", "nf_multipole.cu", "nf_far.cu", "nf_probe.cu", "nf_api.cu"]
 HEADERS = ["nf_internal.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+LINK_LIBS = ["-lcufft"]  # the far field's 3-D FFTs
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
 
@@ -68,7 +69,7 @@ def build_library(force: bool = False, verbose: bool = False, extra_flags: List[
     if failed:
         raise RuntimeError(f"nvcc failed on {failed}")
     tmp = LIB + f".{os.getpid()}.tmp"
-    subprocess.check_call([cc, "-shared", *ARCH, "-o", tmp, *objs])
+    subprocess.check_call([cc, "-shared", *ARCH, "-o", tmp, *objs, *LINK_LIBS])
     os.replace(tmp, LIB)
     return LIB
 

@@ -89,6 +89,10 @@ def load(build: bool = True) -> ctypes.CDLL:
         "nf_timestep": (i32, [P, P, P, i64, f64, i32, P, P, P, sz, P]),
         "nf_kdk_step": (i32, [P, P, P, i64, f64, i32, i32, f64, P, P, P, sz, P]),
         "nf_multipoles": (i32, [P, i64, f64, i32, i32, P, P, sz, P]),
+        "nf_derivatives_bytes": (sz, [i32, i32]),
+        "nf_far_workspace_bytes": (sz, [i64, i32, i32]),
+        "nf_derivatives": (i32, [i32, i32, i32, f64, P, sz, P, sz, P]),
+        "nf_far_forces": (i32, [P, i64, f64, i32, i32, i32, P, sz, P, P, P, P, sz, P]),
         "nf_set_debug": (i32, [i32]),
         "nf_debug_check": (i32, [P, P]),
         "nf_fma_probe_sink_floats": (sz, []),
@@ -109,6 +113,7 @@ def exported_symbols() -> Sequence[str]:
             "nf_status_read", "nf_stats_read", "nf_profile_enable", "nf_profile_read",
             "nf_kernel_launches", "nf_forces_noalloc", "nf_forces_density", "nf_timestep",
             "nf_kdk_step", "nf_multipoles", "nf_set_debug", "nf_debug_check",
+            "nf_derivatives_bytes", "nf_far_workspace_bytes", "nf_derivatives", "nf_far_forces",
             "nf_fma_probe_sink_floats", "nf_fma_probe")
 
 
@@ -303,6 +308,32 @@ def nf_multipoles(pos: torch.Tensor, box: float, K: int, p: int, M: torch.Tensor
     _check(load().nf_multipoles(_ptr(pos), pos.shape[0], float(box), int(K), int(p), _ptr(M), _ptr(ws),
                                 ws.numel() * ws.element_size(), _stream(stream)),
            "nf_multipoles")
+
+
+def nf_derivatives_bytes(K: int, p: int) -> int:
+    return int(load().nf_derivatives_bytes(int(K), int(p)))
+
+
+def nf_far_workspace_bytes(N: int, K: int, p: int) -> int:
+    return int(load().nf_far_workspace_bytes(int(N), int(K), int(p)))
+
+
+def _nbytes(t: torch.Tensor) -> int:
+    return t.numel() * t.element_size()
+
+
+def nf_derivatives(K: int, R: int, p: int, box: float, derivs: torch.Tensor, ws: torch.Tensor,
+                   stream=None) -> None:
+    _check(load().nf_derivatives(int(K), int(R), int(p), float(box), _ptr(derivs), _nbytes(derivs), _ptr(ws),
+                                 _nbytes(ws), _stream(stream)), "nf_derivatives")
+
+
+def nf_far_forces(pos: torch.Tensor, box: float, K: int, R: int, p: int, derivs: torch.Tensor,
+                  acc_far: Optional[torch.Tensor], acc_add: Optional[torch.Tensor],
+                  taylors: Optional[torch.Tensor], ws: torch.Tensor, stream=None) -> None:
+    _check(load().nf_far_forces(_ptr(pos), pos.shape[0], float(box), int(K), int(R), int(p), _ptr(derivs),
+                                _nbytes(derivs), _ptr(acc_far), _ptr(acc_add), _ptr(taylors), _ptr(ws),
+                                _nbytes(ws), _stream(stream)), "nf_far_forces")
 
 
 def nf_set_debug(on: bool) -> None:

@@ -667,6 +667,215 @@ int nf_multipoles(const float* pos, int64_t N, double box, int K, int p, double*
     return finish_call(ws, s);
 }
 
+// ---- far field -------------------------------------------------------------
+
+namespace {
+
+// Ewald split of the derivatives tensor: alpha * box, real-space images
+// n in [-1, 1]^3 around the centred offset, reciprocal vectors |h_i| <= 14.
+// With these the left-out terms are below 1e-20 of the kept ones up to order 12.
+constexpr double kFarAlphaL = 5.0;
+constexpr int kFarNimg = 1;
+constexpr int kFarHmax = 14;
+
+struct DerivLayout {
+    int nt = 0;
+    long long npairs = 0;
+    size_t o_seg = 0, o_pairs = 0, o_dh = 0, total = 0;
+};
+
+bool far_args_ok(int K, int p)
+{
+    return K >= 1 && p >= 0 && p <= NF_MAX_FAR_ORDER && (int64_t)K * K * K < (int64_t(1) << 31);
+}
+
+DerivLayout deriv_layout(int K, int p)
+{
+    DerivLayout L;
+    L.nt = far_terms_host(p);
+    L.npairs = far_pairs_count(p);
+    size_t o = align_up(sizeof(DerivHeader));
+    L.o_seg = o;
+    o = align_up(o + 4 * (size_t)(L.nt + 1));
+    L.o_pairs = o;
+    o = align_up(o + sizeof(FarPair) * (size_t)L.npairs);
+    L.o_dh = o;
+    o = align_up(o + 16 * (size_t)L.nt * K * K * (K / 2 + 1));
+    L.total = o;
+    return L;
+}
+
+struct FarLayout {
+    size_t o_M = 0, o_Mh = 0, o_Th = 0, o_work = 0, work = 0, total = 0;
+};
+
+FarLayout far_layout(const Plan& pl, int K, int p)
+{
+    FarLayout F;
+    const int nt = far_terms_host(p);
+    const size_t spec = 16 * (size_t)nt * K * K * (K / 2 + 1);
+    size_t o = align_up(pl.total);
+    F.o_M = o;
+    o = align_up(o + 8 * (size_t)nt * K * K * K);
+    F.o_Mh = o;
+    o = align_up(o + spec);
+    F.o_Th = o;
+    o = align_up(o + spec);
+    F.o_work = o;
+    F.work = far_fft_work_bytes(K, nt);
+    o = align_up(o + F.work);
+    F.total = o;
+    return F;
+}
+
+struct DerivKey {
+    int K, R, p;
+    double box;
+};
+std::mutex g_deriv_mu;
+std::map<const void*, DerivKey> g_derivs;
+
+int far_validate(int K, int R, int p, double box)
+{
+    if (!far_args_ok(K, p)) return fail(NF_ERR_ARG, "far field: K = %d or order p = %d out of range (p <= %d)", K, p, NF_MAX_FAR_ORDER);
+    if (R < 1 || R > NF_MAX_R) return fail(NF_ERR_ARG, "R = %d out of [1, %d]", R, NF_MAX_R);
+    if (K < 2 * R + 1) return fail(NF_ERR_ARG, "K = %d < 2R+1 = %d: the stencil would wrap onto itself", K, 2 * R + 1);
+    if (!(box > 0.0) || !std::isfinite(box)) return fail(NF_ERR_ARG, "box = %g must be finite and > 0", box);
+    return NF_OK;
+}
+
+}  // namespace
+
+size_t nf_derivatives_bytes(int K, int p)
+{
+    if (!far_args_ok(K, p)) return 0;
+    return deriv_layout(K, p).total;
+}
+
+size_t nf_far_workspace_bytes(int64_t N, int K, int p)
+{
+    if (!far_args_ok(K, p)) return 0;
+    nf_box b = one_box(N, 1.0, K, 0, 0.0);
+    Plan pl;
+    if (make_plan(&b, 1, false, 32, &pl)) return 0;
+    return far_layout(pl, K, p).total;
+}
+
+int nf_derivatives(int K, int R, int p, double box, void* derivs, size_t derivs_bytes, void* ws, size_t ws_bytes,
+                   void* stream)
+{
+    g_last_error.clear();
+    int rc = far_validate(K, R, p, box);
+    if (rc) return rc;
+    if (!derivs) return fail(NF_ERR_ARG, "derivs is NULL");
+    const DerivLayout L = deriv_layout(K, p);
+    if ((reinterpret_cast<uintptr_t>(derivs) & (kAlign - 1)) != 0)
+        return fail(NF_ERR_WORKSPACE, "derivs must be %zu-byte aligned", kAlign);
+    if (derivs_bytes < L.total)
+        return fail(NF_ERR_WORKSPACE, "derivs too small: %zu bytes given, %zu needed", derivs_bytes, L.total);
+    nf_box b = one_box(1, box, K, 0, 0.0);
+    Plan pl;
+    rc = make_plan(&b, 1, false, 32, &pl);
+    if (rc) return rc;
+    const FarLayout F = far_layout(pl, K, p);
+    if (!ws) return fail(NF_ERR_WORKSPACE, "workspace is NULL");
+    if ((reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)) != 0)
+        return fail(NF_ERR_WORKSPACE, "workspace must be %zu-byte aligned", kAlign);
+    if (ws_bytes < F.total)
+        return fail(NF_ERR_WORKSPACE, "workspace too small: %zu bytes given, %zu needed", ws_bytes, F.total);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const double alpha = kFarAlphaL / box;
+    double* D = at<double>(ws, F.o_M);
+    double2* Dh = at<double2>(derivs, L.o_dh);
+    NF_CUDA(launch_deriv_real(K, R, p, box, alpha, kFarNimg, D, s), "derivatives (real space)");
+    cudaError_t e = launch_far_fft(K, L.nt, true, D, Dh, at<void>(ws, F.o_work), F.work, s);
+    if (e == cudaErrorMemoryAllocation) return fail(NF_ERR_WORKSPACE, "cuFFT work area larger than reserved");
+    if (e != cudaSuccess) return cuda_fail(e, "derivatives (forward FFT)");
+    NF_CUDA(launch_deriv_recip(K, p, box, alpha, kFarHmax, Dh, s), "derivatives (reciprocal space)");
+    NF_CUDA(launch_far_pairs(p, at<int>(derivs, L.o_seg), at<FarPair>(derivs, L.o_pairs), s), "convolution pairs");
+    DerivHeader h;
+    std::memset(&h, 0, sizeof h);
+    h.magic = kDerivMagic;
+    h.K = K;
+    h.R = R;
+    h.p = p;
+    h.box = box;
+    h.alpha = alpha;
+    h.nimg = kFarNimg;
+    h.hmax = kFarHmax;
+    h.nt = L.nt;
+    h.npairs = L.npairs;
+    h.o_seg = L.o_seg;
+    h.o_pairs = L.o_pairs;
+    h.o_dh = L.o_dh;
+    h.total = L.total;
+    NF_CUDA(launch_deriv_header(h, derivs, s), "derivatives header");
+    {
+        std::lock_guard<std::mutex> lk(g_deriv_mu);
+        g_derivs[derivs] = DerivKey{K, R, p, box};
+    }
+    return NF_OK;
+}
+
+int nf_far_forces(const float* pos, int64_t N, double box, int K, int R, int p, const void* derivs,
+                  size_t derivs_bytes, double* acc_far, float* acc_add, double* taylors, void* ws, size_t ws_bytes,
+                  void* stream)
+{
+    g_last_error.clear();
+    int rc = far_validate(K, R, p, box);
+    if (rc) return rc;
+    if (!pos || !derivs) return fail(NF_ERR_ARG, "null pointer argument");
+    const DerivLayout L = deriv_layout(K, p);
+    if (derivs_bytes < L.total)
+        return fail(NF_ERR_ARG, "derivs too small for K = %d, p = %d: %zu bytes given, %zu needed", K, p,
+                    derivs_bytes, L.total);
+    {
+        std::lock_guard<std::mutex> lk(g_deriv_mu);
+        auto it = g_derivs.find(derivs);
+        if (it != g_derivs.end()) {
+            const DerivKey& k = it->second;
+            if (k.K != K || k.R != R || k.p != p || k.box != box)
+                return fail(NF_ERR_ARG, "derivs were made for K = %d, R = %d, p = %d, box = %g", k.K, k.R, k.p, k.box);
+        }
+    }
+    nf_box b = one_box(N, box, K, 0, 0.0);
+    Plan pl;
+    rc = make_plan(&b, 1, false, 32, &pl);
+    if (rc) return rc;
+    const FarLayout F = far_layout(pl, K, p);
+    rc = check_ws(pl, ws, ws_bytes);
+    if (rc) return rc;
+    if (ws_bytes < F.total)
+        return fail(NF_ERR_WORKSPACE, "workspace too small: %zu bytes given, %zu needed", ws_bytes, F.total);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int32_t* off = at<int32_t>(ws, pl.o_off);
+    float4* rel = at<float4>(ws, pl.o_rel);
+    rc = run_binning(pl, pos, ws, off, rel, at<int32_t>(ws, pl.o_perm), s);
+    if (rc) return rc;
+    const int C = (int)pl.C;
+    double* M = at<double>(ws, F.o_M);
+    double2* Mh = at<double2>(ws, F.o_Mh);
+    double2* Th = at<double2>(ws, F.o_Th);
+    NF_CUDA(launch_multipoles(off, rel, C, box / K, p, M, s), "multipoles");
+    cudaError_t e = launch_far_fft(K, L.nt, true, M, Mh, at<void>(ws, F.o_work), F.work, s);
+    if (e == cudaErrorMemoryAllocation) return fail(NF_ERR_WORKSPACE, "cuFFT work area larger than reserved");
+    if (e != cudaSuccess) return cuda_fail(e, "multipoles (forward FFT)");
+    NF_CUDA(launch_far_contract(K, p, at<const int>(const_cast<void*>(derivs), L.o_seg),
+                                at<const FarPair>(const_cast<void*>(derivs), L.o_pairs),
+                                at<const double2>(const_cast<void*>(derivs), L.o_dh), Mh, Th, s),
+            "convolution");
+    double* T = M;  // the multipoles are no longer needed
+    e = launch_far_fft(K, L.nt, false, Th, T, at<void>(ws, F.o_work), F.work, s);
+    if (e == cudaErrorMemoryAllocation) return fail(NF_ERR_WORKSPACE, "cuFFT work area larger than reserved");
+    if (e != cudaSuccess) return cuda_fail(e, "Taylors (inverse FFT)");
+    if (acc_far || acc_add)
+        NF_CUDA(launch_taylor_forces(p, off, rel, T, C, box / K, 1.0 / (double)N, acc_far, acc_add, s),
+                "Taylor forces");
+    if (taylors)
+        NF_CUDA(cudaMemcpyAsync(taylors, T, 8 * (size_t)L.nt * C, cudaMemcpyDeviceToDevice, s), "Taylors copy");
+    return finish_call(ws, s);
+}
+
 int nf_set_debug(int on)
 {
     g_debug = on != 0;

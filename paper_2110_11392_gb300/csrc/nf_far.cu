@@ -1,0 +1,568 @@
+// Far field of the force split (Sec. "Far-field Computation"): the
+// derivatives tensor, the convolution of the cell multipoles with it on the
+// K^3 grid (by FFT), and the acceleration from the resulting Taylor series.
+//
+// Derivatives tensor.  D^{abc}(g), for every cell offset g (sink minus source
+// cell, mod K), is the (a,b,c)-th Cartesian derivative of the periodic
+// potential of a unit mass at the cell-centre separation: every image of the
+// box, the images of the central and near-field cells included, with the
+// uniform neutralising background of Ewald summation, minus the single image
+// that the near field computes directly (an offset whose centred components
+// all lie in [-R, R]).  With Ewald's split at parameter alpha
+//     sum_n 1/|r+nL| = sum_n erfc(alpha|r+nL|)/|r+nL|
+//                      + (4 pi / V) sum_{k != 0} exp(-k^2 / 4 alpha^2) / k^2 cos(k.r)
+//                      - pi / (alpha^2 V),                k = 2 pi h / L,
+// the real-space images are summed on the grid (k_deriv_real) and the
+// reciprocal part is added after the FFT directly in k-space: on the grid
+// r = g w, its discrete Fourier transform at q is K^3 times the sum of
+// (4 pi/V) exp(-k^2/4alpha^2)/k^2 (i k)^{abc} over the h congruent to q mod K
+// (k_deriv_recip), so it needs no real-space evaluation at all.
+// Cartesian derivatives of a radial g(r) use the Hermite recursion of
+// McMurchie & Davidson (1978): with g_m = (r^-1 d/dr)^m g and R^m_{tuv} the
+// (t,u,v) derivative of g_m, R^m_{t+1,u,v} = t R^{m+1}_{t-1,u,v} +
+// X R^{m+1}_{t,u,v} (likewise in Y, Z) and R^0_{abc} is the derivative.  For
+// erfc(alpha r)/r, g_m = (-1)^m B_m with B_0 = erfc(alpha r)/r and
+// B_m = [(2m-1) B_{m-1} + (2 alpha^2)^m exp(-alpha^2 r^2) / (alpha sqrt(pi))] / r^2
+// (Smith's recurrence).  The near image's smooth erf(alpha r)/r part is
+// subtracted with g_m from its power series (alpha r < 2) or as the Coulomb
+// g_m minus the erfc g_m (alpha r >= 2, where that difference is well
+// conditioned).
+//
+// Taylors.  T^n(c) = sum_{c'} sum_k (-1)^{|k|} / (n! k!) D^{n+k}(c - c') M^k(c'),
+// |n| + |k| <= p: the Taylor expansion of 1/|Delta + x - s| in the sink and
+// source displacements about the cell-centre separation.  By the convolution
+// theorem each term is a product in k-space (k_far_contract) between the
+// forward transforms of D and of the multipoles; the inverse transform gives
+// T in every cell.  The FFTs are cuFFT's (a plain library transform); every
+// other step is a kernel of this file.
+//
+// Acceleration.  The potential in a cell is -m sum_n T^n x^n (G = 1), so
+// a = m sum_n T^n grad(x^n), x the displacement from the cell centre (the
+// particle's FP32 cell-centred offset times w), evaluated by nested Horner
+// schemes in z, y and x (k_taylor_forces).  All far-field arithmetic is FP64.
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <utility>
+
+#include "nf_internal.cuh"
+
+namespace nf {
+
+namespace {
+
+constexpr int kDerivThreads = 256;
+constexpr int kTermsPerThread = (kMaxFarTerms + kDerivThreads - 1) / kDerivThreads;
+
+__host__ __device__ inline int far_terms(int p) { return (p + 3) * (p + 2) * (p + 1) / 6; }
+
+// (a, b, c) of term t in the complete-basis order of order p
+__device__ inline void decode_term(int t, int p, int& a, int& b, int& c)
+{
+    int r = t;
+    for (a = 0; a <= p; ++a) {
+        const int n_a = (p - a + 1) * (p - a + 2) / 2;
+        if (r < n_a) break;
+        r -= n_a;
+    }
+    for (b = 0; b <= p - a; ++b) {
+        const int n_b = p - a - b + 1;
+        if (r < n_b) break;
+        r -= n_b;
+    }
+    c = r;
+}
+
+__host__ __device__ inline int encode_term(int a, int b, int c, int p)
+{
+    int t = 0;
+    for (int a2 = 0; a2 < a; ++a2) t += (p - a2 + 1) * (p - a2 + 2) / 2;
+    for (int b2 = 0; b2 < b; ++b2) t += p - a - b2 + 1;
+    return t + c;
+}
+
+__device__ inline int centred(int g, int K) { return 2 * g > K ? g - K : g; }
+
+// g_m of erfc(alpha r)/r (sign (-1)^m included), m = 0..p
+__device__ void gm_erfc(int p, double alpha, double r, double* gm)
+{
+    const double r2 = r * r;
+    const double e = exp(-alpha * alpha * r2) / (alpha * 1.7724538509055160273);
+    double B = erfc(alpha * r) / r, pw = 1.0;
+    gm[0] = B;
+    for (int m = 1; m <= p; ++m) {
+        pw *= 2.0 * alpha * alpha;
+        B = ((2 * m - 1) * B + pw * e) / r2;
+        gm[m] = (m & 1) ? -B : B;
+    }
+}
+
+// g_m of erf(alpha r)/r, m = 0..p, any r >= 0
+__device__ void gm_erf(int p, double alpha, double r, double* gm)
+{
+    if (alpha * r >= 2.0) {
+        gm_erfc(p, alpha, r, gm);
+        double v = 1.0 / r;
+        const double ir2 = 1.0 / (r * r);
+        for (int m = 0; m <= p; ++m) {
+            if (m) v *= -(double)(2 * m - 1) * ir2;
+            gm[m] = v - gm[m];
+        }
+        return;
+    }
+    const double x = -r * r;
+    double am = alpha;  // alpha^(2m+1)
+    double sgn = 1.0;   // (-2)^m
+    for (int m = 0; m <= p; ++m) {
+        double sum = 0.0, term = 1.0, ap = am;
+        for (int j = 0; j < 120; ++j) {
+            const double add = term * ap / (double)(2 * m + 2 * j + 1);
+            sum += add;
+            if (j > 4 && fabs(add) <= 1e-18 * fabs(sum)) break;
+            term *= x / (double)(j + 1);
+            ap *= alpha * alpha;
+        }
+        gm[m] = 1.1283791670955125739 * sgn * sum;  // 2/sqrt(pi)
+        am *= alpha * alpha;
+        sgn *= -2.0;
+    }
+}
+
+// Block-wide Hermite recursion for one point: adds scale * R^0_{abc} to the
+// calling thread's accumulators (terms threadIdx.x + j * blockDim.x).
+// lay: 2 * (p+1)^3 doubles of shared memory; gm: p+1 values in shared memory.
+__device__ void hermite_block(int p, int nt, double X, double Y, double Z, const double* gm, double scale,
+                              double* lay, double* acc)
+{
+    const int P1 = p + 1, cube = P1 * P1 * P1;
+    double* nxt = lay;
+    double* cur = lay + cube;
+    if (threadIdx.x == 0) nxt[0] = gm[p];
+    __syncthreads();
+    for (int m = p - 1; m >= 0; --m) {
+        const int top = p - m;
+        for (int e = threadIdx.x; e < cube; e += blockDim.x) {
+            const int t = e / (P1 * P1), u = (e / P1) % P1, v = e % P1;
+            if (t + u + v > top) continue;
+            double r;
+            if (t + u + v == 0)
+                r = gm[m];
+            else if (t > 0)
+                r = (t >= 2 ? (t - 1) * nxt[e - 2 * P1 * P1] : 0.0) + X * nxt[e - P1 * P1];
+            else if (u > 0)
+                r = (u >= 2 ? (u - 1) * nxt[e - 2 * P1] : 0.0) + Y * nxt[e - P1];
+            else
+                r = (v >= 2 ? (v - 1) * nxt[e - 2] : 0.0) + Z * nxt[e - 1];
+            cur[e] = r;
+        }
+        __syncthreads();
+        double* sw = cur;
+        cur = nxt;
+        nxt = sw;
+    }
+    // layer 0 is in nxt
+#pragma unroll
+    for (int j = 0; j < kTermsPerThread; ++j) {
+        const int t = threadIdx.x + j * blockDim.x;
+        if (t < nt) {
+            int a, b, c;
+            decode_term(t, p, a, b, c);
+            acc[j] += scale * nxt[(a * P1 + b) * P1 + c];
+        }
+    }
+    __syncthreads();  // lay and gm are reused by the next point
+}
+
+// Real-space part of D, one block per cell offset g: images n in [-nimg, nimg]^3
+// (the near image left out), minus the near image's erf part.  D is cell-major
+// [C][nt], the layout of the multipoles.
+__global__ void __launch_bounds__(kDerivThreads) k_deriv_real(int K, int R, int p, int nt, double box, double alpha,
+                                                              int nimg, double* __restrict__ D)
+{
+    extern __shared__ double sm[];
+    const int P1 = p + 1;
+    double* lay = sm;
+    double* gm = sm + 2 * P1 * P1 * P1;
+    const int C = K * K * K;
+    const double w = box / K;
+    for (int g = blockIdx.x; g < C; g += gridDim.x) {
+        const int cx = centred(g / (K * K), K), cy = centred((g / K) % K, K), cz = centred(g % K, K);
+        const bool near = abs(cx) <= R && abs(cy) <= R && abs(cz) <= R;
+        const double dx = cx * w, dy = cy * w, dz = cz * w;
+        double acc[kTermsPerThread];
+#pragma unroll
+        for (int j = 0; j < kTermsPerThread; ++j) acc[j] = 0.0;
+        const int side = 2 * nimg + 1;
+        for (int n = 0; n < side * side * side; ++n) {
+            const int nx = n / (side * side) - nimg, ny = (n / side) % side - nimg, nz = n % side - nimg;
+            if (near && nx == 0 && ny == 0 && nz == 0) continue;
+            const double X = dx + nx * box, Y = dy + ny * box, Z = dz + nz * box;
+            if (threadIdx.x == 0) gm_erfc(p, alpha, sqrt(X * X + Y * Y + Z * Z), gm);
+            __syncthreads();
+            hermite_block(p, nt, X, Y, Z, gm, 1.0, lay, acc);
+        }
+        if (near) {
+            if (threadIdx.x == 0) gm_erf(p, alpha, sqrt(dx * dx + dy * dy + dz * dz), gm);
+            __syncthreads();
+            hermite_block(p, nt, dx, dy, dz, gm, -1.0, lay, acc);
+        }
+#pragma unroll
+        for (int j = 0; j < kTermsPerThread; ++j) {
+            const int t = threadIdx.x + j * blockDim.x;
+            if (t < nt) D[(size_t)g * nt + t] = acc[j];
+        }
+    }
+}
+
+// Reciprocal part and background constant, added to the transformed real-space
+// part: Dh[t][q] += K^3 sum_{h = q mod K, h != 0, |h_i| <= hmax} w(k) (i k)^{abc},
+// q over the K x K x (K/2+1) half spectrum of the real-to-complex transform.
+__global__ void k_deriv_recip(int K, int p, int nt, double box, double alpha, int hmax, double2* __restrict__ Dh)
+{
+    const int KH = K / 2 + 1;
+    const long long nq = (long long)K * K * KH;
+    const long long total = nq * nt;
+    const double V = box * box * box;
+    const double twopi_L = 6.283185307179586477 / box;
+    const double K3 = (double)K * K * K;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int t = (int)(e / nq);
+        const long long q = e - (long long)t * nq;
+        const int qx = (int)(q / (K * KH)), qy = (int)((q / KH) % K), qz = (int)(q % KH);
+        int a, b, c;
+        decode_term(t, p, a, b, c);
+        const int s = a + b + c;
+        double re = 0.0, im = 0.0;
+        for (int hx = -hmax + (qx + hmax) % K; hx <= hmax; hx += K)
+            for (int hy = -hmax + (qy + hmax) % K; hy <= hmax; hy += K)
+                for (int hz = -hmax + (qz + hmax) % K; hz <= hmax; hz += K) {
+                    if (hx == 0 && hy == 0 && hz == 0) continue;
+                    const double kx = twopi_L * hx, ky = twopi_L * hy, kz = twopi_L * hz;
+                    const double k2 = kx * kx + ky * ky + kz * kz;
+                    double f = (12.566370614359172954 / V) * exp(-k2 / (4.0 * alpha * alpha)) / k2;
+                    for (int i = 0; i < a; ++i) f *= kx;
+                    for (int i = 0; i < b; ++i) f *= ky;
+                    for (int i = 0; i < c; ++i) f *= kz;
+                    // times i^s
+                    switch (s & 3) {
+                        case 0: re += f; break;
+                        case 1: im += f; break;
+                        case 2: re -= f; break;
+                        default: im -= f; break;
+                    }
+                }
+        double2 v = Dh[e];
+        v.x += K3 * re;
+        v.y += K3 * im;
+        if (t == 0 && q == 0) v.x += K3 * (-3.14159265358979323846 / (alpha * alpha * V));
+        Dh[e] = v;
+    }
+}
+
+// The (n, k) pairs of the convolution, grouped by n: seg[n]..seg[n+1] index
+// pairs (k, n+k) with coefficient (-1)^{|k|} / (n! k!).  One thread.
+__global__ void k_far_pairs(int p, int* __restrict__ seg, FarPair* __restrict__ pairs)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double fac[kMaxFarOrder + 1];
+    fac[0] = 1.0;
+    for (int i = 1; i <= p; ++i) fac[i] = fac[i - 1] * i;
+    int e = 0, n = 0;
+    for (int na = 0; na <= p; ++na)
+        for (int nb = 0; nb <= p - na; ++nb)
+            for (int nc = 0; nc <= p - na - nb; ++nc, ++n) {
+                seg[n] = e;
+                const int rem = p - na - nb - nc;
+                for (int ka = 0; ka <= rem; ++ka)
+                    for (int kb = 0; kb <= rem - ka; ++kb)
+                        for (int kc = 0; kc <= rem - ka - kb; ++kc) {
+                            FarPair pr;
+                            pr.k = encode_term(ka, kb, kc, p);
+                            pr.j = encode_term(na + ka, nb + kb, nc + kc, p);
+                            pr.coef = (((ka + kb + kc) & 1) ? -1.0 : 1.0) /
+                                      (fac[na] * fac[nb] * fac[nc] * fac[ka] * fac[kb] * fac[kc]);
+                            pairs[e++] = pr;
+                        }
+            }
+    seg[n] = e;
+}
+
+// Th[n][q] = scale * sum_{pairs of n} coef * Dh[n+k][q] * Mh[k][q], one thread per q.
+__global__ void __launch_bounds__(128) k_far_contract(long long nq, int nt, const int* __restrict__ seg,
+                                                      const FarPair* __restrict__ pairs,
+                                                      const double2* __restrict__ Dh,
+                                                      const double2* __restrict__ Mh, double2* __restrict__ Th,
+                                                      double scale)
+{
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq;
+         q += (long long)gridDim.x * blockDim.x) {
+        for (int n = 0; n < nt; ++n) {
+            double re = 0.0, im = 0.0;
+            const int e1 = seg[n + 1];
+            for (int e = seg[n]; e < e1; ++e) {
+                const FarPair pr = pairs[e];
+                const double2 d = Dh[(size_t)pr.j * nq + q];
+                const double2 m = Mh[(size_t)pr.k * nq + q];
+                re += pr.coef * (d.x * m.x - d.y * m.y);
+                im += pr.coef * (d.x * m.y + d.y * m.x);
+            }
+            Th[(size_t)n * nq + q] = make_double2(scale * re, scale * im);
+        }
+    }
+}
+
+// Far-field acceleration of every particle: one block per cell (grid-stride),
+// the cell's Taylors in shared memory, one thread per particle.  The
+// potential sum_{a,b,c} T_{abc} x^a y^b z^c and its gradient are evaluated by
+// nested Horner schemes (in z, then y, then x), each carrying its derivative
+// along: no power tables, about two FMAs per term.  a = m * gradient.
+// Writes acc_far[orig] (FP64) and/or adds to acc_add[orig] (FP32).
+template <int P>
+__global__ void __launch_bounds__(128) k_taylor_forces(const int* __restrict__ off, const float4* __restrict__ rel,
+                                                      const double* __restrict__ T, int C, double w, double mass,
+                                                      double* __restrict__ acc_far, float* __restrict__ acc_add)
+{
+    constexpr int NT = (P + 3) * (P + 2) * (P + 1) / 6;
+    __shared__ double Ts[NT];
+    for (int cell = blockIdx.x; cell < C; cell += gridDim.x) {
+        const int s0 = off[cell], s1 = off[cell + 1];
+        if (s0 == s1) continue;
+        __syncthreads();
+        for (int t = threadIdx.x; t < NT; t += blockDim.x) Ts[t] = T[(size_t)cell * NT + t];
+        __syncthreads();
+        for (int i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
+            const float4 r4 = rel[i];
+            const double x = (double)r4.x * w, y = (double)r4.y * w, z = (double)r4.z * w;
+            double F = 0.0, Fx = 0.0, Fy = 0.0, Fz = 0.0;
+            // rolled loops: FP64 arithmetic, not issue, is the limit, and full
+            // unrolling would hoist every shared-memory load into registers
+#pragma unroll 1
+            for (int a = P; a >= 0; --a) {
+                // terms with first index a start at NT - C(P - a + 3, 3)
+                const int base_a = NT - (P - a + 3) * (P - a + 2) * (P - a + 1) / 6;
+                double U = 0.0, Uy = 0.0, Uz = 0.0;
+#pragma unroll 1
+                for (int b = P - a; b >= 0; --b) {
+                    const int base = base_a + b * (P - a + 1) - b * (b - 1) / 2;
+                    double S = 0.0, Sz = 0.0;
+                    for (int c = P - a - b; c >= 0; --c) {
+                        Sz = fma(Sz, z, S);
+                        S = fma(S, z, Ts[base + c]);
+                    }
+                    Uy = fma(Uy, y, U);
+                    U = fma(U, y, S);
+                    Uz = fma(Uz, y, Sz);
+                }
+                Fx = fma(Fx, x, F);
+                F = fma(F, x, U);
+                Fy = fma(Fy, x, Uy);
+                Fz = fma(Fz, x, Uz);
+            }
+            const int orig = __float_as_int(r4.w);
+            const double ax = mass * Fx, ay = mass * Fy, az = mass * Fz;
+            if (acc_far) {
+                acc_far[3 * (size_t)orig] = ax;
+                acc_far[3 * (size_t)orig + 1] = ay;
+                acc_far[3 * (size_t)orig + 2] = az;
+            }
+            if (acc_add) {
+                acc_add[3 * (size_t)orig] += (float)ax;
+                acc_add[3 * (size_t)orig + 1] += (float)ay;
+                acc_add[3 * (size_t)orig + 2] += (float)az;
+            }
+        }
+    }
+}
+
+__global__ void k_deriv_header(DerivHeader h, DerivHeader* dst)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) *dst = h;
+}
+
+int device_sms()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+// ---- cuFFT plans: one per (device, K, nt, direction), cell-major real side
+struct PlanEntry {
+    cufftHandle h = 0;
+    size_t work = 0;
+};
+std::mutex g_fft_mu;
+std::map<std::tuple<int, int, int, int>, PlanEntry> g_plans;
+
+cufftResult plan_layout(int K, int nt, bool forward, cufftHandle h, size_t* work, bool estimate_only)
+{
+    int n[3] = {K, K, K};
+    int real_emb[3] = {K, K, K};
+    int cplx_emb[3] = {K, K, K / 2 + 1};
+    const int cdist = K * K * (K / 2 + 1);
+    if (forward) {
+        if (estimate_only)
+            return cufftEstimateMany(3, n, real_emb, nt, 1, cplx_emb, 1, cdist, CUFFT_D2Z, nt, work);
+        return cufftMakePlanMany(h, 3, n, real_emb, nt, 1, cplx_emb, 1, cdist, CUFFT_D2Z, nt, work);
+    }
+    if (estimate_only) return cufftEstimateMany(3, n, cplx_emb, 1, cdist, real_emb, nt, 1, CUFFT_Z2D, nt, work);
+    return cufftMakePlanMany(h, 3, n, cplx_emb, 1, cdist, real_emb, nt, 1, CUFFT_Z2D, nt, work);
+}
+
+cudaError_t get_plan(int K, int nt, bool forward, PlanEntry* out)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(dev, K, nt, forward ? 1 : 0);
+    auto it = g_plans.find(key);
+    if (it != g_plans.end()) {
+        *out = it->second;
+        return cudaSuccess;
+    }
+    PlanEntry pe;
+    if (cufftCreate(&pe.h) != CUFFT_SUCCESS) return cudaErrorUnknown;
+    if (cufftSetAutoAllocation(pe.h, 0) != CUFFT_SUCCESS || plan_layout(K, nt, forward, pe.h, &pe.work, false) != CUFFT_SUCCESS) {
+        cufftDestroy(pe.h);
+        return cudaErrorUnknown;
+    }
+    g_plans[key] = pe;
+    *out = pe;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+int far_terms_host(int p) { return far_terms(p); }
+
+long long far_pairs_count(int p)
+{
+    // 6-tuples of non-negative integers with sum <= p: C(p + 6, 6)
+    long long c = 1;
+    for (int i = 1; i <= 6; ++i) c = c * (p + i) / i;
+    return c;
+}
+
+size_t far_fft_work_bytes(int K, int nt)
+{
+    // Cached per (K, nt): the size query that sizes a workspace always comes
+    // first, so a call being captured into a CUDA graph never asks cuFFT (its
+    // estimate is not a capture-safe call).
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, size_t> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_pair(K, nt);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    size_t w1 = 0, w2 = 0;
+    const bool ok = plan_layout(K, nt, true, 0, &w1, true) == CUFFT_SUCCESS &&
+                    plan_layout(K, nt, false, 0, &w2, true) == CUFFT_SUCCESS;
+    const size_t data = (size_t)nt * K * K * (K / 2 + 1) * 16;
+    size_t w = ok ? (w1 > w2 ? w1 : w2) : data;
+    // keep a margin: cuFFT's estimate is an upper bound, a made plan may choose differently
+    w += (w >> 2) + (1u << 20);
+    cache[key] = w;
+    return w;
+}
+
+cudaError_t launch_far_fft(int K, int nt, bool forward, void* in, void* out, void* work, size_t work_bytes,
+                           cudaStream_t s)
+{
+    std::lock_guard<std::mutex> lk(g_fft_mu);
+    PlanEntry pe;
+    cudaError_t e = get_plan(K, nt, forward, &pe);
+    if (e != cudaSuccess) return e;
+    if (pe.work > work_bytes) return cudaErrorMemoryAllocation;
+    if (cufftSetStream(pe.h, s) != CUFFT_SUCCESS || cufftSetWorkArea(pe.h, work) != CUFFT_SUCCESS)
+        return cudaErrorUnknown;
+    const cufftResult r = forward ? cufftExecD2Z(pe.h, (cufftDoubleReal*)in, (cufftDoubleComplex*)out)
+                                  : cufftExecZ2D(pe.h, (cufftDoubleComplex*)in, (cufftDoubleReal*)out);
+    return r == CUFFT_SUCCESS ? cudaGetLastError() : cudaErrorUnknown;
+}
+
+cudaError_t launch_deriv_real(int K, int R, int p, double box, double alpha, int nimg, double* D, cudaStream_t s)
+{
+    const int nt = far_terms(p);
+    const size_t smem = (size_t)(2 * (p + 1) * (p + 1) * (p + 1) + (p + 1)) * sizeof(double);
+    cudaError_t e = ensure_smem((const void*)k_deriv_real, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int C = K * K * K;
+    const int grid = C < device_sms() * 8 ? C : device_sms() * 8;
+    k_deriv_real<<<grid, kDerivThreads, smem, s>>>(K, R, p, nt, box, alpha, nimg, D);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_deriv_recip(int K, int p, double box, double alpha, int hmax, double2* Dh, cudaStream_t s)
+{
+    const int nt = far_terms(p);
+    const long long total = (long long)nt * K * K * (K / 2 + 1);
+    long long blocks = (total + 255) / 256;
+    const long long cap = (long long)device_sms() * 16;
+    if (blocks > cap) blocks = cap;
+    k_deriv_recip<<<(int)blocks, 256, 0, s>>>(K, p, nt, box, alpha, hmax, Dh);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_deriv_header(const DerivHeader& h, void* dst, cudaStream_t s)
+{
+    k_deriv_header<<<1, 32, 0, s>>>(h, static_cast<DerivHeader*>(dst));
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_far_pairs(int p, int* seg, FarPair* pairs, cudaStream_t s)
+{
+    k_far_pairs<<<1, 32, 0, s>>>(p, seg, pairs);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_far_contract(int K, int p, const int* seg, const FarPair* pairs, const double2* Dh,
+                                const double2* Mh, double2* Th, cudaStream_t s)
+{
+    const long long nq = (long long)K * K * (K / 2 + 1);
+    long long blocks = (nq + 127) / 128;
+    const long long cap = (long long)device_sms() * 32;
+    if (blocks > cap) blocks = cap;
+    const double scale = 1.0 / ((double)K * K * K);  // the unnormalised inverse transform
+    k_far_contract<<<(int)blocks, 128, 0, s>>>(nq, far_terms(p), seg, pairs, Dh, Mh, Th, scale);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_taylor_forces(int p, const int* off, const float4* rel, const double* T, int C, double w,
+                                 double mass, double* acc_far, float* acc_add, cudaStream_t s)
+{
+    const int grid = C < device_sms() * 16 ? C : device_sms() * 16;
+    switch (p) {
+#define NF_TAYLOR_CASE(P)                                                                           \
+    case P:                                                                                         \
+        k_taylor_forces<P><<<grid, 128, 0, s>>>(off, rel, T, C, w, mass, acc_far, acc_add);         \
+        break;
+        NF_TAYLOR_CASE(0)
+        NF_TAYLOR_CASE(1)
+        NF_TAYLOR_CASE(2)
+        NF_TAYLOR_CASE(3)
+        NF_TAYLOR_CASE(4)
+        NF_TAYLOR_CASE(5)
+        NF_TAYLOR_CASE(6)
+        NF_TAYLOR_CASE(7)
+        NF_TAYLOR_CASE(8)
+        NF_TAYLOR_CASE(9)
+        NF_TAYLOR_CASE(10)
+        NF_TAYLOR_CASE(11)
+        NF_TAYLOR_CASE(12)
+#undef NF_TAYLOR_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace nf

@@ -83,6 +83,43 @@ struct StepScratch {
     double v2_block[kStepBlocks];  // per-block FP64 sums of |v|^2
 };
 
+// ---- far field (nf_far.cu) ----
+constexpr int kMaxFarOrder = 12;  // NF_MAX_FAR_ORDER
+constexpr int kMaxFarTerms = (kMaxFarOrder + 3) * (kMaxFarOrder + 2) * (kMaxFarOrder + 1) / 6;
+// One (n, k) pair of the Taylor convolution: terms k and j = n + k, coefficient (-1)^{|k|} / (n! k!).
+struct FarPair {
+    int k;
+    int j;
+    double coef;
+};
+// Header of a derivatives buffer (nf_derivatives): where its parts live and what it was made for.
+struct DerivHeader {
+    unsigned magic;
+    int K, R, p;
+    double box, alpha;
+    int nimg, hmax, nt, pad0;
+    long long npairs;
+    unsigned long long o_seg, o_pairs, o_dh, total;
+    unsigned long long pad[21];
+};
+static_assert(sizeof(DerivHeader) == 256, "derivatives header is 256 bytes");
+constexpr unsigned kDerivMagic = 0x4E464452u;
+cudaError_t launch_deriv_header(const DerivHeader& h, void* dst, cudaStream_t s);
+int far_terms_host(int p);
+long long far_pairs_count(int p);
+// cuFFT work-area bytes to reserve for the forward and inverse transforms of nt fields on K^3
+size_t far_fft_work_bytes(int K, int nt);
+// forward: real cell-major [K^3][nt] -> complex term-major [nt][K][K][K/2+1]; inverse the reverse
+cudaError_t launch_far_fft(int K, int nt, bool forward, void* in, void* out, void* work, size_t work_bytes,
+                           cudaStream_t s);
+cudaError_t launch_deriv_real(int K, int R, int p, double box, double alpha, int nimg, double* D, cudaStream_t s);
+cudaError_t launch_deriv_recip(int K, int p, double box, double alpha, int hmax, double2* Dh, cudaStream_t s);
+cudaError_t launch_far_pairs(int p, int* seg, FarPair* pairs, cudaStream_t s);
+cudaError_t launch_far_contract(int K, int p, const int* seg, const FarPair* pairs, const double2* Dh,
+                                const double2* Mh, double2* Th, cudaStream_t s);
+cudaError_t launch_taylor_forces(int p, const int* off, const float4* rel, const double* T, int C, double w,
+                                 double mass, double* acc_far, float* acc_add, cudaStream_t s);
+
 // Counts kernel launches (all translation units).
 // FP32 multiply-add throughput probe (measurement aid)
 size_t fma_probe_sink_floats();

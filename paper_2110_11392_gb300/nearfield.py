@@ -110,6 +110,42 @@ def multipoles(pos: torch.Tensor, box: float, K: int, p: int, ws: Optional[torch
     return M
 
 
+class FarField:
+    """The far field of one grid (nf_derivatives once, nf_far_forces per call).
+
+    f = FarField(K, R, p, box); a_far = f(pos); or f(pos, add_to=acc) adds the
+    far acceleration into an FP32 [N, 3] tensor (e.g. the output of forces()).
+    """
+
+    def __init__(self, K: int, R: int, p: int, box: float = 1.0, device=None):
+        self.K, self.R, self.p, self.box = int(K), int(R), int(p), float(box)
+        self.device = torch.device(device if device is not None else "cuda")
+        nbytes = _lib.nf_derivatives_bytes(self.K, self.p)
+        if nbytes == 0:
+            raise ValueError(f"far field: K = {K}, p = {p} out of range")
+        self.derivs = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        ws = torch.empty(_lib.nf_far_workspace_bytes(1, self.K, self.p), dtype=torch.uint8, device=self.device)
+        _lib.nf_derivatives(self.K, self.R, self.p, self.box, self.derivs, ws)
+        self.nterms = (self.p + 3) * (self.p + 2) * (self.p + 1) // 6
+
+    def workspace(self, N: int) -> torch.Tensor:
+        return workspace(_lib.nf_far_workspace_bytes(N, self.K, self.p), self.device, key="far")
+
+    def __call__(self, pos: torch.Tensor, add_to: Optional[torch.Tensor] = None, want_far: bool = True,
+                 want_taylors: bool = False, ws: Optional[torch.Tensor] = None):
+        pos = _check_pos(pos)
+        N = pos.shape[0]
+        if ws is None:
+            ws = self.workspace(N)
+        acc = torch.empty((N, 3), dtype=torch.float64, device=pos.device) if want_far else None
+        T = (torch.empty((self.K ** 3, self.nterms), dtype=torch.float64, device=pos.device)
+             if want_taylors else None)
+        _lib.nf_far_forces(pos, self.box, self.K, self.R, self.p, self.derivs, acc, add_to, T, ws)
+        if want_taylors:
+            return acc, T
+        return acc
+
+
 def status(ws: Optional[torch.Tensor] = None, N: int = 1, K: int = 5, R: int = 2) -> int:
     """Device status of the last call on the default workspace (synchronises)."""
     if ws is None:

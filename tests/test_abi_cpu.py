@@ -127,3 +127,27 @@ def test_workloads_are_seeded_and_exact():
     w = config_batched(nboxes=4)
     assert sum(bx["N"] for bx in w.boxes) == w.N
     assert all(bx["K"] >= 5 for bx in w.boxes)
+
+
+def test_far_field_sizes_and_host_checks():
+    lib = _lib.load()
+    nt = lambda p: (p + 3) * (p + 2) * (p + 1) // 6
+    for K, p in [(5, 0), (8, 8), (11, 8), (32, 12)]:
+        b = _lib.nf_derivatives_bytes(K, p)
+        assert b >= 16 * nt(p) * K * K * (K // 2 + 1) + 256
+        assert b % 256 == 0
+        assert _lib.nf_far_workspace_bytes(1000, K, p) > 8 * nt(p) * K ** 3
+    assert _lib.nf_derivatives_bytes(8, 13) == 0 and _lib.nf_derivatives_bytes(0, 4) == 0
+    assert _lib.nf_far_workspace_bytes(0, 8, 4) == 0
+    big = 1 << 40
+    # rejected on the host before anything is launched
+    for K, R, p, box in [(4, 2, 4, 1.0), (8, 0, 4, 1.0), (8, 2, 13, 1.0), (8, 2, -1, 1.0), (8, 2, 4, 0.0)]:
+        assert lib.nf_derivatives(K, R, p, box, FAKE_WS, big, FAKE_WS, big, None) == _lib.NF_ERR_ARG
+    assert lib.nf_derivatives(8, 2, 4, 1.0, None, big, FAKE_WS, big, None) == _lib.NF_ERR_ARG
+    assert lib.nf_derivatives(8, 2, 4, 1.0, FAKE_WS, 100, FAKE_WS, big, None) == _lib.NF_ERR_WORKSPACE
+    assert lib.nf_far_forces(FAKE, 1000, 1.0, 4, 2, 4, FAKE_WS, big, None, None, None, FAKE_WS, big,
+                             None) == _lib.NF_ERR_ARG
+    assert lib.nf_far_forces(FAKE, 1000, 1.0, 8, 2, 4, FAKE_WS, 100, None, None, None, FAKE_WS, big,
+                             None) == _lib.NF_ERR_ARG
+    assert lib.nf_far_forces(FAKE, 1000, 1.0, 8, 2, 4, FAKE_WS, big, None, None, None, FAKE_WS, 4096,
+                             None) == _lib.NF_ERR_WORKSPACE

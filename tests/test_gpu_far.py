@@ -1,0 +1,153 @@
+"""nf_derivatives / nf_far_forces against the FP64 far-field oracle
+(Sec. "Far-field Computation"), and near + far against plain Ewald sums."""
+import numpy as np
+import pytest
+
+import oracle
+
+from _helpers import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _uniform(N, seed):
+    pos = np.random.default_rng(seed).random((N, 3)).astype(np.float32)
+    pos[pos >= 1.0] = 0.0
+    return pos
+
+
+def _clustered(N, K, seed):
+    from workloads import config_plain
+    return config_plain(N=N, K=K, seed=seed).pos
+
+
+def _dhat_gpu(ff):
+    """The transformed derivatives from a derivatives buffer, [nt][K][K][K/2+1] complex."""
+    import torch
+    head = ff.derivs[:256].cpu().numpy()
+    o_dh = int(np.frombuffer(head[72:80].tobytes(), np.uint64)[0])   # DerivHeader.o_dh
+    K, nt = ff.K, ff.nterms
+    n = nt * K * K * (K // 2 + 1)
+    raw = ff.derivs[o_dh:o_dh + 16 * n].cpu().numpy()
+    return np.frombuffer(raw.tobytes(), np.complex128).reshape(nt, K, K, K // 2 + 1)
+
+
+@pytest.mark.parametrize("K,R,p,box", [(5, 2, 4, 1.0), (8, 2, 8, 1.0), (11, 2, 8, 1.0), (9, 3, 6, 3.0),
+                                       (6, 2, 12, 1.0)])
+def test_derivatives_match_oracle(K, R, p, box):
+    import paper_2110_11392_gb300 as nf
+    ff = nf.FarField(K, R, p, box)
+    D = oracle.derivatives(K, R, p, box)          # another Ewald split than the library's
+    ref = np.fft.rfftn(D.reshape(K, K, K, -1), axes=(0, 1, 2)).transpose(3, 0, 1, 2)
+    got = _dhat_gpu(ff)
+    scale = np.abs(ref).reshape(ref.shape[0], -1).max(axis=1)[:, None, None, None]
+    assert np.abs(got - ref).max() / 1.0 <= 1e-11 * scale.max()
+    assert (np.abs(got - ref) / scale).max() < 1e-10
+
+
+@pytest.mark.parametrize("K,R,p,N,kind", [(5, 2, 4, 3000, "uniform"), (8, 2, 8, 20000, "clustered"),
+                                          (11, 2, 8, 65536, "uniform"), (7, 3, 5, 9000, "clustered"),
+                                          (16, 2, 8, 40000, "clustered"), (6, 2, 1, 500, "uniform")])
+def test_far_forces_match_oracle(K, R, p, N, kind):
+    import torch
+    import paper_2110_11392_gb300 as nf
+    pos = _uniform(N, 21) if kind == "uniform" else _clustered(N, K, 22)
+    ff = nf.FarField(K, R, p)
+    a, T = ff(to_dev(pos), want_taylors=True)
+    torch.cuda.synchronize()
+    aref, Tref = oracle.far_field(pos, 1.0, K, R, p, return_taylors=True)
+    T = T.cpu().numpy()
+    tscale = np.abs(Tref).max(axis=0) + 1e-300
+    assert (np.abs(T - Tref).max(axis=0) / tscale).max() < 1e-10
+    a = a.cpu().numpy()
+    assert np.abs(a - aref).max() < 1e-10 * np.abs(aref).max()
+    rel = np.linalg.norm(a - aref, axis=1) / np.linalg.norm(aref, axis=1)
+    assert np.median(rel) < 1e-11
+
+
+def test_add_to_near_field_output():
+    import torch
+    import paper_2110_11392_gb300 as nf
+    pos = to_dev(_uniform(8000, 5))
+    ff = nf.FarField(8, 2, 6)
+    near = nf.forces(pos, 1.0, 8, 2, 1e-4)
+    far = ff(pos)
+    tot = near.clone()
+    ff(pos, add_to=tot, want_far=False)
+    torch.cuda.synchronize()
+    assert torch.equal(tot, near + far.float())
+
+
+def test_total_force_matches_ewald_at_the_papers_configuration():
+    # 65536 random particles, CPD 11, order 8 (Sec. "Ewald"); FP32 near field
+    # plus FP64 far field against plain Ewald sums.
+    import torch
+    import paper_2110_11392_gb300 as nf
+    N, K, R, p = 65536, 11, 2, 8
+    pos = _uniform(N, 11)
+    eps = 1e-5
+    d = to_dev(pos)
+    tot = nf.forces(d, 1.0, K, R, eps)
+    nf.FarField(K, R, p)(d, add_to=tot, want_far=False)
+    torch.cuda.synchronize()
+    sinks = np.sort(np.random.default_rng(11).choice(N, 256, replace=False))
+    ref = oracle.ewald_forces(pos, 1.0, sinks=sinks)
+    fe = oracle.frac_error(tot.cpu().numpy()[sinks].astype(np.float64), ref)
+    assert np.median(fe) < 2.4e-5 and np.percentile(fe, 99) < 3.2e-4
+
+
+def test_single_particle_and_lattice():
+    import torch
+    import paper_2110_11392_gb300 as nf
+    ff = nf.FarField(8, 2, 8)
+    one = ff(to_dev(np.array([[0.37, 0.61, 0.12]], np.float32)))
+    g = (np.arange(8) + 0.5) / 8
+    lat = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3).astype(np.float32)
+    a = ff(to_dev(lat))
+    torch.cuda.synchronize()
+    assert one.abs().max().item() < 1e-12
+    assert a.abs().max().item() < 1e-12 * (1.0 / 512) * 64
+
+
+def test_graph_replay_is_bit_identical():
+    import torch
+    import paper_2110_11392_gb300 as nf
+    pos = to_dev(_clustered(30000, 10, 4))
+    ff = nf.FarField(10, 2, 8)
+    ws = ff.workspace(30000)
+    eager = ff(pos, ws=ws)
+    out = torch.zeros_like(eager)
+    from paper_2110_11392_gb300 import _lib
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    # one call on the capture stream first: cuFFT sets up per-stream state on first use
+    _lib.nf_far_forces(pos, 1.0, ff.K, ff.R, ff.p, ff.derivs, out, None, None, ws, stream=s)
+    torch.cuda.synchronize()
+    out.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        _lib.nf_far_forces(pos, 1.0, ff.K, ff.R, ff.p, ff.derivs, out, None, None, ws, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, eager)
+
+
+def test_argument_errors():
+    import torch
+    import paper_2110_11392_gb300 as nf
+    from paper_2110_11392_gb300 import _lib
+    ff = nf.FarField(8, 2, 4)
+    pos = to_dev(_uniform(100, 1))
+    ws = ff.workspace(100)
+    acc = torch.empty((100, 3), dtype=torch.float64, device="cuda")
+    with pytest.raises(_lib.NFError):   # derivatives made for another R
+        _lib.nf_far_forces(pos, 1.0, 8, 3, 4, ff.derivs, acc, None, None, ws)
+    with pytest.raises(_lib.NFError):   # another box side
+        _lib.nf_far_forces(pos, 2.0, 8, 2, 4, ff.derivs, acc, None, None, ws)
+    with pytest.raises(_lib.NFError):   # too small a buffer for K = 9
+        _lib.nf_far_forces(pos, 1.0, 9, 2, 4, ff.derivs, acc, None, None, ws)
+    with pytest.raises(_lib.NFError):   # workspace too small
+        _lib.nf_far_forces(pos, 1.0, 8, 2, 4, ff.derivs, acc, None, None, ws[:1024])
+    assert _lib.nf_derivatives_bytes(8, 13) == 0
+    with pytest.raises(_lib.NFError):
+        nf.FarField(4, 2, 4)            # K < 2R + 1 is caught by the library
