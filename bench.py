@@ -356,6 +356,7 @@ def run_native(args, rank, world, local):
     out["density"] = measure_density(w, pos, ws, acc, fwd_pair_ms, flush)
     out["kdk"] = measure_kdk(w, dev, flush)
     out["multipoles"] = measure_multipoles(w, pos, dev, flush)
+    out["far"] = measure_far(w, pos, dev, flush, fma, fwd_ms_for_far(out))
     if not args.no_e2e:
         out["e2e"] = measure_e2e(args, w, g_np, dev, P, flush)
     if not args.no_batched:
@@ -387,11 +388,11 @@ def measure_fma_peak(dev, target_ms=40.0, reps=3):
     sink = torch.empty(_lib.nf_fma_probe_sink_floats(), dtype=torch.float32, device=dev)
     s = torch.cuda.current_stream(dev)
     out = {}
-    for packed in (False, True):
+    for mode in (0, 1, 2):
         def timed(iters):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(s)
-            flop = _lib.nf_fma_probe(sink, iters, packed, s)
+            flop = _lib.nf_fma_probe(sink, iters, mode, s)
             e1.record(s)
             e1.synchronize()
             return flop, e0.elapsed_time(e1)
@@ -402,9 +403,10 @@ def measure_fma_peak(dev, target_ms=40.0, reps=3):
         for _ in range(reps):
             flop, ms = timed(iters)
             best = max(best, flop / (ms / 1e3) / 1e12)
-        out["packed_tflops" if packed else "scalar_tflops"] = best
+        out[("scalar_tflops", "packed_tflops", "fp64_tflops")[mode]] = best
     out["unit"] = "TFLOP/s"
-    out["probe"] = "nf_fma_probe: 4 x 256 threads per SM, 8 independent multiply-add chains per thread, best of 3"
+    out["probe"] = ("nf_fma_probe: 4 x 256 threads per SM, 8 independent multiply-add chains per thread "
+                    "(f32, f32x2, f64), best of 3")
     return out
 
 
@@ -455,6 +457,81 @@ def measure_kdk(w, dev, flush, steps=5):
     t = float(np.mean(ms))
     return {"ms_per_step": t, "particle_updates_per_s": w.N / (t / 1e3), "last_dt": float(dt.item()),
             "steps": steps, "note": "kick + drift + nf_forces + kick + Eq. (timestep), near field only"}
+
+
+def fwd_ms_for_far(out):
+    return out["fwd"]["ms"]
+
+
+def taylor_flop_per_particle(p: int) -> int:
+    """FP64 flops of the nested Horner evaluation of the Taylor series and its
+    gradient at one particle: 2 multiply-adds per term (z), 3 per (a, b) (y),
+    4 per a (x); 2 flops each."""
+    nt = (p + 3) * (p + 2) * (p + 1) // 6
+    nab = (p + 2) * (p + 1) // 2
+    return 2 * (2 * nt + 3 * nab + 4 * (p + 1))
+
+
+def measure_far(w, pos, dev, flush, fma, fwd_ms, p=8, reps=5):
+    """The far field at order p on the same particles: derivatives once, then
+    nf_far_forces per call (binning, multipoles, FFT convolution, Taylors);
+    and the total force of a user's step, nf_forces + nf_far_forces adding
+    into its output."""
+    import torch
+    import paper_2110_11392_gb300 as nf
+    from paper_2110_11392_gb300 import _lib
+    stream = torch.cuda.current_stream(dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    a, b = ev(), ev()
+    torch.cuda.synchronize(dev)
+    a.record(stream)
+    ff = nf.FarField(w.K, w.R, p, w.box, device=dev)
+    b.record(stream)
+    b.synchronize()
+    deriv_ms = a.elapsed_time(b)
+    ws = ff.workspace(w.N)
+    acc = torch.empty((w.N, 3), dtype=torch.float64, device=dev)
+    wsn = torch.empty(_lib.nf_workspace_bytes(w.N, w.K, w.R), dtype=torch.uint8, device=dev)
+    tot = torch.empty((w.N, 3), dtype=torch.float32, device=dev)
+    for _ in range(2):
+        _lib.nf_far_forces(pos, w.box, w.K, w.R, p, ff.derivs, acc, None, None, ws)
+    _lib.nf_profile_enable(True)
+    far_ms, prof = [], []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = ev(), ev()
+        a.record(stream)
+        _lib.nf_far_forces(pos, w.box, w.K, w.R, p, ff.derivs, acc, None, None, ws)
+        b.record(stream)
+        b.synchronize()
+        far_ms.append(a.elapsed_time(b))
+        prof.append(_lib.nf_far_profile_read(0))
+    _lib.nf_profile_enable(False)
+    tot_ms = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = ev(), ev()
+        a.record(stream)
+        _lib.nf_forces(pos, w.box, w.K, w.R, w.eps, tot, None, wsn)
+        _lib.nf_far_forces(pos, w.box, w.K, w.R, p, ff.derivs, None, tot, None, ws)
+        b.record(stream)
+        b.synchronize()
+        tot_ms.append(a.elapsed_time(b))
+    stage = {k: float(np.median([q[k] for q in prof])) for k in prof[0]}
+    t_ms = float(np.median(far_ms))
+    flop = taylor_flop_per_particle(p) * w.N
+    taylor_tf = flop / (stage["taylor_ms"] / 1e3) / 1e12
+    peak64 = fma["fp64_tflops"]
+    return {"order": p, "terms": (p + 3) * (p + 2) * (p + 1) // 6, "derivatives_ms": deriv_ms,
+            "ms": t_ms, "particles_per_s": w.N / (t_ms / 1e3), "stages_ms": stage,
+            "total_force_ms": float(np.median(tot_ms)),
+            "total_force_particles_per_s": w.N / (float(np.median(tot_ms)) / 1e3),
+            "near_forward_ms": fwd_ms,
+            "taylor_roofline": {"bound": "fp64", "achieved": taylor_tf, "peak": peak64, "unit": "TFLOP/s",
+                                "frac": taylor_tf / peak64, "flop_per_particle": taylor_flop_per_particle(p),
+                                "peak_basis": "measured: nf_fma_probe fma.rn.f64, this run"},
+            "note": "FP64 throughout; derivatives once per (K, R, p, box); Ewald-summed periodic force "
+                    "= near + far"}
 
 
 def measure_multipoles(w, pos, dev, flush, p=8, reps=3):

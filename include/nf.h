@@ -280,7 +280,10 @@ int nf_multipoles(const float *pos, int64_t N, double box, int K, int p, double 
 
 /* Bytes of a derivatives buffer for grid K and order p (0 if out of range):
  * a 256-byte header, the convolution's coefficient table and the transformed
- * derivatives, (p+3)(p+2)(p+1)/6 complex FP64 fields of K*K*(K/2+1) values. */
+ * derivatives, (p+3)(p+2)(p+1)/6 FP64 fields of K*K*(K/2+1) values.  The
+ * transform of a term of even order is real and of odd order imaginary (the
+ * derivatives have definite parity, Sec. "Far-field Computation"), so one
+ * real number per term and frequency is kept. */
 size_t nf_derivatives_bytes(int K, int p);
 
 /* Workspace bytes of nf_far_forces (N particles) and of nf_derivatives (any
@@ -418,25 +421,43 @@ int nf_profile_enable(int on);
  * to NF_PROFILE_RING - 1.  Returns NF_ERR_ARG if there is no such call. */
 int nf_profile_read(int back, nf_profile *out);
 
+/* Device time of the stages of a recent nf_far_forces call (same event ring
+ * and the same rules as nf_profile_read; read a far call with this function):
+ *   bin_ms          cell ids, offsets, radix sort, cell-centred offsets;
+ *   multipoles_ms   the cell multipoles;
+ *   convolution_ms  forward FFT, k-space product with the derivatives, inverse FFT;
+ *   taylor_ms       the Taylor-series evaluation at every particle;
+ *   total_ms        first event to last. */
+typedef struct {
+    double bin_ms;
+    double multipoles_ms;
+    double convolution_ms;
+    double taylor_ms;
+    double total_ms;
+} nf_far_profile;
+
+int nf_far_profile_read(int back, nf_far_profile *out);
+
 /* Number of kernels libnf has launched in this process (all entry points). */
 int64_t nf_kernel_launches(void);
 
 /* ---- Measurement aid (no counterpart in the paper) ----------------------
- * FP32 multiply-add throughput probe, the measured denominator beside the
- * derived FP32 peak (SMs x 128 lanes x 2 flop x clock) of the pair kernels'
- * roofline.  Launches one kernel of 4 blocks of 256 threads per SM; every
- * thread runs 8 independent multiply-add chains for iters x 16 trips, as
- * scalar fma.rn.f32 (packed = 0) or packed fma.rn.f32x2 (packed != 0).
+ * Multiply-add throughput probe, the measured denominator beside the derived
+ * peaks of the rooflines: FP32 for the pair kernels (SMs x 128 lanes x 2 flop
+ * x clock), FP64 for the far field.  Launches one kernel of 4 blocks of 256
+ * threads per SM; every thread runs 8 independent multiply-add chains for
+ * iters x 16 trips, as scalar fma.rn.f32 (mode 0), packed fma.rn.f32x2
+ * (mode 1) or fma.rn.f64 (mode 2).
  *   sink   device float buffer of at least nf_fma_probe_sink_floats() values,
  *          caller-owned; receives one value per thread (keeps the work live)
  *   iters  1 .. 2^24
  *   flop   host double; receives the floating-point operations the launch
  *          performs (2 per multiply-add and lane)
  * The call is asynchronous on `stream`; time it with events on that stream.
- * Returns NF_ERR_ARG for NULL pointers or iters out of range, NF_ERR_CUDA if
- * the launch fails. */
+ * Returns NF_ERR_ARG for NULL pointers, iters out of range or another mode,
+ * NF_ERR_CUDA if the launch fails. */
 size_t nf_fma_probe_sink_floats(void);
-int nf_fma_probe(float *sink, int iters, int packed, double *flop, cudaStream_t stream);
+int nf_fma_probe(float *sink, int iters, int mode, double *flop, cudaStream_t stream);
 
 #ifdef __cplusplus
 }

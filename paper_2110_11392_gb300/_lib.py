@@ -37,6 +37,12 @@ class nf_profile(ctypes.Structure):
                 ("combine_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
 
 
+class nf_far_profile(ctypes.Structure):
+    _fields_ = [("bin_ms", ctypes.c_double), ("multipoles_ms", ctypes.c_double),
+                ("convolution_ms", ctypes.c_double), ("taylor_ms", ctypes.c_double),
+                ("total_ms", ctypes.c_double)]
+
+
 class nf_step_params(ctypes.Structure):
     _fields_ = [("eta_acc", ctypes.c_double), ("eta_h", ctypes.c_double), ("hubble", ctypes.c_double)]
 
@@ -93,6 +99,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         "nf_far_workspace_bytes": (sz, [i64, i32, i32]),
         "nf_derivatives": (i32, [i32, i32, i32, f64, P, sz, P, sz, P]),
         "nf_far_forces": (i32, [P, i64, f64, i32, i32, i32, P, sz, P, P, P, P, sz, P]),
+        "nf_far_profile_read": (i32, [i32, P]),
         "nf_set_debug": (i32, [i32]),
         "nf_debug_check": (i32, [P, P]),
         "nf_fma_probe_sink_floats": (sz, []),
@@ -114,6 +121,7 @@ def exported_symbols() -> Sequence[str]:
             "nf_kernel_launches", "nf_forces_noalloc", "nf_forces_density", "nf_timestep",
             "nf_kdk_step", "nf_multipoles", "nf_set_debug", "nf_debug_check",
             "nf_derivatives_bytes", "nf_far_workspace_bytes", "nf_derivatives", "nf_far_forces",
+            "nf_far_profile_read",
             "nf_fma_probe_sink_floats", "nf_fma_probe")
 
 
@@ -256,6 +264,13 @@ def nf_profile_read(back: int = 0) -> dict:
             "combine_ms": p.combine_ms, "total_ms": p.total_ms}
 
 
+def nf_far_profile_read(back: int = 0) -> dict:
+    p = nf_far_profile()
+    _check(load().nf_far_profile_read(int(back), ctypes.byref(p)), "nf_far_profile_read")
+    return {"bin_ms": p.bin_ms, "multipoles_ms": p.multipoles_ms, "convolution_ms": p.convolution_ms,
+            "taylor_ms": p.taylor_ms, "total_ms": p.total_ms}
+
+
 def nf_kernel_launches() -> int:
     return int(load().nf_kernel_launches())
 
@@ -264,12 +279,13 @@ def nf_fma_probe_sink_floats() -> int:
     return int(load().nf_fma_probe_sink_floats())
 
 
-def nf_fma_probe(sink: torch.Tensor, iters: int, packed: bool, stream=None) -> float:
-    """Launches the FP32 multiply-add probe; returns the flop count of the launch."""
+def nf_fma_probe(sink: torch.Tensor, iters: int, mode, stream=None) -> float:
+    """Launches the multiply-add probe (mode 0 f32, 1 f32x2, 2 f64; a bool
+    selects 0 or 1); returns the flop count of the launch."""
     if sink.dtype != torch.float32 or not sink.is_cuda or sink.numel() < nf_fma_probe_sink_floats():
         raise ValueError("sink must be a CUDA float32 tensor of nf_fma_probe_sink_floats() values")
     flop = ctypes.c_double(0.0)
-    _check(load().nf_fma_probe(_ptr(sink), int(iters), int(bool(packed)), ctypes.byref(flop), _stream(stream)),
+    _check(load().nf_fma_probe(_ptr(sink), int(iters), int(mode), ctypes.byref(flop), _stream(stream)),
            "nf_fma_probe")
     return flop.value
 

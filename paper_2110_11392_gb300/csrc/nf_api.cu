@@ -700,7 +700,7 @@ DerivLayout deriv_layout(int K, int p)
     L.o_pairs = o;
     o = align_up(o + sizeof(FarPair) * (size_t)L.npairs);
     L.o_dh = o;
-    o = align_up(o + 16 * (size_t)L.nt * K * K * (K / 2 + 1));
+    o = align_up(o + 8 * (size_t)L.nt * K * K * (K / 2 + 1));  // one real per (term, frequency)
     L.total = o;
     return L;
 }
@@ -786,12 +786,13 @@ int nf_derivatives(int K, int R, int p, double box, void* derivs, size_t derivs_
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const double alpha = kFarAlphaL / box;
     double* D = at<double>(ws, F.o_M);
-    double2* Dh = at<double2>(derivs, L.o_dh);
+    double2* Dh = at<double2>(ws, F.o_Mh);
     NF_CUDA(launch_deriv_real(K, R, p, box, alpha, kFarNimg, D, s), "derivatives (real space)");
     cudaError_t e = launch_far_fft(K, L.nt, true, D, Dh, at<void>(ws, F.o_work), F.work, s);
     if (e == cudaErrorMemoryAllocation) return fail(NF_ERR_WORKSPACE, "cuFFT work area larger than reserved");
     if (e != cudaSuccess) return cuda_fail(e, "derivatives (forward FFT)");
-    NF_CUDA(launch_deriv_recip(K, p, box, alpha, kFarHmax, Dh, s), "derivatives (reciprocal space)");
+    NF_CUDA(launch_deriv_recip(K, p, box, alpha, kFarHmax, Dh, at<double>(derivs, L.o_dh), s),
+            "derivatives (reciprocal space)");
     NF_CUDA(launch_far_pairs(p, at<int>(derivs, L.o_seg), at<FarPair>(derivs, L.o_pairs), s), "convolution pairs");
     DerivHeader h;
     std::memset(&h, 0, sizeof h);
@@ -850,27 +851,33 @@ int nf_far_forces(const float* pos, int64_t N, double box, int K, int R, int p, 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int32_t* off = at<int32_t>(ws, pl.o_off);
     float4* rel = at<float4>(ws, pl.o_rel);
+    NF_CUDA(prof_mark(0, s), "profile");
     rc = run_binning(pl, pos, ws, off, rel, at<int32_t>(ws, pl.o_perm), s);
     if (rc) return rc;
+    NF_CUDA(prof_mark(1, s), "profile");
     const int C = (int)pl.C;
     double* M = at<double>(ws, F.o_M);
     double2* Mh = at<double2>(ws, F.o_Mh);
     double2* Th = at<double2>(ws, F.o_Th);
     NF_CUDA(launch_multipoles(off, rel, C, box / K, p, M, s), "multipoles");
+    NF_CUDA(prof_mark(2, s), "profile");
     cudaError_t e = launch_far_fft(K, L.nt, true, M, Mh, at<void>(ws, F.o_work), F.work, s);
     if (e == cudaErrorMemoryAllocation) return fail(NF_ERR_WORKSPACE, "cuFFT work area larger than reserved");
     if (e != cudaSuccess) return cuda_fail(e, "multipoles (forward FFT)");
     NF_CUDA(launch_far_contract(K, p, at<const int>(const_cast<void*>(derivs), L.o_seg),
                                 at<const FarPair>(const_cast<void*>(derivs), L.o_pairs),
-                                at<const double2>(const_cast<void*>(derivs), L.o_dh), Mh, Th, s),
+                                at<const double>(const_cast<void*>(derivs), L.o_dh), Mh, Th, s),
             "convolution");
     double* T = M;  // the multipoles are no longer needed
     e = launch_far_fft(K, L.nt, false, Th, T, at<void>(ws, F.o_work), F.work, s);
     if (e == cudaErrorMemoryAllocation) return fail(NF_ERR_WORKSPACE, "cuFFT work area larger than reserved");
     if (e != cudaSuccess) return cuda_fail(e, "Taylors (inverse FFT)");
+    NF_CUDA(prof_mark(3, s), "profile");
     if (acc_far || acc_add)
-        NF_CUDA(launch_taylor_forces(p, off, rel, T, C, box / K, 1.0 / (double)N, acc_far, acc_add, s),
+        NF_CUDA(launch_taylor_forces(p, off, rel, T, (int)N, C, box / K, 1.0 / (double)N, acc_far, acc_add, s),
                 "Taylor forces");
+    NF_CUDA(prof_mark(4, s), "profile");
+    if (g_profile_on) ++g_prof_count;
     if (taylors)
         NF_CUDA(cudaMemcpyAsync(taylors, T, 8 * (size_t)L.nt * C, cudaMemcpyDeviceToDevice, s), "Taylors copy");
     return finish_call(ws, s);
@@ -912,20 +919,47 @@ int nf_profile_enable(int on)
     return NF_OK;
 }
 
-int nf_profile_read(int back, nf_profile* out)
+namespace {
+
+// the four stage times of a profiled call, `back` calls ago
+int profile_stages(int back, float ms[4])
 {
-    g_last_error.clear();
-    if (!out) return fail(NF_ERR_ARG, "null pointer argument");
     if (back < 0 || back >= NF_PROFILE_RING || back >= g_prof_count)
         return fail(NF_ERR_ARG, "no profiled call %d back (%lld recorded)", back, g_prof_count);
     cudaEvent_t* ev = g_ev[(g_prof_count - 1 - back) % NF_PROFILE_RING];
     cudaError_t e = cudaEventSynchronize(ev[4]);
     if (e != cudaSuccess) return cuda_fail(e, "profile sync");
-    float ms[4];
     for (int i = 0; i < 4; ++i) {
         e = cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
         if (e != cudaSuccess) return cuda_fail(e, "profile elapsed");
     }
+    return NF_OK;
+}
+
+}  // namespace
+
+int nf_far_profile_read(int back, nf_far_profile* out)
+{
+    g_last_error.clear();
+    if (!out) return fail(NF_ERR_ARG, "null pointer argument");
+    float ms[4];
+    const int rc = profile_stages(back, ms);
+    if (rc) return rc;
+    out->bin_ms = ms[0];
+    out->multipoles_ms = ms[1];
+    out->convolution_ms = ms[2];
+    out->taylor_ms = ms[3];
+    out->total_ms = (double)ms[0] + ms[1] + ms[2] + ms[3];
+    return NF_OK;
+}
+
+int nf_profile_read(int back, nf_profile* out)
+{
+    g_last_error.clear();
+    if (!out) return fail(NF_ERR_ARG, "null pointer argument");
+    float ms[4];
+    const int rc = profile_stages(back, ms);
+    if (rc) return rc;
     out->bin_ms = ms[0];
     out->worklist_ms = ms[1];
     out->pair_ms = ms[2];
@@ -938,12 +972,13 @@ int64_t nf_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
 size_t nf_fma_probe_sink_floats(void) { return nf::fma_probe_sink_floats(); }
 
-int nf_fma_probe(float* sink, int iters, int packed, double* flop, cudaStream_t stream)
+int nf_fma_probe(float* sink, int iters, int mode, double* flop, cudaStream_t stream)
 {
     g_last_error.clear();
     if (!sink || !flop) return fail(NF_ERR_ARG, "nf_fma_probe: sink and flop must be non-NULL");
     if (iters < 1 || iters > (1 << 24)) return fail(NF_ERR_ARG, "nf_fma_probe: iters %d outside [1, 2^24]", iters);
-    const cudaError_t e = nf::launch_fma_probe(sink, iters, packed != 0, flop, stream);
+    if (mode < 0 || mode > 2) return fail(NF_ERR_ARG, "nf_fma_probe: mode %d is not 0, 1 or 2", mode);
+    const cudaError_t e = nf::launch_fma_probe(sink, iters, mode, flop, stream);
     return e == cudaSuccess ? NF_OK : cuda_fail(e, "nf_fma_probe");
 }
 

@@ -218,9 +218,15 @@ __global__ void __launch_bounds__(kDerivThreads) k_deriv_real(int K, int R, int 
 }
 
 // Reciprocal part and background constant, added to the transformed real-space
-// part: Dh[t][q] += K^3 sum_{h = q mod K, h != 0, |h_i| <= hmax} w(k) (i k)^{abc},
-// q over the K x K x (K/2+1) half spectrum of the real-to-complex transform.
-__global__ void k_deriv_recip(int K, int p, int nt, double box, double alpha, int hmax, double2* __restrict__ Dh)
+// part, and the result compressed to one real number per (term, q).
+// Dh (input) is the transform of the real-space part, [nt][K][K][K/2+1];
+// the reciprocal part adds K^3 sum_{h = q mod K, h != 0, |h_i| <= hmax}
+// w(k) (i k)^{abc}.  D^{abc}(-g) = (-1)^{a+b+c} D^{abc}(g) on the periodic
+// grid, so the transform of a term is real for even a+b+c and imaginary for
+// odd a+b+c (the parity the paper uses to halve the convolution): Dr keeps
+// the real part of even terms and the imaginary part of odd ones.
+__global__ void k_deriv_recip(int K, int p, int nt, double box, double alpha, int hmax,
+                              const double2* __restrict__ Dh, double* __restrict__ Dr)
 {
     const int KH = K / 2 + 1;
     const long long nq = (long long)K * K * KH;
@@ -236,7 +242,7 @@ __global__ void k_deriv_recip(int K, int p, int nt, double box, double alpha, in
         int a, b, c;
         decode_term(t, p, a, b, c);
         const int s = a + b + c;
-        double re = 0.0, im = 0.0;
+        double acc = 0.0;  // coefficient of i^(s mod 2): real part (s even) or imaginary part (s odd)
         for (int hx = -hmax + (qx + hmax) % K; hx <= hmax; hx += K)
             for (int hy = -hmax + (qy + hmax) % K; hy <= hmax; hy += K)
                 for (int hz = -hmax + (qz + hmax) % K; hz <= hmax; hz += K) {
@@ -247,24 +253,19 @@ __global__ void k_deriv_recip(int K, int p, int nt, double box, double alpha, in
                     for (int i = 0; i < a; ++i) f *= kx;
                     for (int i = 0; i < b; ++i) f *= ky;
                     for (int i = 0; i < c; ++i) f *= kz;
-                    // times i^s
-                    switch (s & 3) {
-                        case 0: re += f; break;
-                        case 1: im += f; break;
-                        case 2: re -= f; break;
-                        default: im -= f; break;
-                    }
+                    // i^s = +1, +i, -1, -i for s mod 4 = 0, 1, 2, 3
+                    acc += (s & 2) ? -f : f;
                 }
-        double2 v = Dh[e];
-        v.x += K3 * re;
-        v.y += K3 * im;
-        if (t == 0 && q == 0) v.x += K3 * (-3.14159265358979323846 / (alpha * alpha * V));
-        Dh[e] = v;
+        const double2 v = Dh[e];
+        double out = ((s & 1) ? v.y : v.x) + K3 * acc;
+        if (t == 0 && q == 0) out += K3 * (-3.14159265358979323846 / (alpha * alpha * V));
+        Dr[e] = out;
     }
 }
 
 // The (n, k) pairs of the convolution, grouped by n: seg[n]..seg[n+1] index
-// pairs (k, n+k) with coefficient (-1)^{|k|} / (n! k!).  One thread.
+// pairs (k, n+k) with coefficient (-1)^{|k|} / (n! k!); the sign bit of j
+// marks an odd total order.  One thread.
 __global__ void k_far_pairs(int p, int* __restrict__ seg, FarPair* __restrict__ pairs)
 {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
@@ -283,6 +284,8 @@ __global__ void k_far_pairs(int p, int* __restrict__ seg, FarPair* __restrict__ 
                             FarPair pr;
                             pr.k = encode_term(ka, kb, kc, p);
                             pr.j = encode_term(na + ka, nb + kb, nc + kc, p);
+                            // odd total order: the transform of D^j is imaginary (sign bit of j)
+                            if ((na + nb + nc + ka + kb + kc) & 1) pr.j |= (int)0x80000000u;
                             pr.coef = (((ka + kb + kc) & 1) ? -1.0 : 1.0) /
                                       (fac[na] * fac[nb] * fac[nc] * fac[ka] * fac[kb] * fac[kc]);
                             pairs[e++] = pr;
@@ -291,10 +294,13 @@ __global__ void k_far_pairs(int p, int* __restrict__ seg, FarPair* __restrict__ 
     seg[n] = e;
 }
 
-// Th[n][q] = scale * sum_{pairs of n} coef * Dh[n+k][q] * Mh[k][q], one thread per q.
+// Th[n][q] = scale * sum_{pairs of n} coef * D^{n+k}(q) * Mh[k][q], one thread
+// per q.  D^{j}(q) is Dr[j][q] for even |j| and i Dr[j][q] for odd |j|, so a
+// pair costs one real-times-complex product (3 FP64 operations) instead of a
+// complex one.
 __global__ void __launch_bounds__(128) k_far_contract(long long nq, int nt, const int* __restrict__ seg,
                                                       const FarPair* __restrict__ pairs,
-                                                      const double2* __restrict__ Dh,
+                                                      const double* __restrict__ Dr,
                                                       const double2* __restrict__ Mh, double2* __restrict__ Th,
                                                       double scale)
 {
@@ -305,75 +311,85 @@ __global__ void __launch_bounds__(128) k_far_contract(long long nq, int nt, cons
             const int e1 = seg[n + 1];
             for (int e = seg[n]; e < e1; ++e) {
                 const FarPair pr = pairs[e];
-                const double2 d = Dh[(size_t)pr.j * nq + q];
+                const double cd = pr.coef * Dr[(size_t)(pr.j & 0x7fffffff) * nq + q];
                 const double2 m = Mh[(size_t)pr.k * nq + q];
-                re += pr.coef * (d.x * m.x - d.y * m.y);
-                im += pr.coef * (d.x * m.y + d.y * m.x);
+                if (pr.j < 0) {  // odd |j|: i * cd * m
+                    re = fma(-cd, m.y, re);
+                    im = fma(cd, m.x, im);
+                } else {
+                    re = fma(cd, m.x, re);
+                    im = fma(cd, m.y, im);
+                }
             }
             Th[(size_t)n * nq + q] = make_double2(scale * re, scale * im);
         }
     }
 }
 
-// Far-field acceleration of every particle: one block per cell (grid-stride),
-// the cell's Taylors in shared memory, one thread per particle.  The
-// potential sum_{a,b,c} T_{abc} x^a y^b z^c and its gradient are evaluated by
-// nested Horner schemes (in z, then y, then x), each carrying its derivative
-// along: no power tables, about two FMAs per term.  a = m * gradient.
-// Writes acc_far[orig] (FP64) and/or adds to acc_add[orig] (FP32).
+// Far-field acceleration of every particle, one thread per particle in the
+// binned order; the particle's cell comes from a binary search of the cell
+// offsets (cells are ragged, so one block per cell would leave most of a
+// block idle).  The potential sum_{a,b,c} T_{abc} x^a y^b z^c and its
+// gradient are evaluated by nested Horner schemes (in z, then y, then x),
+// each carrying its derivative along: no power tables, about two FMAs per
+// term.  a = m * gradient.  Writes acc_far[orig] (FP64) and/or adds to
+// acc_add[orig] (FP32).
 template <int P>
 __global__ void __launch_bounds__(128) k_taylor_forces(const int* __restrict__ off, const float4* __restrict__ rel,
-                                                      const double* __restrict__ T, int C, double w, double mass,
-                                                      double* __restrict__ acc_far, float* __restrict__ acc_add)
+                                                      const double* __restrict__ T, int N, int C, double w,
+                                                      double mass, double* __restrict__ acc_far,
+                                                      float* __restrict__ acc_add)
 {
     constexpr int NT = (P + 3) * (P + 2) * (P + 1) / 6;
-    __shared__ double Ts[NT];
-    for (int cell = blockIdx.x; cell < C; cell += gridDim.x) {
-        const int s0 = off[cell], s1 = off[cell + 1];
-        if (s0 == s1) continue;
-        __syncthreads();
-        for (int t = threadIdx.x; t < NT; t += blockDim.x) Ts[t] = T[(size_t)cell * NT + t];
-        __syncthreads();
-        for (int i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
-            const float4 r4 = rel[i];
-            const double x = (double)r4.x * w, y = (double)r4.y * w, z = (double)r4.z * w;
-            double F = 0.0, Fx = 0.0, Fy = 0.0, Fz = 0.0;
-            // rolled loops: FP64 arithmetic, not issue, is the limit, and full
-            // unrolling would hoist every shared-memory load into registers
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        // the cell with off[cell] <= i < off[cell + 1]
+        int lo = 0, hi = C;  // off[lo] <= i < off[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(off + mid) <= i)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        const double* __restrict__ Tc = T + (size_t)lo * NT;
+        const float4 r4 = rel[i];
+        const double x = (double)r4.x * w, y = (double)r4.y * w, z = (double)r4.z * w;
+        double F = 0.0, Fx = 0.0, Fy = 0.0, Fz = 0.0;
+        // rolled loops: FP64 arithmetic, not issue, is the limit, and full
+        // unrolling would hoist every coefficient load into registers
 #pragma unroll 1
-            for (int a = P; a >= 0; --a) {
-                // terms with first index a start at NT - C(P - a + 3, 3)
-                const int base_a = NT - (P - a + 3) * (P - a + 2) * (P - a + 1) / 6;
-                double U = 0.0, Uy = 0.0, Uz = 0.0;
+        for (int a = P; a >= 0; --a) {
+            // terms with first index a start at NT - C(P - a + 3, 3)
+            const int base_a = NT - (P - a + 3) * (P - a + 2) * (P - a + 1) / 6;
+            double U = 0.0, Uy = 0.0, Uz = 0.0;
 #pragma unroll 1
-                for (int b = P - a; b >= 0; --b) {
-                    const int base = base_a + b * (P - a + 1) - b * (b - 1) / 2;
-                    double S = 0.0, Sz = 0.0;
-                    for (int c = P - a - b; c >= 0; --c) {
-                        Sz = fma(Sz, z, S);
-                        S = fma(S, z, Ts[base + c]);
-                    }
-                    Uy = fma(Uy, y, U);
-                    U = fma(U, y, S);
-                    Uz = fma(Uz, y, Sz);
+            for (int b = P - a; b >= 0; --b) {
+                const int base = base_a + b * (P - a + 1) - b * (b - 1) / 2;
+                double S = 0.0, Sz = 0.0;
+                for (int c = P - a - b; c >= 0; --c) {
+                    Sz = fma(Sz, z, S);
+                    S = fma(S, z, __ldg(Tc + base + c));
                 }
-                Fx = fma(Fx, x, F);
-                F = fma(F, x, U);
-                Fy = fma(Fy, x, Uy);
-                Fz = fma(Fz, x, Uz);
+                Uy = fma(Uy, y, U);
+                U = fma(U, y, S);
+                Uz = fma(Uz, y, Sz);
             }
-            const int orig = __float_as_int(r4.w);
-            const double ax = mass * Fx, ay = mass * Fy, az = mass * Fz;
-            if (acc_far) {
-                acc_far[3 * (size_t)orig] = ax;
-                acc_far[3 * (size_t)orig + 1] = ay;
-                acc_far[3 * (size_t)orig + 2] = az;
-            }
-            if (acc_add) {
-                acc_add[3 * (size_t)orig] += (float)ax;
-                acc_add[3 * (size_t)orig + 1] += (float)ay;
-                acc_add[3 * (size_t)orig + 2] += (float)az;
-            }
+            Fx = fma(Fx, x, F);
+            F = fma(F, x, U);
+            Fy = fma(Fy, x, Uy);
+            Fz = fma(Fz, x, Uz);
+        }
+        const int orig = __float_as_int(r4.w);
+        const double ax = mass * Fx, ay = mass * Fy, az = mass * Fz;
+        if (acc_far) {
+            acc_far[3 * (size_t)orig] = ax;
+            acc_far[3 * (size_t)orig + 1] = ay;
+            acc_far[3 * (size_t)orig + 2] = az;
+        }
+        if (acc_add) {
+            acc_add[3 * (size_t)orig] += (float)ax;
+            acc_add[3 * (size_t)orig + 1] += (float)ay;
+            acc_add[3 * (size_t)orig + 2] += (float)az;
         }
     }
 }
@@ -497,14 +513,15 @@ cudaError_t launch_deriv_real(int K, int R, int p, double box, double alpha, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_deriv_recip(int K, int p, double box, double alpha, int hmax, double2* Dh, cudaStream_t s)
+cudaError_t launch_deriv_recip(int K, int p, double box, double alpha, int hmax, const double2* Dh, double* Dr,
+                               cudaStream_t s)
 {
     const int nt = far_terms(p);
     const long long total = (long long)nt * K * K * (K / 2 + 1);
     long long blocks = (total + 255) / 256;
     const long long cap = (long long)device_sms() * 16;
     if (blocks > cap) blocks = cap;
-    k_deriv_recip<<<(int)blocks, 256, 0, s>>>(K, p, nt, box, alpha, hmax, Dh);
+    k_deriv_recip<<<(int)blocks, 256, 0, s>>>(K, p, nt, box, alpha, hmax, Dh, Dr);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -523,7 +540,7 @@ cudaError_t launch_far_pairs(int p, int* seg, FarPair* pairs, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_far_contract(int K, int p, const int* seg, const FarPair* pairs, const double2* Dh,
+cudaError_t launch_far_contract(int K, int p, const int* seg, const FarPair* pairs, const double* Dr,
                                 const double2* Mh, double2* Th, cudaStream_t s)
 {
     const long long nq = (long long)K * K * (K / 2 + 1);
@@ -531,19 +548,20 @@ cudaError_t launch_far_contract(int K, int p, const int* seg, const FarPair* pai
     const long long cap = (long long)device_sms() * 32;
     if (blocks > cap) blocks = cap;
     const double scale = 1.0 / ((double)K * K * K);  // the unnormalised inverse transform
-    k_far_contract<<<(int)blocks, 128, 0, s>>>(nq, far_terms(p), seg, pairs, Dh, Mh, Th, scale);
+    k_far_contract<<<(int)blocks, 128, 0, s>>>(nq, far_terms(p), seg, pairs, Dr, Mh, Th, scale);
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_taylor_forces(int p, const int* off, const float4* rel, const double* T, int C, double w,
+cudaError_t launch_taylor_forces(int p, const int* off, const float4* rel, const double* T, int N, int C, double w,
                                  double mass, double* acc_far, float* acc_add, cudaStream_t s)
 {
-    const int grid = C < device_sms() * 16 ? C : device_sms() * 16;
+    const int need = (N + 127) / 128;
+    const int grid = need < device_sms() * 16 ? need : device_sms() * 16;
     switch (p) {
 #define NF_TAYLOR_CASE(P)                                                                           \
     case P:                                                                                         \
-        k_taylor_forces<P><<<grid, 128, 0, s>>>(off, rel, T, C, w, mass, acc_far, acc_add);         \
+        k_taylor_forces<P><<<grid, 128, 0, s>>>(off, rel, T, N, C, w, mass, acc_far, acc_add);      \
         break;
         NF_TAYLOR_CASE(0)
         NF_TAYLOR_CASE(1)

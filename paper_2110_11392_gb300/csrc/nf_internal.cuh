@@ -86,7 +86,8 @@ struct StepScratch {
 // ---- far field (nf_far.cu) ----
 constexpr int kMaxFarOrder = 12;  // NF_MAX_FAR_ORDER
 constexpr int kMaxFarTerms = (kMaxFarOrder + 3) * (kMaxFarOrder + 2) * (kMaxFarOrder + 1) / 6;
-// One (n, k) pair of the Taylor convolution: terms k and j = n + k, coefficient (-1)^{|k|} / (n! k!).
+// One (n, k) pair of the Taylor convolution: terms k and j = n + k (the sign
+// bit of j set when |n| + |k| is odd), coefficient (-1)^{|k|} / (n! k!).
 struct FarPair {
     int k;
     int j;
@@ -113,17 +114,18 @@ size_t far_fft_work_bytes(int K, int nt);
 cudaError_t launch_far_fft(int K, int nt, bool forward, void* in, void* out, void* work, size_t work_bytes,
                            cudaStream_t s);
 cudaError_t launch_deriv_real(int K, int R, int p, double box, double alpha, int nimg, double* D, cudaStream_t s);
-cudaError_t launch_deriv_recip(int K, int p, double box, double alpha, int hmax, double2* Dh, cudaStream_t s);
+cudaError_t launch_deriv_recip(int K, int p, double box, double alpha, int hmax, const double2* Dh, double* Dr,
+                               cudaStream_t s);
 cudaError_t launch_far_pairs(int p, int* seg, FarPair* pairs, cudaStream_t s);
-cudaError_t launch_far_contract(int K, int p, const int* seg, const FarPair* pairs, const double2* Dh,
+cudaError_t launch_far_contract(int K, int p, const int* seg, const FarPair* pairs, const double* Dr,
                                 const double2* Mh, double2* Th, cudaStream_t s);
-cudaError_t launch_taylor_forces(int p, const int* off, const float4* rel, const double* T, int C, double w,
+cudaError_t launch_taylor_forces(int p, const int* off, const float4* rel, const double* T, int N, int C, double w,
                                  double mass, double* acc_far, float* acc_add, cudaStream_t s);
 
 // Counts kernel launches (all translation units).
-// FP32 multiply-add throughput probe (measurement aid)
+// multiply-add throughput probe (measurement aid); mode 0 f32, 1 f32x2, 2 f64
 size_t fma_probe_sink_floats();
-cudaError_t launch_fma_probe(float* sink, int iters, bool packed, double* flop, cudaStream_t s);
+cudaError_t launch_fma_probe(float* sink, int iters, int mode, double* flop, cudaStream_t s);
 void count_launches(int n);
 // Sets the dynamic shared-memory limit of a kernel once per (device, size).
 cudaError_t ensure_smem(const void* fn, int bytes);

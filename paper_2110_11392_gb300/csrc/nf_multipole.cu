@@ -7,8 +7,10 @@
 // SIMD loops; here one block takes one cell and one thread one term (a, b, c).
 // The particles of the cell (contiguous after binning) are taken 64 at a time:
 // threads first build the powers x^0..x^p, y^0..y^p, z^0..z^p of every particle
-// of the chunk in shared memory (one thread per particle and axis), then every
-// term thread accumulates x^a * y^b * z^c with one multiply and one FMA.
+// of the chunk in shared memory (one thread per particle and axis) and the
+// products x^a y^b (one per particle and (a, b) pair, the paper's
+// precomputation that turns the innermost update into an FMA), then every term
+// thread accumulates (x^a y^b) * z^c with one FMA per particle.
 // Arithmetic is FP64 throughout, as the paper keeps its far-field internals.
 #include <cuda_runtime.h>
 
@@ -23,8 +25,11 @@ constexpr int kChunk = 64;
 __global__ void k_multipoles(const int* __restrict__ off, const float4* __restrict__ rel, int C, double w, int p,
                              int nterms, double* __restrict__ M)
 {
-    extern __shared__ double pw[];  // [3][kChunk][p + 1]
+    // shared: powers [3][kChunk][p + 1], then x^a y^b products [kChunk][nab]
+    extern __shared__ double pw[];
     const int P1 = p + 1;
+    const int nab = (p + 1) * (p + 2) / 2;
+    double* XY = pw + (size_t)3 * kChunk * P1;
     // decode this thread's (a, b, c) from its term index, in the output order
     int a = 0, b = 0, c = 0;
     const int t = threadIdx.x;
@@ -42,6 +47,8 @@ __global__ void k_multipoles(const int* __restrict__ off, const float4* __restri
         }
         c = r;
     }
+    // index of (a, b) among the pairs a = 0..p, b = 0..p-a
+    const int ab = a * (p + 1) - a * (a - 1) / 2 + b;
     for (int cell = blockIdx.x; cell < C; cell += gridDim.x) {
         const int s0 = off[cell], s1 = off[cell + 1];
         double acc = 0.0;
@@ -61,11 +68,20 @@ __global__ void k_multipoles(const int* __restrict__ off, const float4* __restri
                 }
             }
             __syncthreads();
+            // x^a y^b once per particle and (a, b) pair
+            for (int i = threadIdx.x; i < nq * nab; i += blockDim.x) {
+                const int q = i / nab, k = i - q * nab;
+                int aa = 0, kk = k;
+                while (kk > p - aa) {
+                    kk -= p - aa + 1;
+                    ++aa;
+                }
+                XY[(size_t)q * nab + k] = pw[(size_t)q * P1 + aa] * pw[((size_t)kChunk + q) * P1 + kk];
+            }
+            __syncthreads();
             if (t < nterms) {
-                const double* X = pw;
-                const double* Y = pw + (size_t)kChunk * P1;
                 const double* Z = pw + (size_t)2 * kChunk * P1;
-                for (int q = 0; q < nq; ++q) acc = fma(X[q * P1 + a] * Y[q * P1 + b], Z[q * P1 + c], acc);
+                for (int q = 0; q < nq; ++q) acc = fma(XY[(size_t)q * nab + ab], Z[q * P1 + c], acc);
             }
         }
         if (t < nterms) M[(size_t)cell * nterms + t] = acc;
@@ -80,7 +96,7 @@ cudaError_t launch_multipoles(const int* off, const float4* rel, int C, double w
 {
     const int nterms = multipole_terms(p);
     const int threads = ((nterms + 31) / 32) * 32;
-    const size_t smem = (size_t)3 * kChunk * (p + 1) * sizeof(double);
+    const size_t smem = ((size_t)3 * kChunk * (p + 1) + (size_t)kChunk * (p + 1) * (p + 2) / 2) * sizeof(double);
     cudaError_t e = ensure_smem((const void*)k_multipoles, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;

@@ -1,7 +1,8 @@
-// FP32 fused multiply-add throughput probe: a measurement aid for the roofline
-// of the pair kernels, not part of the paper's method.  Every thread runs
-// kChains independent multiply-add chains (scalar FFMA, or packed .f32x2
-// pairs) so the FMA pipe, not latency, limits the rate.  The chain constants
+// Fused multiply-add throughput probe: a measurement aid for the rooflines of
+// the pair kernels (FP32) and of the far field (FP64), not part of the
+// paper's method.  Every thread runs kChains independent multiply-add chains
+// (scalar FP32, packed .f32x2 pairs, or FP64) so the pipe, not latency,
+// limits the rate.  The chain constants
 // keep every value normal and finite: x -> x * 0.999 + 0.001 converges to 1.
 #include <cuda_runtime.h>
 
@@ -35,12 +36,13 @@ __device__ __forceinline__ p2 ffma2(p2 a, p2 b, p2 c)
     return d;
 }
 
-template <bool PACKED>
+// MODE 0: scalar fma.rn.f32; 1: packed fma.rn.f32x2; 2: fma.rn.f64
+template <int MODE>
 __global__ void __launch_bounds__(kProbeThreads) k_fma_probe(float* __restrict__ sink, int iters, float m, float a)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     float s = 0.0f;
-    if constexpr (PACKED) {
+    if constexpr (MODE == 1) {
         p2 x[kChains];
         const p2 mm = pack2(m, m), aa = pack2(a, a);
 #pragma unroll
@@ -58,6 +60,20 @@ __global__ void __launch_bounds__(kProbeThreads) k_fma_probe(float* __restrict__
             unpack2(x[c], lo, hi);
             s += lo + hi;
         }
+    } else if constexpr (MODE == 2) {
+        double x[kChains];
+        const double md = (double)m, ad = (double)a;
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) x[c] = 0.5 + 1e-3 * c + 1e-6 * t;
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+#pragma unroll
+                for (int c = 0; c < kChains; ++c) x[c] = fma(x[c], md, ad);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) s += (float)x[c];
     } else {
         float x[kChains];
 #pragma unroll
@@ -87,16 +103,18 @@ int probe_blocks()
 
 size_t fma_probe_sink_floats() { return (size_t)probe_blocks() * kProbeThreads; }
 
-cudaError_t launch_fma_probe(float* sink, int iters, bool packed, double* flop, cudaStream_t s)
+cudaError_t launch_fma_probe(float* sink, int iters, int mode, double* flop, cudaStream_t s)
 {
     const int blocks = probe_blocks();
-    if (packed)
-        k_fma_probe<true><<<blocks, kProbeThreads, 0, s>>>(sink, iters, 0.999f, 0.001f);
+    if (mode == 1)
+        k_fma_probe<1><<<blocks, kProbeThreads, 0, s>>>(sink, iters, 0.999f, 0.001f);
+    else if (mode == 2)
+        k_fma_probe<2><<<blocks, kProbeThreads, 0, s>>>(sink, iters, 0.999f, 0.001f);
     else
-        k_fma_probe<false><<<blocks, kProbeThreads, 0, s>>>(sink, iters, 0.999f, 0.001f);
+        k_fma_probe<0><<<blocks, kProbeThreads, 0, s>>>(sink, iters, 0.999f, 0.001f);
     count_launches(1);
     // lanes x multiply-adds per lane x 2 flop
-    *flop = (double)blocks * kProbeThreads * iters * kUnroll * kChains * (packed ? 2 : 1) * 2.0;
+    *flop = (double)blocks * kProbeThreads * iters * kUnroll * kChains * (mode == 1 ? 2 : 1) * 2.0;
     return cudaGetLastError();
 }
 

@@ -134,7 +134,7 @@ def test_far_field_sizes_and_host_checks():
     nt = lambda p: (p + 3) * (p + 2) * (p + 1) // 6
     for K, p in [(5, 0), (8, 8), (11, 8), (32, 12)]:
         b = _lib.nf_derivatives_bytes(K, p)
-        assert b >= 16 * nt(p) * K * K * (K // 2 + 1) + 256
+        assert b >= 8 * nt(p) * K * K * (K // 2 + 1) + 256   # one real per (term, frequency)
         assert b % 256 == 0
         assert _lib.nf_far_workspace_bytes(1000, K, p) > 8 * nt(p) * K ** 3
     assert _lib.nf_derivatives_bytes(8, 13) == 0 and _lib.nf_derivatives_bytes(0, 4) == 0

@@ -4,7 +4,7 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("packed,chains", [(False, 8), (True, 16)])
+@pytest.mark.parametrize("packed,chains", [(0, 8), (1, 16), (2, 8)])
 def test_probe_values_and_flop_count(packed, chains):
     import torch
     from paper_2110_11392_gb300 import _lib
@@ -16,7 +16,7 @@ def test_probe_values_and_flop_count(packed, chains):
     flop = _lib.nf_fma_probe(sink, iters, packed)
     torch.cuda.synchronize()
     # n threads x iters x 16 trips x 8 chains x (2 lanes if packed) x 2 flop
-    assert flop == n * iters * 16 * 8 * (2 if packed else 1) * 2
+    assert flop == n * iters * 16 * 8 * (2 if packed == 1 else 1) * 2
     # x -> 0.999 x + 0.001 has its fixed point at 1: after 32768 trips every chain is 1
     assert torch.allclose(sink, torch.full_like(sink, float(chains)), rtol=0, atol=1e-3)
 
@@ -30,3 +30,5 @@ def test_probe_rejects_bad_arguments():
     sink = torch.empty(_lib.nf_fma_probe_sink_floats(), dtype=torch.float32, device="cuda")
     with pytest.raises(_lib.NFError):
         _lib.nf_fma_probe(sink, 0, True)
+    with pytest.raises(_lib.NFError):
+        _lib.nf_fma_probe(sink, 16, 3)
