@@ -295,34 +295,37 @@ __global__ void k_far_pairs(int p, int* __restrict__ seg, FarPair* __restrict__ 
 }
 
 // Th[n][q] = scale * sum_{pairs of n} coef * D^{n+k}(q) * Mh[k][q], one thread
-// per q.  D^{j}(q) is Dr[j][q] for even |j| and i Dr[j][q] for odd |j|, so a
-// pair costs one real-times-complex product (3 FP64 operations) instead of a
-// complex one.
-__global__ void __launch_bounds__(128) k_far_contract(long long nq, int nt, const int* __restrict__ seg,
+// per (n, q), q fastest: a warp shares n, so the pair list is a broadcast and
+// the Dr and Mh rows are read coalesced; one thread per q alone would leave
+// a few warps per SM waiting on their dependent FMA chains.  D^{j}(q) is
+// Dr[j][q] for even |j| and i Dr[j][q] for odd |j|, so a pair costs one
+// real-times-complex product (3 FP64 operations) instead of a complex one.
+__global__ void __launch_bounds__(256) k_far_contract(long long nq, int nt, const int* __restrict__ seg,
                                                       const FarPair* __restrict__ pairs,
                                                       const double* __restrict__ Dr,
                                                       const double2* __restrict__ Mh, double2* __restrict__ Th,
                                                       double scale)
 {
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq;
-         q += (long long)gridDim.x * blockDim.x) {
-        for (int n = 0; n < nt; ++n) {
-            double re = 0.0, im = 0.0;
-            const int e1 = seg[n + 1];
-            for (int e = seg[n]; e < e1; ++e) {
-                const FarPair pr = pairs[e];
-                const double cd = pr.coef * Dr[(size_t)(pr.j & 0x7fffffff) * nq + q];
-                const double2 m = Mh[(size_t)pr.k * nq + q];
-                if (pr.j < 0) {  // odd |j|: i * cd * m
-                    re = fma(-cd, m.y, re);
-                    im = fma(cd, m.x, im);
-                } else {
-                    re = fma(cd, m.x, re);
-                    im = fma(cd, m.y, im);
-                }
+    const long long total = nq * nt;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int n = (int)(e / nq);
+        const long long q = e - (long long)n * nq;
+        double re = 0.0, im = 0.0;
+        const int e1 = seg[n + 1];
+        for (int i = seg[n]; i < e1; ++i) {
+            const FarPair pr = pairs[i];
+            const double cd = pr.coef * Dr[(size_t)(pr.j & 0x7fffffff) * nq + q];
+            const double2 m = Mh[(size_t)pr.k * nq + q];
+            if (pr.j < 0) {  // odd |j|: i * cd * m
+                re = fma(-cd, m.y, re);
+                im = fma(cd, m.x, im);
+            } else {
+                re = fma(cd, m.x, re);
+                im = fma(cd, m.y, im);
             }
-            Th[(size_t)n * nq + q] = make_double2(scale * re, scale * im);
         }
+        Th[e] = make_double2(scale * re, scale * im);
     }
 }
 
@@ -544,11 +547,11 @@ cudaError_t launch_far_contract(int K, int p, const int* seg, const FarPair* pai
                                 const double2* Mh, double2* Th, cudaStream_t s)
 {
     const long long nq = (long long)K * K * (K / 2 + 1);
-    long long blocks = (nq + 127) / 128;
-    const long long cap = (long long)device_sms() * 32;
+    long long blocks = (nq * far_terms(p) + 255) / 256;
+    const long long cap = (long long)device_sms() * 64;
     if (blocks > cap) blocks = cap;
     const double scale = 1.0 / ((double)K * K * K);  // the unnormalised inverse transform
-    k_far_contract<<<(int)blocks, 128, 0, s>>>(nq, far_terms(p), seg, pairs, Dr, Mh, Th, scale);
+    k_far_contract<<<(int)blocks, 256, 0, s>>>(nq, far_terms(p), seg, pairs, Dr, Mh, Th, scale);
     count_launches(1);
     return cudaGetLastError();
 }
