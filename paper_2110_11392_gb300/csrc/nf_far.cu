@@ -317,13 +317,14 @@ __global__ void __launch_bounds__(256) k_far_contract(long long nq, int nt, cons
             const FarPair pr = pairs[i];
             const double cd = pr.coef * Dr[(size_t)(pr.j & 0x7fffffff) * nq + q];
             const double2 m = Mh[(size_t)pr.k * nq + q];
-            if (pr.j < 0) {  // odd |j|: i * cd * m
-                re = fma(-cd, m.y, re);
-                im = fma(cd, m.x, im);
-            } else {
-                re = fma(cd, m.x, re);
-                im = fma(cd, m.y, im);
-            }
+            // odd |j|: i * cd * m = (-cd m.y, cd m.x).  The rotation is done with
+            // integer selects and a sign-bit flip, so the FP64 pipe sees exactly
+            // one multiply and two FMAs per pair.
+            const bool odd = pr.j < 0;
+            const double mr = odd ? m.y : m.x, mi = odd ? m.x : m.y;
+            const double cr = __longlong_as_double(__double_as_longlong(cd) ^ (odd ? (long long)0x8000000000000000ull : 0ll));
+            re = fma(cr, mr, re);
+            im = fma(cd, mi, im);
         }
         Th[e] = make_double2(scale * re, scale * im);
     }
