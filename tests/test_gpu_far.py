@@ -155,3 +155,35 @@ def test_argument_errors():
     assert _lib.nf_derivatives_bytes(8, 13) == 0
     with pytest.raises(_lib.NFError):
         nf.FarField(4, 2, 4)            # K < 2R + 1 is caught by the library
+
+
+@pytest.mark.parametrize("K,p", [(6, 12), (5, 10)])
+def test_highest_orders_match_oracle(K, p):
+    import torch
+    import paper_2110_11392_gb300 as nf
+    pos = _uniform(2000, 31)
+    a = nf.FarField(K, 2, p)(to_dev(pos))
+    torch.cuda.synchronize()
+    aref = oracle.far_field(pos, 1.0, K, 2, p)
+    assert np.abs(a.cpu().numpy() - aref).max() < 1e-10 * np.abs(aref).max()
+
+
+def test_sparse_cells_faces_and_wrapping():
+    # far fewer particles than cells (most cells empty), particles on cell
+    # faces, and coordinates outside [0, box) that must wrap like nf_forces
+    import torch
+    import paper_2110_11392_gb300 as nf
+    K = 12
+    rng = np.random.default_rng(8)
+    pos = rng.random((300, 3))
+    pos[:40] = np.round(pos[:40] * K) / K                    # exactly on faces
+    pos[40:80] += rng.integers(-3, 4, size=(40, 3))          # whole boxes away
+    pos = pos.astype(np.float32)
+    a = nf.FarField(K, 2, 6)(to_dev(pos))
+    torch.cuda.synchronize()
+    aref = oracle.far_field(pos, 1.0, K, 2, 6)
+    assert np.abs(a.cpu().numpy() - aref).max() < 1e-10 * np.abs(aref).max()
+    # the same particles moved by whole boxes feel the same force
+    b = nf.FarField(K, 2, 6)(to_dev(((pos.astype(np.float64) % 1.0) % 1.0).astype(np.float32)))
+    torch.cuda.synchronize()
+    assert np.abs(a.cpu().numpy() - b.cpu().numpy()).max() < 1e-6 * np.abs(aref).max()
