@@ -316,10 +316,17 @@ int nf_derivatives(int K, int R, int p, double box, void *derivs, size_t derivs_
  * bytes.  Asynchronous on `stream` and graph-capturable once the cuFFT plans
  * exist (after the first call for this (K, p)).  Errors: as nf_derivatives;
  * NF_ERR_ARG also when `derivs` was made for another (K, R, p, box) by this
- * process. */
+ * process; NF_ERR_CUDA with cuFFT's status in nf_last_error() if a
+ * transform fails. */
 int nf_far_forces(const float *pos, int64_t N, double box, int K, int R, int p,
                   const void *derivs, size_t derivs_bytes, double *acc_far, float *acc_add,
                   double *taylors, void *ws, size_t ws_bytes, void *stream);
+
+/* Destroys the cuFFT plans the far-field calls keep per (device, K, p), e.g.
+ * before cudaDeviceReset or to return cuFFT's tables; later calls create them
+ * again (so the next call must not be captured into a graph).  Call only
+ * when no far-field work is being enqueued.  Always NF_OK. */
+int nf_far_release(void);
 
 /* ------------------------------------------------------------------------ */
 /* Time stepping (Sec. "Time Stepping": Kick-Drift-Kick leapfrog with a      */

@@ -69,7 +69,9 @@ def build_library(force: bool = False, verbose: bool = False, extra_flags: List[
     if failed:
         raise RuntimeError(f"nvcc failed on {failed}")
     tmp = LIB + f".{os.getpid()}.tmp"
-    subprocess.check_call([cc, "-shared", *ARCH, "-o", tmp, *objs, *LINK_LIBS])
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(cc)), "lib64")
+    rpath = ["-Xlinker", "-rpath", "-Xlinker", cuda_lib] if os.path.isdir(cuda_lib) else []
+    subprocess.check_call([cc, "-shared", *ARCH, "-o", tmp, *objs, *LINK_LIBS, *rpath])
     os.replace(tmp, LIB)
     return LIB
 

@@ -100,6 +100,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         "nf_derivatives": (i32, [i32, i32, i32, f64, P, sz, P, sz, P]),
         "nf_far_forces": (i32, [P, i64, f64, i32, i32, i32, P, sz, P, P, P, P, sz, P]),
         "nf_far_profile_read": (i32, [i32, P]),
+        "nf_far_release": (i32, []),
         "nf_set_debug": (i32, [i32]),
         "nf_debug_check": (i32, [P, P]),
         "nf_fma_probe_sink_floats": (sz, []),
@@ -121,7 +122,7 @@ def exported_symbols() -> Sequence[str]:
             "nf_kernel_launches", "nf_forces_noalloc", "nf_forces_density", "nf_timestep",
             "nf_kdk_step", "nf_multipoles", "nf_set_debug", "nf_debug_check",
             "nf_derivatives_bytes", "nf_far_workspace_bytes", "nf_derivatives", "nf_far_forces",
-            "nf_far_profile_read",
+            "nf_far_profile_read", "nf_far_release",
             "nf_fma_probe_sink_floats", "nf_fma_probe")
 
 
@@ -350,6 +351,10 @@ def nf_far_forces(pos: torch.Tensor, box: float, K: int, R: int, p: int, derivs:
     _check(load().nf_far_forces(_ptr(pos), pos.shape[0], float(box), int(K), int(R), int(p), _ptr(derivs),
                                 _nbytes(derivs), _ptr(acc_far), _ptr(acc_add), _ptr(taylors), _ptr(ws),
                                 _nbytes(ws), _stream(stream)), "nf_far_forces")
+
+
+def nf_far_release() -> None:
+    _check(load().nf_far_release(), "nf_far_release")
 
 
 def nf_set_debug(on: bool) -> None:

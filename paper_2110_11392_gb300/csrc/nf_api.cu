@@ -746,6 +746,24 @@ int far_validate(int K, int R, int p, double box)
 
 }  // namespace
 
+namespace {
+
+int fft_fail(cudaError_t e, const char* where)
+{
+    if (e == cudaErrorMemoryAllocation) return fail(NF_ERR_WORKSPACE, "%s: cuFFT work area larger than reserved", where);
+    if (e == cudaErrorUnknown) return fail(NF_ERR_CUDA, "%s: cuFFT status %d", where, far_fft_last_status());
+    return cuda_fail(e, where);
+}
+
+}  // namespace
+
+int nf_far_release(void)
+{
+    g_last_error.clear();
+    far_release_plans();
+    return NF_OK;
+}
+
 size_t nf_derivatives_bytes(int K, int p)
 {
     if (!far_args_ok(K, p)) return 0;
@@ -789,8 +807,7 @@ int nf_derivatives(int K, int R, int p, double box, void* derivs, size_t derivs_
     double2* Dh = at<double2>(ws, F.o_Mh);
     NF_CUDA(launch_deriv_real(K, R, p, box, alpha, kFarNimg, D, s), "derivatives (real space)");
     cudaError_t e = launch_far_fft(K, L.nt, true, D, Dh, at<void>(ws, F.o_work), F.work, s);
-    if (e == cudaErrorMemoryAllocation) return fail(NF_ERR_WORKSPACE, "cuFFT work area larger than reserved");
-    if (e != cudaSuccess) return cuda_fail(e, "derivatives (forward FFT)");
+    if (e != cudaSuccess) return fft_fail(e, "derivatives (forward FFT)");
     NF_CUDA(launch_deriv_recip(K, p, box, alpha, kFarHmax, Dh, at<double>(derivs, L.o_dh), s),
             "derivatives (reciprocal space)");
     NF_CUDA(launch_far_pairs(p, at<int>(derivs, L.o_seg), at<FarPair>(derivs, L.o_pairs), s), "convolution pairs");
@@ -862,16 +879,14 @@ int nf_far_forces(const float* pos, int64_t N, double box, int K, int R, int p, 
     NF_CUDA(launch_multipoles(off, rel, C, box / K, p, M, s), "multipoles");
     NF_CUDA(prof_mark(2, s), "profile");
     cudaError_t e = launch_far_fft(K, L.nt, true, M, Mh, at<void>(ws, F.o_work), F.work, s);
-    if (e == cudaErrorMemoryAllocation) return fail(NF_ERR_WORKSPACE, "cuFFT work area larger than reserved");
-    if (e != cudaSuccess) return cuda_fail(e, "multipoles (forward FFT)");
+    if (e != cudaSuccess) return fft_fail(e, "multipoles (forward FFT)");
     NF_CUDA(launch_far_contract(K, p, at<const int>(const_cast<void*>(derivs), L.o_seg),
                                 at<const FarPair>(const_cast<void*>(derivs), L.o_pairs),
                                 at<const double>(const_cast<void*>(derivs), L.o_dh), Mh, Th, s),
             "convolution");
     double* T = M;  // the multipoles are no longer needed
     e = launch_far_fft(K, L.nt, false, Th, T, at<void>(ws, F.o_work), F.work, s);
-    if (e == cudaErrorMemoryAllocation) return fail(NF_ERR_WORKSPACE, "cuFFT work area larger than reserved");
-    if (e != cudaSuccess) return cuda_fail(e, "Taylors (inverse FFT)");
+    if (e != cudaSuccess) return fft_fail(e, "Taylors (inverse FFT)");
     NF_CUDA(prof_mark(3, s), "profile");
     if (acc_far || acc_add)
         NF_CUDA(launch_taylor_forces(p, off, rel, T, (int)N, C, box / K, 1.0 / (double)N, acc_far, acc_add, s),

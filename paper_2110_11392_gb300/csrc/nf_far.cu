@@ -418,6 +418,7 @@ struct PlanEntry {
 };
 std::mutex g_fft_mu;
 std::map<std::tuple<int, int, int, int>, PlanEntry> g_plans;
+thread_local int g_cufft_status = 0;  // cuFFT's status of the last failed transform
 
 cufftResult plan_layout(int K, int nt, bool forward, cufftHandle h, size_t* work, bool estimate_only)
 {
@@ -445,8 +446,15 @@ cudaError_t get_plan(int K, int nt, bool forward, PlanEntry* out)
         return cudaSuccess;
     }
     PlanEntry pe;
-    if (cufftCreate(&pe.h) != CUFFT_SUCCESS) return cudaErrorUnknown;
-    if (cufftSetAutoAllocation(pe.h, 0) != CUFFT_SUCCESS || plan_layout(K, nt, forward, pe.h, &pe.work, false) != CUFFT_SUCCESS) {
+    cufftResult r = cufftCreate(&pe.h);
+    if (r != CUFFT_SUCCESS) {
+        g_cufft_status = (int)r;
+        return cudaErrorUnknown;
+    }
+    r = cufftSetAutoAllocation(pe.h, 0);
+    if (r == CUFFT_SUCCESS) r = plan_layout(K, nt, forward, pe.h, &pe.work, false);
+    if (r != CUFFT_SUCCESS) {
+        g_cufft_status = (int)r;
         cufftDestroy(pe.h);
         return cudaErrorUnknown;
     }
@@ -497,11 +505,31 @@ cudaError_t launch_far_fft(int K, int nt, bool forward, void* in, void* out, voi
     cudaError_t e = get_plan(K, nt, forward, &pe);
     if (e != cudaSuccess) return e;
     if (pe.work > work_bytes) return cudaErrorMemoryAllocation;
-    if (cufftSetStream(pe.h, s) != CUFFT_SUCCESS || cufftSetWorkArea(pe.h, work) != CUFFT_SUCCESS)
+    cufftResult r = cufftSetStream(pe.h, s);
+    if (r == CUFFT_SUCCESS) r = cufftSetWorkArea(pe.h, work);
+    if (r == CUFFT_SUCCESS)
+        r = forward ? cufftExecD2Z(pe.h, (cufftDoubleReal*)in, (cufftDoubleComplex*)out)
+                    : cufftExecZ2D(pe.h, (cufftDoubleComplex*)in, (cufftDoubleReal*)out);
+    if (r != CUFFT_SUCCESS) {
+        g_cufft_status = (int)r;
         return cudaErrorUnknown;
-    const cufftResult r = forward ? cufftExecD2Z(pe.h, (cufftDoubleReal*)in, (cufftDoubleComplex*)out)
-                                  : cufftExecZ2D(pe.h, (cufftDoubleComplex*)in, (cufftDoubleReal*)out);
-    return r == CUFFT_SUCCESS ? cudaGetLastError() : cudaErrorUnknown;
+    }
+    return cudaGetLastError();
+}
+
+int far_fft_last_status() { return g_cufft_status; }
+
+void far_release_plans()
+{
+    std::lock_guard<std::mutex> lk(g_fft_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto& kv : g_plans) {
+        cudaSetDevice(std::get<0>(kv.first));
+        cufftDestroy(kv.second.h);
+    }
+    g_plans.clear();
+    cudaSetDevice(cur);
 }
 
 cudaError_t launch_deriv_real(int K, int R, int p, double box, double alpha, int nimg, double* D, cudaStream_t s)

@@ -113,6 +113,8 @@ size_t far_fft_work_bytes(int K, int nt);
 // forward: real cell-major [K^3][nt] -> complex term-major [nt][K][K][K/2+1]; inverse the reverse
 cudaError_t launch_far_fft(int K, int nt, bool forward, void* in, void* out, void* work, size_t work_bytes,
                            cudaStream_t s);
+int far_fft_last_status();   // cuFFT status behind the last cudaErrorUnknown of launch_far_fft
+void far_release_plans();    // destroys every cached cuFFT plan
 cudaError_t launch_deriv_real(int K, int R, int p, double box, double alpha, int nimg, double* D, cudaStream_t s);
 cudaError_t launch_deriv_recip(int K, int p, double box, double alpha, int hmax, const double2* Dh, double* Dr,
                                cudaStream_t s);

@@ -1,8 +1,8 @@
 /*
  * Plain-C use of libnf's C ABI (include/nf.h): no Python, no torch.
  * Allocates device memory with the CUDA runtime, bins a small uniform box,
- * computes near-field accelerations and the adjoint, and prints a summary
- * line that the test compares with its own expectations.
+ * computes near-field accelerations, the adjoint and the far field, and
+ * prints a summary line that the test compares with its own expectations.
  *
  * Build (see tests/test_gpu_c_abi.py):
  *   gcc -O2 -I include tests/c_abi/nf_c_example.c -o nf_c_example \
@@ -88,10 +88,30 @@ int main(void)
     CHECK_NF(nf_forces_adjoint(pos, g, N, box, K, R, eps, grad, ws, ws_bytes, s));
     CHECK_NF(nf_status_read(ws, s));
 
-    printf("ok N=%lld pairs=%lld items=%lld maxocc=%lld net=%.3e mean_abs_acc=%.6e acc0=%.9e %.9e %.9e\n",
+    /* far field at order 4: derivatives once, then the far accelerations in FP64 */
+    const int p = 4;
+    void *derivs, *wsf;
+    double *far;
+    const size_t d_bytes = nf_derivatives_bytes(K, p), f_bytes = nf_far_workspace_bytes(N, K, p);
+    if (d_bytes == 0 || f_bytes == 0) return 5;
+    CHECK_CUDA(cudaMalloc(&derivs, d_bytes));
+    CHECK_CUDA(cudaMalloc(&wsf, f_bytes));
+    CHECK_CUDA(cudaMalloc((void **)&far, sizeof(double) * 3 * N));
+    CHECK_NF(nf_derivatives(K, R, p, box, derivs, d_bytes, wsf, f_bytes, s));
+    CHECK_NF(nf_far_forces(pos, N, box, K, R, p, derivs, d_bytes, far, NULL, NULL, wsf, f_bytes, s));
+    CHECK_NF(nf_status_read(wsf, s));
+    double h_far[3];
+    CHECK_CUDA(cudaMemcpy(h_far, far, sizeof(double) * 3, cudaMemcpyDeviceToHost));
+    CHECK_NF(nf_far_release());
+
+    printf("ok N=%lld pairs=%lld items=%lld maxocc=%lld net=%.3e mean_abs_acc=%.6e acc0=%.9e %.9e %.9e "
+           "far0=%.15e %.15e %.15e\n",
            (long long)N, (long long)stats[0], (long long)stats[1], (long long)stats[2],
            fmax(fabs(h_net[0]), fmax(fabs(h_net[1]), fabs(h_net[2]))), sum_abs / (3.0 * N),
-           h_acc[0], h_acc[1], h_acc[2]);
+           h_acc[0], h_acc[1], h_acc[2], h_far[0], h_far[1], h_far[2]);
+    cudaFree(derivs);
+    cudaFree(wsf);
+    cudaFree(far);
     cudaFree(pos);
     cudaFree(acc);
     cudaFree(g);

@@ -53,5 +53,9 @@ def test_c_example_runs_and_matches_oracle(tmp_path):
     eps = 1.0 / (40.0 * np.cbrt(N))
     ref = oracle.forces(pos, 1.0, 7, 2, eps, sinks=np.array([0]))[0]
     assert np.linalg.norm(acc0 - ref) / np.linalg.norm(ref) < 1e-5
+    assert line[10].startswith("far0=")
+    far0 = np.array([float(line[10][5:]), float(line[11]), float(line[12])])
+    fref = oracle.far_field(pos, 1.0, 7, 2, 4)
+    assert np.abs(far0 - fref[0]).max() < 1e-10 * np.abs(fref).max()
     assert int(kv["N"]) == N and int(kv["pairs"]) > 0 and int(kv["items"]) > 0
     assert float(kv["net"]) < 1e-3 * float(kv["mean_abs_acc"])

@@ -187,3 +187,16 @@ def test_sparse_cells_faces_and_wrapping():
     b = nf.FarField(K, 2, 6)(to_dev(((pos.astype(np.float64) % 1.0) % 1.0).astype(np.float32)))
     torch.cuda.synchronize()
     assert np.abs(a.cpu().numpy() - b.cpu().numpy()).max() < 1e-6 * np.abs(aref).max()
+
+
+def test_release_recreates_plans():
+    import torch
+    import paper_2110_11392_gb300 as nf
+    from paper_2110_11392_gb300 import _lib
+    pos = to_dev(_uniform(3000, 2))
+    ff = nf.FarField(7, 2, 5)
+    a = ff(pos)
+    _lib.nf_far_release()
+    b = ff(pos)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
