@@ -518,6 +518,25 @@ def measure_far(w, pos, dev, flush, fma, fwd_ms, p=8, reps=5):
         b.record(stream)
         b.synchronize()
         tot_ms.append(a.elapsed_time(b))
+    # leapfrog steps with the total force (nf_kdk_step_far, adaptive dt)
+    rng = np.random.default_rng(9)
+    xs = pos.clone()
+    vel = torch.from_numpy((0.01 * rng.standard_normal((w.N, 3))).astype(np.float32)).to(dev)
+    acc_t = torch.empty((w.N, 3), dtype=torch.float32, device=dev)
+    _lib.nf_forces(xs, w.box, w.K, w.R, w.eps, acc_t, None, wsn)
+    _lib.nf_far_forces(xs, w.box, w.K, w.R, p, ff.derivs, None, acc_t, None, ws)
+    dt = torch.zeros(1, dtype=torch.float64, device=dev)
+    prm = _lib.make_step_params(0.25)
+    _lib.nf_timestep(xs, vel, acc_t, w.box, w.K, prm, dt, wsn)
+    step_ms = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = ev(), ev()
+        a.record(stream)
+        _lib.nf_kdk_step_far(xs, vel, acc_t, w.box, w.K, w.R, w.eps, p, ff.derivs, dt, prm, wsn, ws)
+        b.record(stream)
+        b.synchronize()
+        step_ms.append(a.elapsed_time(b))
     stage = {k: float(np.median([q[k] for q in prof])) for k in prof[0]}
     t_ms = float(np.median(far_ms))
     flop = taylor_flop_per_particle(p) * w.N
@@ -528,6 +547,8 @@ def measure_far(w, pos, dev, flush, fma, fwd_ms, p=8, reps=5):
             "total_force_ms": float(np.median(tot_ms)),
             "total_force_particles_per_s": w.N / (float(np.median(tot_ms)) / 1e3),
             "near_forward_ms": fwd_ms,
+            "kdk_total_force_ms_per_step": float(np.median(step_ms)),
+            "kdk_total_force_particle_updates_per_s": w.N / (float(np.median(step_ms)) / 1e3),
             "taylor_roofline": {"bound": "fp64", "achieved": taylor_tf, "peak": peak64, "unit": "TFLOP/s",
                                 "frac": taylor_tf / peak64, "flop_per_particle": taylor_flop_per_particle(p),
                                 "peak_basis": "measured: nf_fma_probe fma.rn.f64, this run"},

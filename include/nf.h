@@ -364,6 +364,21 @@ int nf_timestep(const float *pos, const float *vel, const float *acc, int64_t N,
 int nf_kdk_step(float *pos, float *vel, float *acc, int64_t N, double box, int K, int R, double eps,
                 double *dt, const nf_step_params *prm, void *ws, size_t ws_bytes, void *stream);
 
+/* One leapfrog step with the total force, near + far, all on the device:
+ *     vel += acc dt/2;  pos = wrap(pos + vel dt);
+ *     acc = nf_forces(pos) + nf_far_forces(pos);  vel += acc dt/2;
+ * then, when prm != NULL, dt = Eq. (timestep) at the new state (as
+ * nf_kdk_step).  acc (FP32 [N][3]) must hold the total acceleration at the
+ * input positions.  derivs comes from nf_derivatives for (K, R, p, box) (the
+ * far field, Sec. "Far-field Computation"); ws is
+ * a near-field workspace (nf_workspace_bytes(N, K, R)) and ws_far a far-field
+ * one (nf_far_workspace_bytes(N, K, p)).  Graph-capturable once the cuFFT
+ * plans for (K, p) exist.  Errors as nf_kdk_step and nf_far_forces. */
+int nf_kdk_step_far(float *pos, float *vel, float *acc, int64_t N, double box, int K, int R, double eps,
+                    int p, const void *derivs, size_t derivs_bytes, double *dt, const nf_step_params *prm,
+                    void *ws, size_t ws_bytes, void *ws_far, size_t ws_far_bytes, void *stream);
+
+
 /* ------------------------------------------------------------------------ */
 /* Status and statistics                                                     */
 /* ------------------------------------------------------------------------ */

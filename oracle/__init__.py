@@ -253,10 +253,13 @@ def timestep(vel, acc, cell, eta_acc: float, eta_h: float = 0.0, hubble: float =
     return float(dt)
 
 
-def kdk_step(pos, vel, acc, dt: float, box: float, K: int, R: int, eps: float):
+def kdk_step(pos, vel, acc, dt: float, box: float, K: int, R: int, eps: float,
+             far_order: Optional[int] = None, D: Optional[np.ndarray] = None):
     """One leapfrog step: v += a dt/2; x += v dt (wrapped into [0, box)); a = F(x);
     v += a dt/2.  State stored as the API stores it (FP32 positions and
-    velocities); arithmetic in FP64.  Returns (pos, vel, acc_FP64)."""
+    velocities); arithmetic in FP64.  F is the near field, plus the far field
+    of order far_order (derivatives D, computed when not given) when far_order
+    is set.  Returns (pos, vel, acc_FP64)."""
     pos = np.asarray(pos, np.float32)
     v = np.asarray(vel, np.float32).astype(np.float64)
     a = np.asarray(acc, np.float64)
@@ -265,6 +268,8 @@ def kdk_step(pos, vel, acc, dt: float, box: float, K: int, R: int, eps: float):
     x = np.mod(x, box).astype(np.float32)
     x[x >= np.float32(box)] = np.float32(0.0)
     a_new = forces(x, box, K, R, eps)
+    if far_order is not None:
+        a_new = a_new + far_field(x, box, K, R, far_order, D=D)
     v_new = (v_half.astype(np.float64) + 0.5 * dt * a_new).astype(np.float32)
     return x, v_new, a_new
 

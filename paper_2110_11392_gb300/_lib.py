@@ -101,6 +101,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         "nf_far_forces": (i32, [P, i64, f64, i32, i32, i32, P, sz, P, P, P, P, sz, P]),
         "nf_far_profile_read": (i32, [i32, P]),
         "nf_far_release": (i32, []),
+        "nf_kdk_step_far": (i32, [P, P, P, i64, f64, i32, i32, f64, i32, P, sz, P, P, P, sz, P, sz, P]),
         "nf_set_debug": (i32, [i32]),
         "nf_debug_check": (i32, [P, P]),
         "nf_fma_probe_sink_floats": (sz, []),
@@ -122,7 +123,7 @@ def exported_symbols() -> Sequence[str]:
             "nf_kernel_launches", "nf_forces_noalloc", "nf_forces_density", "nf_timestep",
             "nf_kdk_step", "nf_multipoles", "nf_set_debug", "nf_debug_check",
             "nf_derivatives_bytes", "nf_far_workspace_bytes", "nf_derivatives", "nf_far_forces",
-            "nf_far_profile_read", "nf_far_release",
+            "nf_far_profile_read", "nf_far_release", "nf_kdk_step_far",
             "nf_fma_probe_sink_floats", "nf_fma_probe")
 
 
@@ -351,6 +352,15 @@ def nf_far_forces(pos: torch.Tensor, box: float, K: int, R: int, p: int, derivs:
     _check(load().nf_far_forces(_ptr(pos), pos.shape[0], float(box), int(K), int(R), int(p), _ptr(derivs),
                                 _nbytes(derivs), _ptr(acc_far), _ptr(acc_add), _ptr(taylors), _ptr(ws),
                                 _nbytes(ws), _stream(stream)), "nf_far_forces")
+
+
+def nf_kdk_step_far(pos: torch.Tensor, vel: torch.Tensor, acc: torch.Tensor, box: float, K: int, R: int,
+                    eps: float, p: int, derivs: torch.Tensor, dt: torch.Tensor, prm, ws: torch.Tensor,
+                    ws_far: torch.Tensor, stream=None) -> None:
+    _check(load().nf_kdk_step_far(_ptr(pos), _ptr(vel), _ptr(acc), pos.shape[0], float(box), int(K), int(R),
+                                  float(eps), int(p), _ptr(derivs), _nbytes(derivs), _ptr(dt),
+                                  None if prm is None else ctypes.byref(prm), _ptr(ws), _nbytes(ws),
+                                  _ptr(ws_far), _nbytes(ws_far), _stream(stream)), "nf_kdk_step_far")
 
 
 def nf_far_release() -> None:

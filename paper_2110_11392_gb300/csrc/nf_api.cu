@@ -835,18 +835,26 @@ int nf_derivatives(int K, int R, int p, double box, void* derivs, size_t derivs_
     return NF_OK;
 }
 
-int nf_far_forces(const float* pos, int64_t N, double box, int K, int R, int p, const void* derivs,
-                  size_t derivs_bytes, double* acc_far, float* acc_add, double* taylors, void* ws, size_t ws_bytes,
-                  void* stream)
+namespace {
+
+// A validated far-field call: its binning plan and the layouts of the
+// derivatives buffer and of the workspace.
+struct FarCall {
+    Plan pl;
+    FarLayout F;
+    DerivLayout L;
+};
+
+int far_prepare(const float* pos, int64_t N, double box, int K, int R, int p, const void* derivs,
+                size_t derivs_bytes, void* ws, size_t ws_bytes, FarCall* fc)
 {
-    g_last_error.clear();
     int rc = far_validate(K, R, p, box);
     if (rc) return rc;
     if (!pos || !derivs) return fail(NF_ERR_ARG, "null pointer argument");
-    const DerivLayout L = deriv_layout(K, p);
-    if (derivs_bytes < L.total)
+    fc->L = deriv_layout(K, p);
+    if (derivs_bytes < fc->L.total)
         return fail(NF_ERR_ARG, "derivs too small for K = %d, p = %d: %zu bytes given, %zu needed", K, p,
-                    derivs_bytes, L.total);
+                    derivs_bytes, fc->L.total);
     {
         std::lock_guard<std::mutex> lk(g_deriv_mu);
         auto it = g_derivs.find(derivs);
@@ -857,27 +865,36 @@ int nf_far_forces(const float* pos, int64_t N, double box, int K, int R, int p, 
         }
     }
     nf_box b = one_box(N, box, K, 0, 0.0);
-    Plan pl;
-    rc = make_plan(&b, 1, false, 32, &pl);
+    rc = make_plan(&b, 1, false, 32, &fc->pl);
     if (rc) return rc;
-    const FarLayout F = far_layout(pl, K, p);
-    rc = check_ws(pl, ws, ws_bytes);
+    fc->F = far_layout(fc->pl, K, p);
+    rc = check_ws(fc->pl, ws, ws_bytes);
     if (rc) return rc;
-    if (ws_bytes < F.total)
-        return fail(NF_ERR_WORKSPACE, "workspace too small: %zu bytes given, %zu needed", ws_bytes, F.total);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (ws_bytes < fc->F.total)
+        return fail(NF_ERR_WORKSPACE, "far workspace too small: %zu bytes given, %zu needed", ws_bytes, fc->F.total);
+    return NF_OK;
+}
+
+// Binning, multipoles, convolution, Taylor forces (profile marks when `profile`).
+int run_far(const FarCall& fc, const float* pos, int64_t N, double box, int K, int p, const void* derivs,
+            double* acc_far, float* acc_add, double* taylors, void* ws, cudaStream_t s, bool profile)
+{
+    const Plan& pl = fc.pl;
+    const FarLayout& F = fc.F;
+    const DerivLayout& L = fc.L;
+    auto mark = [&](int i) { return profile ? prof_mark(i, s) : cudaSuccess; };
     int32_t* off = at<int32_t>(ws, pl.o_off);
     float4* rel = at<float4>(ws, pl.o_rel);
-    NF_CUDA(prof_mark(0, s), "profile");
-    rc = run_binning(pl, pos, ws, off, rel, at<int32_t>(ws, pl.o_perm), s);
+    NF_CUDA(mark(0), "profile");
+    int rc = run_binning(pl, pos, ws, off, rel, at<int32_t>(ws, pl.o_perm), s);
     if (rc) return rc;
-    NF_CUDA(prof_mark(1, s), "profile");
+    NF_CUDA(mark(1), "profile");
     const int C = (int)pl.C;
     double* M = at<double>(ws, F.o_M);
     double2* Mh = at<double2>(ws, F.o_Mh);
     double2* Th = at<double2>(ws, F.o_Th);
     NF_CUDA(launch_multipoles(off, rel, C, box / K, p, M, s), "multipoles");
-    NF_CUDA(prof_mark(2, s), "profile");
+    NF_CUDA(mark(2), "profile");
     cudaError_t e = launch_far_fft(K, L.nt, true, M, Mh, at<void>(ws, F.o_work), F.work, s);
     if (e != cudaSuccess) return fft_fail(e, "multipoles (forward FFT)");
     NF_CUDA(launch_far_contract(K, p, at<const int>(const_cast<void*>(derivs), L.o_seg),
@@ -887,14 +904,68 @@ int nf_far_forces(const float* pos, int64_t N, double box, int K, int R, int p, 
     double* T = M;  // the multipoles are no longer needed
     e = launch_far_fft(K, L.nt, false, Th, T, at<void>(ws, F.o_work), F.work, s);
     if (e != cudaSuccess) return fft_fail(e, "Taylors (inverse FFT)");
-    NF_CUDA(prof_mark(3, s), "profile");
+    NF_CUDA(mark(3), "profile");
     if (acc_far || acc_add)
         NF_CUDA(launch_taylor_forces(p, off, rel, T, (int)N, C, box / K, 1.0 / (double)N, acc_far, acc_add, s),
                 "Taylor forces");
-    NF_CUDA(prof_mark(4, s), "profile");
-    if (g_profile_on) ++g_prof_count;
+    NF_CUDA(mark(4), "profile");
+    if (profile && g_profile_on) ++g_prof_count;
     if (taylors)
         NF_CUDA(cudaMemcpyAsync(taylors, T, 8 * (size_t)L.nt * C, cudaMemcpyDeviceToDevice, s), "Taylors copy");
+    return NF_OK;
+}
+
+}  // namespace
+
+int nf_far_forces(const float* pos, int64_t N, double box, int K, int R, int p, const void* derivs,
+                  size_t derivs_bytes, double* acc_far, float* acc_add, double* taylors, void* ws, size_t ws_bytes,
+                  void* stream)
+{
+    g_last_error.clear();
+    FarCall fc;
+    int rc = far_prepare(pos, N, box, K, R, p, derivs, derivs_bytes, ws, ws_bytes, &fc);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    rc = run_far(fc, pos, N, box, K, p, derivs, acc_far, acc_add, taylors, ws, s, true);
+    if (rc) return rc;
+    return finish_call(ws, s);
+}
+
+int nf_kdk_step_far(float* pos, float* vel, float* acc, int64_t N, double box, int K, int R, double eps, int p,
+                    const void* derivs, size_t derivs_bytes, double* dt, const nf_step_params* prm, void* ws,
+                    size_t ws_bytes, void* ws_far, size_t ws_far_bytes, void* stream)
+{
+    g_last_error.clear();
+    nf_box b = one_box(N, box, K, R, eps);
+    ForceTuning t;
+    int rc = check_tuning(nullptr, &t);
+    if (rc) return rc;
+    Plan pn;
+    rc = make_plan(&b, 1, true, 32 * t.sinks_per_lane, &pn);
+    if (rc) return rc;
+    if (!pos || !vel || !acc || !dt) return fail(NF_ERR_ARG, "null pointer argument");
+    if (prm && (!(prm->eta_acc > 0.0) || !(prm->hubble >= 0.0) || (prm->hubble > 0.0 && !(prm->eta_h > 0.0))))
+        return fail(NF_ERR_ARG, "step parameters need eta_acc > 0, hubble >= 0 and eta_h > 0 when hubble > 0");
+    rc = check_ws(pn, ws, ws_bytes);
+    if (rc) return rc;
+    FarCall fc;
+    rc = far_prepare(pos, N, box, K, R, p, derivs, derivs_bytes, ws_far, ws_far_bytes, &fc);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    NF_CUDA(launch_kick(vel, acc, (int)N, dt, 0.5, s), "kick");
+    NF_CUDA(launch_drift(pos, vel, (int)N, dt, (float)box, s), "drift");
+    rc = run_forces(pn, false, t, pos, nullptr, acc, nullptr, nullptr, ws, s);
+    if (rc) return rc;
+    rc = run_far(fc, pos, N, box, K, p, derivs, nullptr, acc, nullptr, ws_far, s, false);
+    if (rc) return rc;
+    NF_CUDA(launch_kick(vel, acc, (int)N, dt, 0.5, s), "kick");
+    if (prm)
+        NF_CUDA(launch_timestep(at<int32_t>(ws, pn.o_off), at<int32_t>(ws, pn.o_perm), vel, acc, (int)pn.C,
+                                (long long)N, prm->eta_acc, prm->eta_h, prm->hubble, at<StepScratch>(ws, pn.o_step),
+                                dt, s),
+                "time step");
+    rc = finish_call(ws_far, s);
+    if (rc) return rc;
     return finish_call(ws, s);
 }
 

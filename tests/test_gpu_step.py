@@ -131,3 +131,41 @@ def test_adaptive_loop_in_a_cuda_graph_is_bit_identical():
     for a, b in zip((pos, v, acc, dt), eager):
         assert torch.equal(a, b)
     assert 0 < dt.item() < 1.0
+
+
+def test_kdk_with_far_field_matches_oracle():
+    # total force (near + far at order 4): two leapfrog steps against the oracle's
+    import torch
+    import paper_2110_11392_gb300 as nf
+    from paper_2110_11392_gb300 import _lib
+    w, vel = _state(seed=9)
+    p = 4
+    ff = nf.FarField(w.K, w.R, p, w.box)
+    pos, v = to_dev(w.pos), to_dev(vel)
+    acc = nf.forces(pos, w.box, w.K, w.R, w.eps)
+    ff(pos, add_to=acc, want_far=False)
+    dt_val = 2e-3
+    dt = torch.full((1,), dt_val, dtype=torch.float64, device="cuda")
+    ws = _ws(w)
+    wsf = ff.workspace(w.N)
+    D = oracle.derivatives(w.K, w.R, p, w.box)
+    xo, vo = w.pos, vel
+    ao = oracle.forces(w.pos, w.box, w.K, w.R, w.eps) + oracle.far_field(w.pos, w.box, w.K, w.R, p, D=D)
+    for _ in range(2):
+        _lib.nf_kdk_step_far(pos, v, acc, w.box, w.K, w.R, w.eps, p, ff.derivs, dt, None, ws, wsf)
+        xo, vo, ao = oracle.kdk_step(xo, vo, ao, dt_val, w.box, w.K, w.R, w.eps, far_order=p, D=D)
+    torch.cuda.synchronize()
+    xg, vg, ag = pos.cpu().numpy(), v.cpu().numpy(), acc.cpu().numpy()
+    dx = (xg.astype(np.float64) - xo + 0.5) % 1.0 - 0.5
+    assert np.abs(dx).max() < 1e-6
+    dv = np.linalg.norm(vg - vo, axis=1) / np.linalg.norm(vo, axis=1)
+    assert np.median(dv) < 1e-6 and dv.max() < 1e-3
+    ref = oracle.forces(xg, w.box, w.K, w.R, w.eps) + oracle.far_field(xg, w.box, w.K, w.R, p, D=D)
+    assert_force_parity(ag, ref, label="near + far after 2 steps")
+    # the adaptive form writes the next step's dt from the same criterion
+    prm = _lib.make_step_params(ETA)
+    _lib.nf_kdk_step_far(pos, v, acc, w.box, w.K, w.R, w.eps, p, ff.derivs, dt, prm, ws, wsf)
+    torch.cuda.synchronize()
+    cell = oracle.cell_of(pos.cpu().numpy(), w.box, w.K)
+    ref_dt = oracle.timestep(v.cpu().numpy(), acc.cpu().numpy().astype(np.float64), cell, ETA)
+    assert dt.item() == pytest.approx(ref_dt, rel=1e-5)
