@@ -476,8 +476,8 @@ def taylor_flop_per_particle(p: int) -> int:
 def measure_far(w, pos, dev, flush, fma, fwd_ms, p=8, reps=5):
     """The far field at order p on the same particles: derivatives once, then
     nf_far_forces per call (binning, multipoles, FFT convolution, Taylors);
-    and the total force of a user's step, nf_forces + nf_far_forces adding
-    into its output."""
+    the total force of a user's step (nf_forces_total: near + far, one
+    binning); and leapfrog steps with that force (nf_kdk_step_far)."""
     import torch
     import paper_2110_11392_gb300 as nf
     from paper_2110_11392_gb300 import _lib
@@ -513,8 +513,7 @@ def measure_far(w, pos, dev, flush, fma, fwd_ms, p=8, reps=5):
         flush.zero_()
         a, b = ev(), ev()
         a.record(stream)
-        _lib.nf_forces(pos, w.box, w.K, w.R, w.eps, tot, None, wsn)
-        _lib.nf_far_forces(pos, w.box, w.K, w.R, p, ff.derivs, None, tot, None, ws)
+        _lib.nf_forces_total(pos, w.box, w.K, w.R, w.eps, p, ff.derivs, tot, wsn, ws)
         b.record(stream)
         b.synchronize()
         tot_ms.append(a.elapsed_time(b))

@@ -322,6 +322,15 @@ int nf_far_forces(const float *pos, int64_t N, double box, int K, int R, int p,
                   const void *derivs, size_t derivs_bytes, double *acc_far, float *acc_add,
                   double *taylors, void *ws, size_t ws_bytes, void *stream);
 
+/* The periodic force, near + far, in one call: acc (FP32 [N][3], input
+ * order) = nf_forces(pos) + the far field of order p, binning the particles
+ * once for both.  derivs from nf_derivatives for (K, R, p, box); ws a
+ * near-field workspace (nf_workspace_bytes(N, K, R)), ws_far a far-field one
+ * (nf_far_workspace_bytes(N, K, p)).  Errors as nf_forces and nf_far_forces. */
+int nf_forces_total(const float *pos, int64_t N, double box, int K, int R, double eps, int p,
+                    const void *derivs, size_t derivs_bytes, float *acc, void *ws, size_t ws_bytes,
+                    void *ws_far, size_t ws_far_bytes, void *stream);
+
 /* Destroys the cuFFT plans the far-field calls keep per (device, K, p), e.g.
  * before cudaDeviceReset or to return cuFFT's tables; later calls create them
  * again (so the next call must not be captured into a graph).  Call only

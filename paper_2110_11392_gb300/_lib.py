@@ -101,6 +101,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         "nf_far_forces": (i32, [P, i64, f64, i32, i32, i32, P, sz, P, P, P, P, sz, P]),
         "nf_far_profile_read": (i32, [i32, P]),
         "nf_far_release": (i32, []),
+        "nf_forces_total": (i32, [P, i64, f64, i32, i32, f64, i32, P, sz, P, P, sz, P, sz, P]),
         "nf_kdk_step_far": (i32, [P, P, P, i64, f64, i32, i32, f64, i32, P, sz, P, P, P, sz, P, sz, P]),
         "nf_set_debug": (i32, [i32]),
         "nf_debug_check": (i32, [P, P]),
@@ -123,7 +124,7 @@ def exported_symbols() -> Sequence[str]:
             "nf_kernel_launches", "nf_forces_noalloc", "nf_forces_density", "nf_timestep",
             "nf_kdk_step", "nf_multipoles", "nf_set_debug", "nf_debug_check",
             "nf_derivatives_bytes", "nf_far_workspace_bytes", "nf_derivatives", "nf_far_forces",
-            "nf_far_profile_read", "nf_far_release", "nf_kdk_step_far",
+            "nf_far_profile_read", "nf_far_release", "nf_kdk_step_far", "nf_forces_total",
             "nf_fma_probe_sink_floats", "nf_fma_probe")
 
 
@@ -361,6 +362,13 @@ def nf_kdk_step_far(pos: torch.Tensor, vel: torch.Tensor, acc: torch.Tensor, box
                                   float(eps), int(p), _ptr(derivs), _nbytes(derivs), _ptr(dt),
                                   None if prm is None else ctypes.byref(prm), _ptr(ws), _nbytes(ws),
                                   _ptr(ws_far), _nbytes(ws_far), _stream(stream)), "nf_kdk_step_far")
+
+
+def nf_forces_total(pos: torch.Tensor, box: float, K: int, R: int, eps: float, p: int, derivs: torch.Tensor,
+                    acc: torch.Tensor, ws: torch.Tensor, ws_far: torch.Tensor, stream=None) -> None:
+    _check(load().nf_forces_total(_ptr(pos), pos.shape[0], float(box), int(K), int(R), float(eps), int(p),
+                                  _ptr(derivs), _nbytes(derivs), _ptr(acc), _ptr(ws), _nbytes(ws), _ptr(ws_far),
+                                  _nbytes(ws_far), _stream(stream)), "nf_forces_total")
 
 
 def nf_far_release() -> None:

@@ -876,18 +876,30 @@ int far_prepare(const float* pos, int64_t N, double box, int K, int R, int p, co
 }
 
 // Binning, multipoles, convolution, Taylor forces (profile marks when `profile`).
+// With binned != nullptr the particles are already binned on this grid (the
+// cell offsets and sorted offsets of a near-field call on the same positions)
+// and the far call reuses them.
+struct Binned {
+    const int32_t* off;
+    const float4* rel;
+};
+
 int run_far(const FarCall& fc, const float* pos, int64_t N, double box, int K, int p, const void* derivs,
-            double* acc_far, float* acc_add, double* taylors, void* ws, cudaStream_t s, bool profile)
+            double* acc_far, float* acc_add, double* taylors, void* ws, cudaStream_t s, bool profile,
+            const Binned* binned = nullptr)
 {
     const Plan& pl = fc.pl;
     const FarLayout& F = fc.F;
     const DerivLayout& L = fc.L;
     auto mark = [&](int i) { return profile ? prof_mark(i, s) : cudaSuccess; };
-    int32_t* off = at<int32_t>(ws, pl.o_off);
-    float4* rel = at<float4>(ws, pl.o_rel);
+    const int32_t* off = binned ? binned->off : at<int32_t>(ws, pl.o_off);
+    const float4* rel = binned ? binned->rel : at<float4>(ws, pl.o_rel);
     NF_CUDA(mark(0), "profile");
-    int rc = run_binning(pl, pos, ws, off, rel, at<int32_t>(ws, pl.o_perm), s);
-    if (rc) return rc;
+    if (!binned) {
+        int rc = run_binning(pl, pos, ws, at<int32_t>(ws, pl.o_off), at<float4>(ws, pl.o_rel),
+                             at<int32_t>(ws, pl.o_perm), s);
+        if (rc) return rc;
+    }
     NF_CUDA(mark(1), "profile");
     const int C = (int)pl.C;
     double* M = at<double>(ws, F.o_M);
@@ -931,6 +943,35 @@ int nf_far_forces(const float* pos, int64_t N, double box, int K, int R, int p, 
     return finish_call(ws, s);
 }
 
+int nf_forces_total(const float* pos, int64_t N, double box, int K, int R, double eps, int p, const void* derivs,
+                    size_t derivs_bytes, float* acc, void* ws, size_t ws_bytes, void* ws_far, size_t ws_far_bytes,
+                    void* stream)
+{
+    g_last_error.clear();
+    nf_box b = one_box(N, box, K, R, eps);
+    ForceTuning t;
+    int rc = check_tuning(nullptr, &t);
+    if (rc) return rc;
+    Plan pn;
+    rc = make_plan(&b, 1, true, 32 * t.sinks_per_lane, &pn);
+    if (rc) return rc;
+    if (!pos || !acc) return fail(NF_ERR_ARG, "null pointer argument");
+    rc = check_ws(pn, ws, ws_bytes);
+    if (rc) return rc;
+    FarCall fc;
+    rc = far_prepare(pos, N, box, K, R, p, derivs, derivs_bytes, ws_far, ws_far_bytes, &fc);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    rc = run_forces(pn, false, t, pos, nullptr, acc, nullptr, nullptr, ws, s);
+    if (rc) return rc;
+    const Binned bn{at<int32_t>(ws, pn.o_off), at<float4>(ws, pn.o_rel)};
+    rc = run_far(fc, pos, N, box, K, p, derivs, nullptr, acc, nullptr, ws_far, s, false, &bn);
+    if (rc) return rc;
+    rc = finish_call(ws_far, s);
+    if (rc) return rc;
+    return finish_call(ws, s);
+}
+
 int nf_kdk_step_far(float* pos, float* vel, float* acc, int64_t N, double box, int K, int R, double eps, int p,
                     const void* derivs, size_t derivs_bytes, double* dt, const nf_step_params* prm, void* ws,
                     size_t ws_bytes, void* ws_far, size_t ws_far_bytes, void* stream)
@@ -956,7 +997,8 @@ int nf_kdk_step_far(float* pos, float* vel, float* acc, int64_t N, double box, i
     NF_CUDA(launch_drift(pos, vel, (int)N, dt, (float)box, s), "drift");
     rc = run_forces(pn, false, t, pos, nullptr, acc, nullptr, nullptr, ws, s);
     if (rc) return rc;
-    rc = run_far(fc, pos, N, box, K, p, derivs, nullptr, acc, nullptr, ws_far, s, false);
+    const Binned bn{at<int32_t>(ws, pn.o_off), at<float4>(ws, pn.o_rel)};
+    rc = run_far(fc, pos, N, box, K, p, derivs, nullptr, acc, nullptr, ws_far, s, false, &bn);
     if (rc) return rc;
     NF_CUDA(launch_kick(vel, acc, (int)N, dt, 0.5, s), "kick");
     if (prm)

@@ -131,6 +131,15 @@ class FarField:
     def workspace(self, N: int) -> torch.Tensor:
         return workspace(_lib.nf_far_workspace_bytes(N, self.K, self.p), self.device, key="far")
 
+    def total(self, pos: torch.Tensor, eps: float, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """The periodic force near + far (nf_forces_total), FP32 [N, 3]: one binning for both."""
+        pos = _check_pos(pos)
+        N = pos.shape[0]
+        acc = out if out is not None else torch.empty_like(pos)
+        ws = workspace(_lib.nf_workspace_bytes(N, self.K, self.R), self.device)
+        _lib.nf_forces_total(pos, self.box, self.K, self.R, eps, self.p, self.derivs, acc, ws, self.workspace(N))
+        return acc
+
     def __call__(self, pos: torch.Tensor, add_to: Optional[torch.Tensor] = None, want_far: bool = True,
                  want_taylors: bool = False, ws: Optional[torch.Tensor] = None):
         pos = _check_pos(pos)

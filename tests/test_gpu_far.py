@@ -200,3 +200,17 @@ def test_release_recreates_plans():
     b = ff(pos)
     torch.cuda.synchronize()
     assert torch.equal(a, b)
+
+
+def test_total_force_call_equals_near_plus_far():
+    import torch
+    import paper_2110_11392_gb300 as nf
+    pos = to_dev(_clustered(20000, 9, 12))
+    ff = nf.FarField(9, 2, 6)
+    eps = 1e-3
+    near = nf.forces(pos, 1.0, 9, 2, eps)
+    ref = near.clone()
+    ff(pos, add_to=ref, want_far=False)
+    tot = ff.total(pos, eps)
+    torch.cuda.synchronize()
+    assert torch.equal(tot, ref)
