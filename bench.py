@@ -473,6 +473,15 @@ def taylor_flop_per_particle(p: int) -> int:
     return 2 * (2 * nt + 3 * nab + 4 * (p + 1))
 
 
+def taylor_df_ops_per_particle(p: int) -> int:
+    """FP32 instructions of the double-float Taylor evaluation at one particle:
+    the Horner steps of taylor_flop_per_particle, 14 FP32 instructions each
+    (product with its FMA error terms, TwoSum, two adds, FastTwoSum)."""
+    nt = (p + 3) * (p + 2) * (p + 1) // 6
+    nab = (p + 2) * (p + 1) // 2
+    return 14 * (2 * nt + 3 * nab + 4 * (p + 1))
+
+
 def measure_far(w, pos, dev, flush, fma, fwd_ms, p=8, reps=5):
     """The far field at order p on the same particles: derivatives once, then
     nf_far_forces per call (binning, multipoles, FFT convolution, Taylors);
@@ -494,6 +503,25 @@ def measure_far(w, pos, dev, flush, fma, fwd_ms, p=8, reps=5):
     acc = torch.empty((w.N, 3), dtype=torch.float64, device=dev)
     wsn = torch.empty(_lib.nf_workspace_bytes(w.N, w.K, w.R), dtype=torch.uint8, device=dev)
     tot = torch.empty((w.N, 3), dtype=torch.float32, device=dev)
+    def far_call_ms():
+        for _ in range(2):
+            _lib.nf_far_forces(pos, w.box, w.K, w.R, p, ff.derivs, acc, None, None, ws)
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = ev(), ev()
+            a.record(stream)
+            _lib.nf_far_forces(pos, w.box, w.K, w.R, p, ff.derivs, acc, None, None, ws)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return float(np.median(ms))
+    # the other arithmetic of the per-particle kernels, for comparison
+    arith = _lib.nf_far_get_arith()
+    other = _lib.NF_FAR_FP64 if arith == _lib.NF_FAR_DOUBLE_FLOAT else _lib.NF_FAR_DOUBLE_FLOAT
+    _lib.nf_far_set_arith(other)
+    other_ms = far_call_ms()
+    _lib.nf_far_set_arith(arith)
     for _ in range(2):
         _lib.nf_far_forces(pos, w.box, w.K, w.R, p, ff.derivs, acc, None, None, ws)
     _lib.nf_profile_enable(True)
@@ -538,9 +566,22 @@ def measure_far(w, pos, dev, flush, fma, fwd_ms, p=8, reps=5):
         step_ms.append(a.elapsed_time(b))
     stage = {k: float(np.median([q[k] for q in prof])) for k in prof[0]}
     t_ms = float(np.median(far_ms))
-    flop = taylor_flop_per_particle(p) * w.N
-    taylor_tf = flop / (stage["taylor_ms"] / 1e3) / 1e12
-    peak64 = fma["fp64_tflops"]
+    if arith == _lib.NF_FAR_DOUBLE_FLOAT:
+        # FP32-pipe bound: instructions per second against the measured scalar FP32 rate
+        ops = taylor_df_ops_per_particle(p) * w.N
+        achieved = ops / (stage["taylor_ms"] / 1e3) / 1e12
+        peak32 = fma["scalar_tflops"] / 2.0  # one FMA = 2 flop = 1 instruction
+        taylor_roof = {"bound": "alu", "achieved": achieved, "peak": peak32, "unit": "T FP32 instructions/s",
+                       "frac": achieved / peak32, "op_per_particle": taylor_df_ops_per_particle(p),
+                       "peak_basis": "measured: nf_fma_probe fma.rn.f32 rate / 2, this run"}
+    else:
+        flop = taylor_flop_per_particle(p) * w.N
+        achieved = flop / (stage["taylor_ms"] / 1e3) / 1e12
+        peak64 = fma["fp64_tflops"]
+        taylor_roof = {"bound": "fp64", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
+                       "frac": achieved / peak64, "flop_per_particle": taylor_flop_per_particle(p),
+                       "peak_basis": "measured: nf_fma_probe fma.rn.f64, this run"}
+    names = {_lib.NF_FAR_FP64: "fp64", _lib.NF_FAR_DOUBLE_FLOAT: "double-float"}
     return {"order": p, "terms": (p + 3) * (p + 2) * (p + 1) // 6, "derivatives_ms": deriv_ms,
             "ms": t_ms, "particles_per_s": w.N / (t_ms / 1e3), "stages_ms": stage,
             "total_force_ms": float(np.median(tot_ms)),
@@ -548,11 +589,10 @@ def measure_far(w, pos, dev, flush, fma, fwd_ms, p=8, reps=5):
             "near_forward_ms": fwd_ms,
             "kdk_total_force_ms_per_step": float(np.median(step_ms)),
             "kdk_total_force_particle_updates_per_s": w.N / (float(np.median(step_ms)) / 1e3),
-            "taylor_roofline": {"bound": "fp64", "achieved": taylor_tf, "peak": peak64, "unit": "TFLOP/s",
-                                "frac": taylor_tf / peak64, "flop_per_particle": taylor_flop_per_particle(p),
-                                "peak_basis": "measured: nf_fma_probe fma.rn.f64, this run"},
-            "note": "FP64 throughout; derivatives once per (K, R, p, box); Ewald-summed periodic force "
-                    "= near + far"}
+            "arith": names[arith], "other_arith": {"arith": names[other], "ms": other_ms},
+            "taylor_roofline": taylor_roof,
+            "note": "derivatives, FFTs and k-space product in FP64; multipoles and Taylors in the stated "
+                    "arithmetic; derivatives once per (K, R, p, box); Ewald-summed periodic force = near + far"}
 
 
 def measure_multipoles(w, pos, dev, flush, p=8, reps=3):

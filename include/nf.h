@@ -275,7 +275,9 @@ int nf_multipoles(const float *pos, int64_t N, double box, int K, int p, double 
  * Taylor index n and multipole index k with |n| + |k| <= p, both in the
  * complete basis of (p+3)(p+2)(p+1)/6 terms (ordered as in nf_multipoles).
  * The uniform background of Ewald summation is included (the mean density
- * exerts no force).  Arithmetic is FP64; the FFTs are cuFFT's. */
+ * exerts no force).  Arithmetic: FP64 for the derivatives, FFTs and k-space
+ * product; FP64 or double-float for the per-particle kernels (see
+ * nf_far_set_arith).  The FFTs are cuFFT's. */
 #define NF_MAX_FAR_ORDER 12
 
 /* Bytes of a derivatives buffer for grid K and order p (0 if out of range):
@@ -330,6 +332,22 @@ int nf_far_forces(const float *pos, int64_t N, double box, int K, int R, int p,
 int nf_forces_total(const float *pos, int64_t N, double box, int K, int R, double eps, int p,
                     const void *derivs, size_t derivs_bytes, float *acc, void *ws, size_t ws_bytes,
                     void *ws_far, size_t ws_far_bytes, void *stream);
+
+/* Arithmetic of the per-particle far-field kernels (the multipoles and the
+ * Taylor evaluation), process-wide.  The paper keeps every internal
+ * far-field computation in double precision to avoid round-off build-up.
+ * NF_FAR_FP64 does so with IEEE binary64 arithmetic, which GB300 runs at
+ * 1/64 of its FP32 rate.  NF_FAR_DOUBLE_FLOAT (the default) keeps each value
+ * as an unevaluated sum of two FP32 numbers, held exact by error-free
+ * transformations, on the FP32 pipe: about 48 significant bits.  Both modes
+ * give the same far field to ~1e-13 relative.  The FFTs, the k-space
+ * product and the derivatives are FP64 in both.  nf_far_set_arith returns
+ * NF_ERR_ARG for another mode; calls already enqueued keep the mode they
+ * were enqueued with. */
+#define NF_FAR_FP64 0
+#define NF_FAR_DOUBLE_FLOAT 1
+int nf_far_set_arith(int mode);
+int nf_far_get_arith(void);
 
 /* Destroys the cuFFT plans the far-field calls keep per (device, K, p), e.g.
  * before cudaDeviceReset or to return cuFFT's tables; later calls create them

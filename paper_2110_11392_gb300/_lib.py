@@ -101,6 +101,8 @@ def load(build: bool = True) -> ctypes.CDLL:
         "nf_far_forces": (i32, [P, i64, f64, i32, i32, i32, P, sz, P, P, P, P, sz, P]),
         "nf_far_profile_read": (i32, [i32, P]),
         "nf_far_release": (i32, []),
+        "nf_far_set_arith": (i32, [i32]),
+        "nf_far_get_arith": (i32, []),
         "nf_forces_total": (i32, [P, i64, f64, i32, i32, f64, i32, P, sz, P, P, sz, P, sz, P]),
         "nf_kdk_step_far": (i32, [P, P, P, i64, f64, i32, i32, f64, i32, P, sz, P, P, P, sz, P, sz, P]),
         "nf_set_debug": (i32, [i32]),
@@ -125,6 +127,7 @@ def exported_symbols() -> Sequence[str]:
             "nf_kdk_step", "nf_multipoles", "nf_set_debug", "nf_debug_check",
             "nf_derivatives_bytes", "nf_far_workspace_bytes", "nf_derivatives", "nf_far_forces",
             "nf_far_profile_read", "nf_far_release", "nf_kdk_step_far", "nf_forces_total",
+            "nf_far_set_arith", "nf_far_get_arith",
             "nf_fma_probe_sink_floats", "nf_fma_probe")
 
 
@@ -369,6 +372,17 @@ def nf_forces_total(pos: torch.Tensor, box: float, K: int, R: int, eps: float, p
     _check(load().nf_forces_total(_ptr(pos), pos.shape[0], float(box), int(K), int(R), float(eps), int(p),
                                   _ptr(derivs), _nbytes(derivs), _ptr(acc), _ptr(ws), _nbytes(ws), _ptr(ws_far),
                                   _nbytes(ws_far), _stream(stream)), "nf_forces_total")
+
+
+NF_FAR_FP64, NF_FAR_DOUBLE_FLOAT = 0, 1
+
+
+def nf_far_set_arith(mode: int) -> None:
+    _check(load().nf_far_set_arith(int(mode)), "nf_far_set_arith")
+
+
+def nf_far_get_arith() -> int:
+    return int(load().nf_far_get_arith())
 
 
 def nf_far_release() -> None:

@@ -732,6 +732,9 @@ struct DerivKey {
     int K, R, p;
     double box;
 };
+// Arithmetic of the per-particle far-field kernels (multipoles, Taylor
+// evaluation): NF_FAR_DOUBLE_FLOAT or NF_FAR_FP64; process-wide.
+std::atomic<int> g_far_arith{NF_FAR_DOUBLE_FLOAT};
 std::mutex g_deriv_mu;
 std::map<const void*, DerivKey> g_derivs;
 
@@ -756,6 +759,17 @@ int fft_fail(cudaError_t e, const char* where)
 }
 
 }  // namespace
+
+int nf_far_set_arith(int mode)
+{
+    g_last_error.clear();
+    if (mode != NF_FAR_FP64 && mode != NF_FAR_DOUBLE_FLOAT)
+        return fail(NF_ERR_ARG, "far-field arithmetic %d is neither NF_FAR_FP64 nor NF_FAR_DOUBLE_FLOAT", mode);
+    g_far_arith.store(mode);
+    return NF_OK;
+}
+
+int nf_far_get_arith(void) { return g_far_arith.load(); }
 
 int nf_far_release(void)
 {
@@ -810,7 +824,8 @@ int nf_derivatives(int K, int R, int p, double box, void* derivs, size_t derivs_
     if (e != cudaSuccess) return fft_fail(e, "derivatives (forward FFT)");
     NF_CUDA(launch_deriv_recip(K, p, box, alpha, kFarHmax, Dh, at<double>(derivs, L.o_dh), s),
             "derivatives (reciprocal space)");
-    NF_CUDA(launch_far_pairs(p, at<int>(derivs, L.o_seg), at<FarPair>(derivs, L.o_pairs), s), "convolution pairs");
+    NF_CUDA(launch_far_pairs(p, box / K, at<int>(derivs, L.o_seg), at<FarPair>(derivs, L.o_pairs), s),
+            "convolution pairs");
     DerivHeader h;
     std::memset(&h, 0, sizeof h);
     h.magic = kDerivMagic;
@@ -905,7 +920,12 @@ int run_far(const FarCall& fc, const float* pos, int64_t N, double box, int K, i
     double* M = at<double>(ws, F.o_M);
     double2* Mh = at<double2>(ws, F.o_Mh);
     double2* Th = at<double2>(ws, F.o_Th);
-    NF_CUDA(launch_multipoles(off, rel, C, box / K, p, M, s), "multipoles");
+    // cell units throughout: displacements / w (the stored offsets), T'^n = T^n w^{|n|}
+    const bool dfl = g_far_arith.load() == NF_FAR_DOUBLE_FLOAT;
+    if (dfl)
+        NF_CUDA(launch_multipoles_df(off, rel, C, p, M, s), "multipoles (double-float)");
+    else
+        NF_CUDA(launch_multipoles(off, rel, C, 1.0, p, M, s), "multipoles");
     NF_CUDA(mark(2), "profile");
     cudaError_t e = launch_far_fft(K, L.nt, true, M, Mh, at<void>(ws, F.o_work), F.work, s);
     if (e != cudaSuccess) return fft_fail(e, "multipoles (forward FFT)");
@@ -917,13 +937,15 @@ int run_far(const FarCall& fc, const float* pos, int64_t N, double box, int K, i
     e = launch_far_fft(K, L.nt, false, Th, T, at<void>(ws, F.o_work), F.work, s);
     if (e != cudaSuccess) return fft_fail(e, "Taylors (inverse FFT)");
     NF_CUDA(mark(3), "profile");
-    if (acc_far || acc_add)
-        NF_CUDA(launch_taylor_forces(p, off, rel, T, (int)N, C, box / K, 1.0 / (double)N, acc_far, acc_add, s),
-                "Taylor forces");
+    const double scale = 1.0 / ((double)N * (box / K));  // m / w: cell-unit gradient to box units
+    if ((acc_far || acc_add) && dfl)  // the spectrum region is free again: it holds the coefficient pairs
+        NF_CUDA(launch_taylor_forces_df(p, off, rel, T, Th, (int)N, C, scale, acc_far, acc_add, s),
+                "Taylor forces (double-float)");
+    else if (acc_far || acc_add)
+        NF_CUDA(launch_taylor_forces(p, off, rel, T, (int)N, C, 1.0, scale, acc_far, acc_add, s), "Taylor forces");
     NF_CUDA(mark(4), "profile");
     if (profile && g_profile_on) ++g_prof_count;
-    if (taylors)
-        NF_CUDA(cudaMemcpyAsync(taylors, T, 8 * (size_t)L.nt * C, cudaMemcpyDeviceToDevice, s), "Taylors copy");
+    if (taylors) NF_CUDA(launch_unscale_taylors(T, C, p, box / K, taylors, s), "Taylors (box units)");
     return NF_OK;
 }
 

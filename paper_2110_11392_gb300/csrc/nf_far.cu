@@ -264,14 +264,19 @@ __global__ void k_deriv_recip(int K, int p, int nt, double box, double alpha, in
 }
 
 // The (n, k) pairs of the convolution, grouped by n: seg[n]..seg[n+1] index
-// pairs (k, n+k) with coefficient (-1)^{|k|} / (n! k!); the sign bit of j
-// marks an odd total order.  One thread.
-__global__ void k_far_pairs(int p, int* __restrict__ seg, FarPair* __restrict__ pairs)
+// pairs (k, n+k) with coefficient (-1)^{|k|} w^{|n|+|k|} / (n! k!); the sign
+// bit of j marks an odd total order.  The factor w^{|n|+|k|} makes the
+// convolution take multipoles in cell units (displacements / w) and give
+// Taylors in cell units, T'^n = T^n w^{|n|}, so the per-particle kernels
+// work on the stored cell-centred offsets directly.  One thread.
+__global__ void k_far_pairs(int p, double w, int* __restrict__ seg, FarPair* __restrict__ pairs)
 {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    double fac[kMaxFarOrder + 1];
+    double fac[kMaxFarOrder + 1], wp[2 * kMaxFarOrder + 1];
     fac[0] = 1.0;
     for (int i = 1; i <= p; ++i) fac[i] = fac[i - 1] * i;
+    wp[0] = 1.0;
+    for (int i = 1; i <= p; ++i) wp[i] = wp[i - 1] * w;
     int e = 0, n = 0;
     for (int na = 0; na <= p; ++na)
         for (int nb = 0; nb <= p - na; ++nb)
@@ -286,7 +291,7 @@ __global__ void k_far_pairs(int p, int* __restrict__ seg, FarPair* __restrict__ 
                             pr.j = encode_term(na + ka, nb + kb, nc + kc, p);
                             // odd total order: the transform of D^j is imaginary (sign bit of j)
                             if ((na + nb + nc + ka + kb + kc) & 1) pr.j |= (int)0x80000000u;
-                            pr.coef = (((ka + kb + kc) & 1) ? -1.0 : 1.0) /
+                            pr.coef = (((ka + kb + kc) & 1) ? -1.0 : 1.0) * wp[na + nb + nc + ka + kb + kc] /
                                       (fac[na] * fac[nb] * fac[nc] * fac[ka] * fac[kb] * fac[kc]);
                             pairs[e++] = pr;
                         }
@@ -395,6 +400,204 @@ __global__ void __launch_bounds__(128) k_taylor_forces(const int* __restrict__ o
             acc_add[3 * (size_t)orig + 1] += (float)ay;
             acc_add[3 * (size_t)orig + 2] += (float)az;
         }
+    }
+}
+
+// ---- double-float arithmetic ------------------------------------------------
+// GB300 runs FP64 at 1/64 of the FP32 rate.  The per-particle far-field
+// kernels therefore also exist in double-float form: a value is an unevaluated
+// sum hi + lo of two FP32 numbers, kept exact by the error-free
+// transformations TwoSum (Knuth), FastTwoSum (Dekker) and TwoProduct by FMA
+// (Ogita, Rump & Oishi 2005), which carry about 48 significant bits on the
+// FP32 pipe.  The _rn intrinsics keep the compiler from fusing a product into
+// a following sum, which would break the exactness of the transformations.
+struct dfl {
+    float h, l;
+};
+
+__device__ __forceinline__ dfl df_fast(float a, float b)  // |a| >= |b| or a == 0
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ dfl df_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+// a * z + t for a float z
+__device__ __forceinline__ dfl df_fma_f(dfl a, float z, dfl t)
+{
+    const float p = __fmul_rn(a.h, z);
+    float e = __fmaf_rn(a.h, z, -p);
+    e = __fmaf_rn(a.l, z, e);
+    const dfl s = df_two_sum(p, t.h);
+    return df_fast(s.h, __fadd_rn(s.l, __fadd_rn(e, t.l)));
+}
+
+// a * b + t
+__device__ __forceinline__ dfl df_fma(dfl a, dfl b, dfl t)
+{
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    const dfl s = df_two_sum(p, t.h);
+    return df_fast(s.h, __fadd_rn(s.l, __fadd_rn(e, t.l)));
+}
+
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b)
+{
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return df_fast(p, e);
+}
+
+__device__ __forceinline__ dfl df_from(double v)
+{
+    const float h = __double2float_rn(v);
+    return {h, __double2float_rn(v - (double)h)};
+}
+
+// Cell multipoles in cell units, double-float: the structure of k_multipoles
+// (one block per cell, one thread per term, 64 particles at a time with
+// their powers and x^a y^b products in shared memory), each term accumulated
+// as a double-float; the result is written as FP64.
+__global__ void k_multipoles_df(const int* __restrict__ off, const float4* __restrict__ rel, int C, int p,
+                                int nterms, double* __restrict__ M)
+{
+    constexpr int kChunk = 64;
+    extern __shared__ dfl pwd[];  // powers [3][kChunk][p + 1], then products [kChunk][nab]
+    const int P1 = p + 1;
+    const int nab = (p + 1) * (p + 2) / 2;
+    dfl* XY = pwd + (size_t)3 * kChunk * P1;
+    int a = 0, b = 0, c = 0;
+    const int t = threadIdx.x;
+    if (t < nterms) decode_term(t, p, a, b, c);
+    const int ab = a * (p + 1) - a * (a - 1) / 2 + b;
+    for (int cell = blockIdx.x; cell < C; cell += gridDim.x) {
+        const int s0 = off[cell], s1 = off[cell + 1];
+        dfl acc = {0.0f, 0.0f};
+        for (int q0 = s0; q0 < s1; q0 += kChunk) {
+            const int nq = min(kChunk, s1 - q0);
+            __syncthreads();
+            for (int i = threadIdx.x; i < 3 * nq; i += blockDim.x) {
+                const int q = i / 3, d = i - 3 * q;
+                const float4 r4 = rel[q0 + q];
+                const float x = d == 0 ? r4.x : (d == 1 ? r4.y : r4.z);
+                dfl* row = pwd + ((size_t)d * kChunk + q) * P1;
+                dfl v = {1.0f, 0.0f};
+                row[0] = v;
+                for (int e = 1; e <= p; ++e) {
+                    v = df_fma_f(v, x, dfl{0.0f, 0.0f});
+                    row[e] = v;
+                }
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < nq * nab; i += blockDim.x) {
+                const int q = i / nab, k = i - q * nab;
+                int aa = 0, kk = k;
+                while (kk > p - aa) {
+                    kk -= p - aa + 1;
+                    ++aa;
+                }
+                XY[(size_t)q * nab + k] = df_mul(pwd[(size_t)q * P1 + aa], pwd[((size_t)kChunk + q) * P1 + kk]);
+            }
+            __syncthreads();
+            if (t < nterms) {
+                const dfl* Z = pwd + (size_t)2 * kChunk * P1;
+                for (int q = 0; q < nq; ++q) acc = df_fma(XY[(size_t)q * nab + ab], Z[q * P1 + c], acc);
+            }
+        }
+        if (t < nterms) M[(size_t)cell * nterms + t] = (double)acc.h + (double)acc.l;
+    }
+}
+
+// FP64 Taylors [C][nt] -> double-float pairs, same layout.
+__global__ void k_taylors_to_df(const double* __restrict__ T, long long total, dfl* __restrict__ Td)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x)
+        Td[e] = df_from(T[e]);
+}
+
+// The Taylor evaluation of k_taylor_forces in double-float: cell units, the
+// particle's stored FP32 offsets as the float multipliers of the Horner steps.
+template <int P>
+__global__ void __launch_bounds__(128) k_taylor_forces_df(const int* __restrict__ off, const float4* __restrict__ rel,
+                                                         const dfl* __restrict__ T, int N, int C, double scale,
+                                                         double* __restrict__ acc_far, float* __restrict__ acc_add)
+{
+    constexpr int NT = (P + 3) * (P + 2) * (P + 1) / 6;
+    const dfl zero = {0.0f, 0.0f};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        int lo = 0, hi = C;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(off + mid) <= i)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        const dfl* __restrict__ Tc = T + (size_t)lo * NT;
+        const float4 r4 = rel[i];
+        const float x = r4.x, y = r4.y, z = r4.z;
+        dfl F = zero, Fx = zero, Fy = zero, Fz = zero;
+#pragma unroll 1
+        for (int a = P; a >= 0; --a) {
+            const int base_a = NT - (P - a + 3) * (P - a + 2) * (P - a + 1) / 6;
+            dfl U = zero, Uy = zero, Uz = zero;
+#pragma unroll 1
+            for (int b = P - a; b >= 0; --b) {
+                const int base = base_a + b * (P - a + 1) - b * (b - 1) / 2;
+                dfl S = zero, Sz = zero;
+                for (int c = P - a - b; c >= 0; --c) {
+                    const float2 tc = __ldg(reinterpret_cast<const float2*>(Tc + base + c));
+                    Sz = df_fma_f(Sz, z, S);
+                    S = df_fma_f(S, z, dfl{tc.x, tc.y});
+                }
+                Uy = df_fma_f(Uy, y, U);
+                U = df_fma_f(U, y, S);
+                Uz = df_fma_f(Uz, y, Sz);
+            }
+            Fx = df_fma_f(Fx, x, F);
+            F = df_fma_f(F, x, U);
+            Fy = df_fma_f(Fy, x, Uy);
+            Fz = df_fma_f(Fz, x, Uz);
+        }
+        const int orig = __float_as_int(r4.w);
+        const double ax = scale * ((double)Fx.h + (double)Fx.l);
+        const double ay = scale * ((double)Fy.h + (double)Fy.l);
+        const double az = scale * ((double)Fz.h + (double)Fz.l);
+        if (acc_far) {
+            acc_far[3 * (size_t)orig] = ax;
+            acc_far[3 * (size_t)orig + 1] = ay;
+            acc_far[3 * (size_t)orig + 2] = az;
+        }
+        if (acc_add) {
+            acc_add[3 * (size_t)orig] += (float)ax;
+            acc_add[3 * (size_t)orig + 1] += (float)ay;
+            acc_add[3 * (size_t)orig + 2] += (float)az;
+        }
+    }
+}
+
+// Taylors in box units from cell units: T^n = T'^n / w^{|n|}, [C][nt].
+__global__ void k_unscale_taylors(const double* __restrict__ Tc, long long total, int nt, int p, double inv_w,
+                                  double* __restrict__ T)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        int a, b, c;
+        decode_term((int)(e % nt), p, a, b, c);
+        double f = 1.0;
+        for (int i = 0; i < a + b + c; ++i) f *= inv_w;
+        T[e] = Tc[e] * f;
     }
 }
 
@@ -558,6 +761,70 @@ cudaError_t launch_deriv_recip(int K, int p, double box, double alpha, int hmax,
     return cudaGetLastError();
 }
 
+cudaError_t launch_multipoles_df(const int* off, const float4* rel, int C, int p, double* M, cudaStream_t s)
+{
+    const int nterms = far_terms(p);
+    const int threads = ((nterms + 31) / 32) * 32;
+    const size_t smem = ((size_t)3 * 64 * (p + 1) + (size_t)64 * (p + 1) * (p + 2) / 2) * sizeof(dfl);
+    cudaError_t e = ensure_smem((const void*)k_multipoles_df, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = C < device_sms() * 32 ? C : device_sms() * 32;
+    k_multipoles_df<<<grid, threads, smem, s>>>(off, rel, C, p, nterms, M);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_taylor_forces_df(int p, const int* off, const float4* rel, const double* T, void* Tdf, int N,
+                                    int C, double scale, double* acc_far, float* acc_add, cudaStream_t s)
+{
+    const long long total = (long long)C * far_terms(p);
+    long long blocks = (total + 255) / 256;
+    const long long cap = (long long)device_sms() * 16;
+    if (blocks > cap) blocks = cap;
+    dfl* Td = static_cast<dfl*>(Tdf);
+    k_taylors_to_df<<<(int)blocks, 256, 0, s>>>(T, total, Td);
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int need = (N + 127) / 128;
+    const int grid = need < device_sms() * 16 ? need : device_sms() * 16;
+    switch (p) {
+#define NF_TAYLOR_DF_CASE(P)                                                                        \
+    case P:                                                                                         \
+        k_taylor_forces_df<P><<<grid, 128, 0, s>>>(off, rel, Td, N, C, scale, acc_far, acc_add);    \
+        break;
+        NF_TAYLOR_DF_CASE(0)
+        NF_TAYLOR_DF_CASE(1)
+        NF_TAYLOR_DF_CASE(2)
+        NF_TAYLOR_DF_CASE(3)
+        NF_TAYLOR_DF_CASE(4)
+        NF_TAYLOR_DF_CASE(5)
+        NF_TAYLOR_DF_CASE(6)
+        NF_TAYLOR_DF_CASE(7)
+        NF_TAYLOR_DF_CASE(8)
+        NF_TAYLOR_DF_CASE(9)
+        NF_TAYLOR_DF_CASE(10)
+        NF_TAYLOR_DF_CASE(11)
+        NF_TAYLOR_DF_CASE(12)
+#undef NF_TAYLOR_DF_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unscale_taylors(const double* Tc, int C, int p, double w, double* T, cudaStream_t s)
+{
+    const int nt = far_terms(p);
+    const long long total = (long long)C * nt;
+    long long blocks = (total + 255) / 256;
+    const long long cap = (long long)device_sms() * 16;
+    if (blocks > cap) blocks = cap;
+    k_unscale_taylors<<<(int)blocks, 256, 0, s>>>(Tc, total, nt, p, 1.0 / w, T);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_deriv_header(const DerivHeader& h, void* dst, cudaStream_t s)
 {
     k_deriv_header<<<1, 32, 0, s>>>(h, static_cast<DerivHeader*>(dst));
@@ -565,9 +832,9 @@ cudaError_t launch_deriv_header(const DerivHeader& h, void* dst, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_far_pairs(int p, int* seg, FarPair* pairs, cudaStream_t s)
+cudaError_t launch_far_pairs(int p, double w, int* seg, FarPair* pairs, cudaStream_t s)
 {
-    k_far_pairs<<<1, 32, 0, s>>>(p, seg, pairs);
+    k_far_pairs<<<1, 32, 0, s>>>(p, w, seg, pairs);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -118,7 +118,12 @@ void far_release_plans();    // destroys every cached cuFFT plan
 cudaError_t launch_deriv_real(int K, int R, int p, double box, double alpha, int nimg, double* D, cudaStream_t s);
 cudaError_t launch_deriv_recip(int K, int p, double box, double alpha, int hmax, const double2* Dh, double* Dr,
                                cudaStream_t s);
-cudaError_t launch_far_pairs(int p, int* seg, FarPair* pairs, cudaStream_t s);
+cudaError_t launch_far_pairs(int p, double w, int* seg, FarPair* pairs, cudaStream_t s);
+cudaError_t launch_unscale_taylors(const double* Tc, int C, int p, double w, double* T, cudaStream_t s);
+// double-float forms of the per-particle kernels (cell units); Tdf holds C * nt pairs of floats
+cudaError_t launch_multipoles_df(const int* off, const float4* rel, int C, int p, double* M, cudaStream_t s);
+cudaError_t launch_taylor_forces_df(int p, const int* off, const float4* rel, const double* T, void* Tdf, int N,
+                                    int C, double scale, double* acc_far, float* acc_add, cudaStream_t s);
 cudaError_t launch_far_contract(int K, int p, const int* seg, const FarPair* pairs, const double* Dr,
                                 const double2* Mh, double2* Th, cudaStream_t s);
 cudaError_t launch_taylor_forces(int p, const int* off, const float4* rel, const double* T, int N, int C, double w,

@@ -151,3 +151,12 @@ def test_far_field_sizes_and_host_checks():
                              None) == _lib.NF_ERR_ARG
     assert lib.nf_far_forces(FAKE, 1000, 1.0, 8, 2, 4, FAKE_WS, big, None, None, None, FAKE_WS, 4096,
                              None) == _lib.NF_ERR_WORKSPACE
+
+
+def test_far_arith_switch_on_host():
+    lib = _lib.load()
+    before = lib.nf_far_get_arith()
+    assert before in (_lib.NF_FAR_FP64, _lib.NF_FAR_DOUBLE_FLOAT)
+    assert lib.nf_far_set_arith(5) == _lib.NF_ERR_ARG
+    assert lib.nf_far_set_arith(_lib.NF_FAR_FP64) == _lib.NF_OK and lib.nf_far_get_arith() == _lib.NF_FAR_FP64
+    assert lib.nf_far_set_arith(before) == _lib.NF_OK

@@ -10,6 +10,16 @@ from _helpers import to_dev
 pytestmark = pytest.mark.gpu
 
 
+@pytest.fixture(params=[0, 1], ids=["fp64", "double-float"])
+def arith(request):
+    """Runs a test with each arithmetic of the per-particle far-field kernels."""
+    from paper_2110_11392_gb300 import _lib
+    before = _lib.nf_far_get_arith()
+    _lib.nf_far_set_arith(request.param)
+    yield request.param
+    _lib.nf_far_set_arith(before)
+
+
 def _uniform(N, seed):
     pos = np.random.default_rng(seed).random((N, 3)).astype(np.float32)
     pos[pos >= 1.0] = 0.0
@@ -52,7 +62,7 @@ def test_derivatives_match_oracle(K, R, p, box):
 @pytest.mark.parametrize("K,R,p,N,kind", [(5, 2, 4, 3000, "uniform"), (8, 2, 8, 20000, "clustered"),
                                           (11, 2, 8, 65536, "uniform"), (7, 3, 5, 9000, "clustered"),
                                           (16, 2, 8, 40000, "clustered"), (6, 2, 1, 500, "uniform")])
-def test_far_forces_match_oracle(K, R, p, N, kind):
+def test_far_forces_match_oracle(K, R, p, N, kind, arith):
     import torch
     import paper_2110_11392_gb300 as nf
     pos = _uniform(N, 21) if kind == "uniform" else _clustered(N, K, 22)
@@ -158,7 +168,7 @@ def test_argument_errors():
 
 
 @pytest.mark.parametrize("K,p", [(6, 12), (5, 10)])
-def test_highest_orders_match_oracle(K, p):
+def test_highest_orders_match_oracle(K, p, arith):
     import torch
     import paper_2110_11392_gb300 as nf
     pos = _uniform(2000, 31)
@@ -168,7 +178,7 @@ def test_highest_orders_match_oracle(K, p):
     assert np.abs(a.cpu().numpy() - aref).max() < 1e-10 * np.abs(aref).max()
 
 
-def test_sparse_cells_faces_and_wrapping():
+def test_sparse_cells_faces_and_wrapping(arith):
     # far fewer particles than cells (most cells empty), particles on cell
     # faces, and coordinates outside [0, box) that must wrap like nf_forces
     import torch
@@ -214,3 +224,26 @@ def test_total_force_call_equals_near_plus_far():
     tot = ff.total(pos, eps)
     torch.cuda.synchronize()
     assert torch.equal(tot, ref)
+
+
+def test_the_two_arithmetics_agree():
+    import torch
+    import paper_2110_11392_gb300 as nf
+    from paper_2110_11392_gb300 import _lib
+    pos = to_dev(_clustered(60000, 12, 13))
+    ff = nf.FarField(12, 2, 8)
+    before = _lib.nf_far_get_arith()
+    try:
+        _lib.nf_far_set_arith(_lib.NF_FAR_FP64)
+        a64, t64 = ff(pos, want_taylors=True)
+        _lib.nf_far_set_arith(_lib.NF_FAR_DOUBLE_FLOAT)
+        adf, tdf = ff(pos, want_taylors=True)
+        torch.cuda.synchronize()
+    finally:
+        _lib.nf_far_set_arith(before)
+    scale = a64.abs().max().item()
+    assert (a64 - adf).abs().max().item() < 1e-12 * scale
+    tscale = t64.abs().amax(dim=0) + 1e-300
+    assert ((t64 - tdf).abs().amax(dim=0) / tscale).max().item() < 1e-12
+    with pytest.raises(_lib.NFError):
+        _lib.nf_far_set_arith(2)
