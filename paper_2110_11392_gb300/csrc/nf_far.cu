@@ -482,7 +482,9 @@ __global__ void k_multipoles_df(const int* __restrict__ off, const float4* __res
     const int ab = a * (p + 1) - a * (a - 1) / 2 + b;
     for (int cell = blockIdx.x; cell < C; cell += gridDim.x) {
         const int s0 = off[cell], s1 = off[cell + 1];
-        dfl acc = {0.0f, 0.0f};
+        // four independent partial sums: each double-float update is a chain of
+        // dependent FP32 operations, so one accumulator would wait on latency
+        dfl acc[4] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
         for (int q0 = s0; q0 < s1; q0 += kChunk) {
             const int nq = min(kChunk, s1 - q0);
             __syncthreads();
@@ -511,10 +513,22 @@ __global__ void k_multipoles_df(const int* __restrict__ off, const float4* __res
             __syncthreads();
             if (t < nterms) {
                 const dfl* Z = pwd + (size_t)2 * kChunk * P1;
-                for (int q = 0; q < nq; ++q) acc = df_fma(XY[(size_t)q * nab + ab], Z[q * P1 + c], acc);
+                int q = 0;
+                for (; q + 4 <= nq; q += 4) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        acc[u] = df_fma(XY[(size_t)(q + u) * nab + ab], Z[(q + u) * P1 + c], acc[u]);
+                }
+                for (; q < nq; ++q) acc[0] = df_fma(XY[(size_t)q * nab + ab], Z[q * P1 + c], acc[0]);
             }
         }
-        if (t < nterms) M[(size_t)cell * nterms + t] = (double)acc.h + (double)acc.l;
+        if (t < nterms) {
+            // combine the partial sums in FP64 (exact for four double-floats to ~2^-48)
+            double m = 0.0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) m += (double)acc[u].h + (double)acc[u].l;
+            M[(size_t)cell * nterms + t] = m;
+        }
     }
 }
 
@@ -528,6 +542,37 @@ __global__ void k_taylors_to_df(const double* __restrict__ T, long long total, d
 
 // The Taylor evaluation of k_taylor_forces in double-float: cell units, the
 // particle's stored FP32 offsets as the float multipliers of the Horner steps.
+// Each thread evaluates two particles at once (binned slots i and i + half):
+// a double-float Horner step is a chain of dependent FP32 operations, and two
+// independent chains keep the FP32 pipe busy.
+__device__ __forceinline__ int cell_of_slot(const int* __restrict__ off, int C, int i)
+{
+    int lo = 0, hi = C;  // off[lo] <= i < off[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(off + mid) <= i)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void store_far(int orig, double ax, double ay, double az, double* __restrict__ acc_far,
+                                          float* __restrict__ acc_add)
+{
+    if (acc_far) {
+        acc_far[3 * (size_t)orig] = ax;
+        acc_far[3 * (size_t)orig + 1] = ay;
+        acc_far[3 * (size_t)orig + 2] = az;
+    }
+    if (acc_add) {
+        acc_add[3 * (size_t)orig] += (float)ax;
+        acc_add[3 * (size_t)orig + 1] += (float)ay;
+        acc_add[3 * (size_t)orig + 2] += (float)az;
+    }
+}
+
 template <int P>
 __global__ void __launch_bounds__(128) k_taylor_forces_df(const int* __restrict__ off, const float4* __restrict__ rel,
                                                          const dfl* __restrict__ T, int N, int C, double scale,
@@ -535,55 +580,55 @@ __global__ void __launch_bounds__(128) k_taylor_forces_df(const int* __restrict_
 {
     constexpr int NT = (P + 3) * (P + 2) * (P + 1) / 6;
     const dfl zero = {0.0f, 0.0f};
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-        int lo = 0, hi = C;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (__ldg(off + mid) <= i)
-                lo = mid;
-            else
-                hi = mid;
-        }
-        const dfl* __restrict__ Tc = T + (size_t)lo * NT;
-        const float4 r4 = rel[i];
-        const float x = r4.x, y = r4.y, z = r4.z;
-        dfl F = zero, Fx = zero, Fy = zero, Fz = zero;
+    const int half = (N + 1) / 2;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < half; i += gridDim.x * blockDim.x) {
+        const int j = i + half;                 // the second particle (may be past the end)
+        const bool two = j < N;
+        const int jj = two ? j : i;             // evaluate something valid, store only if two
+        const dfl* __restrict__ T0 = T + (size_t)cell_of_slot(off, C, i) * NT;
+        const dfl* __restrict__ T1 = T + (size_t)cell_of_slot(off, C, jj) * NT;
+        const float4 r0 = rel[i], r1 = rel[jj];
+        dfl F0 = zero, Fx0 = zero, Fy0 = zero, Fz0 = zero;
+        dfl F1 = zero, Fx1 = zero, Fy1 = zero, Fz1 = zero;
 #pragma unroll 1
         for (int a = P; a >= 0; --a) {
             const int base_a = NT - (P - a + 3) * (P - a + 2) * (P - a + 1) / 6;
-            dfl U = zero, Uy = zero, Uz = zero;
+            dfl U0 = zero, Uy0 = zero, Uz0 = zero, U1 = zero, Uy1 = zero, Uz1 = zero;
 #pragma unroll 1
             for (int b = P - a; b >= 0; --b) {
                 const int base = base_a + b * (P - a + 1) - b * (b - 1) / 2;
-                dfl S = zero, Sz = zero;
+                dfl S0 = zero, Sz0 = zero, S1 = zero, Sz1 = zero;
                 for (int c = P - a - b; c >= 0; --c) {
-                    const float2 tc = __ldg(reinterpret_cast<const float2*>(Tc + base + c));
-                    Sz = df_fma_f(Sz, z, S);
-                    S = df_fma_f(S, z, dfl{tc.x, tc.y});
+                    const float2 t0 = __ldg(reinterpret_cast<const float2*>(T0 + base + c));
+                    const float2 t1 = __ldg(reinterpret_cast<const float2*>(T1 + base + c));
+                    Sz0 = df_fma_f(Sz0, r0.z, S0);
+                    Sz1 = df_fma_f(Sz1, r1.z, S1);
+                    S0 = df_fma_f(S0, r0.z, dfl{t0.x, t0.y});
+                    S1 = df_fma_f(S1, r1.z, dfl{t1.x, t1.y});
                 }
-                Uy = df_fma_f(Uy, y, U);
-                U = df_fma_f(U, y, S);
-                Uz = df_fma_f(Uz, y, Sz);
+                Uy0 = df_fma_f(Uy0, r0.y, U0);
+                Uy1 = df_fma_f(Uy1, r1.y, U1);
+                U0 = df_fma_f(U0, r0.y, S0);
+                U1 = df_fma_f(U1, r1.y, S1);
+                Uz0 = df_fma_f(Uz0, r0.y, Sz0);
+                Uz1 = df_fma_f(Uz1, r1.y, Sz1);
             }
-            Fx = df_fma_f(Fx, x, F);
-            F = df_fma_f(F, x, U);
-            Fy = df_fma_f(Fy, x, Uy);
-            Fz = df_fma_f(Fz, x, Uz);
+            Fx0 = df_fma_f(Fx0, r0.x, F0);
+            Fx1 = df_fma_f(Fx1, r1.x, F1);
+            F0 = df_fma_f(F0, r0.x, U0);
+            F1 = df_fma_f(F1, r1.x, U1);
+            Fy0 = df_fma_f(Fy0, r0.x, Uy0);
+            Fy1 = df_fma_f(Fy1, r1.x, Uy1);
+            Fz0 = df_fma_f(Fz0, r0.x, Uz0);
+            Fz1 = df_fma_f(Fz1, r1.x, Uz1);
         }
-        const int orig = __float_as_int(r4.w);
-        const double ax = scale * ((double)Fx.h + (double)Fx.l);
-        const double ay = scale * ((double)Fy.h + (double)Fy.l);
-        const double az = scale * ((double)Fz.h + (double)Fz.l);
-        if (acc_far) {
-            acc_far[3 * (size_t)orig] = ax;
-            acc_far[3 * (size_t)orig + 1] = ay;
-            acc_far[3 * (size_t)orig + 2] = az;
-        }
-        if (acc_add) {
-            acc_add[3 * (size_t)orig] += (float)ax;
-            acc_add[3 * (size_t)orig + 1] += (float)ay;
-            acc_add[3 * (size_t)orig + 2] += (float)az;
-        }
+        store_far(__float_as_int(r0.w), scale * ((double)Fx0.h + (double)Fx0.l),
+                  scale * ((double)Fy0.h + (double)Fy0.l), scale * ((double)Fz0.h + (double)Fz0.l), acc_far,
+                  acc_add);
+        if (two)
+            store_far(__float_as_int(r1.w), scale * ((double)Fx1.h + (double)Fx1.l),
+                      scale * ((double)Fy1.h + (double)Fy1.l), scale * ((double)Fz1.h + (double)Fz1.l), acc_far,
+                      acc_add);
     }
 }
 
@@ -786,7 +831,7 @@ cudaError_t launch_taylor_forces_df(int p, const int* off, const float4* rel, co
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int need = (N + 127) / 128;
+    const int need = ((N + 1) / 2 + 127) / 128;
     const int grid = need < device_sms() * 16 ? need : device_sms() * 16;
     switch (p) {
 #define NF_TAYLOR_DF_CASE(P)                                                                        \
