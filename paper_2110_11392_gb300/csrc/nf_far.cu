@@ -458,6 +458,12 @@ __device__ __forceinline__ dfl df_mul(dfl a, dfl b)
     return df_fast(p, e);
 }
 
+__device__ __forceinline__ dfl df_add(dfl a, dfl b)
+{
+    const dfl s = df_two_sum(a.h, b.h);
+    return df_fast(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+
 __device__ __forceinline__ dfl df_from(double v)
 {
     const float h = __double2float_rn(v);
@@ -472,10 +478,19 @@ __global__ void k_multipoles_df(const int* __restrict__ off, const float4* __res
                                 int nterms, double* __restrict__ M)
 {
     constexpr int kChunk = 64;
-    extern __shared__ dfl pwd[];  // powers [3][kChunk][p + 1], then products [kChunk][nab]
+    extern __shared__ dfl pwd[];  // powers [3][kChunk][p + 1], products [kChunk][nab], (a, b) table [nab]
     const int P1 = p + 1;
     const int nab = (p + 1) * (p + 2) / 2;
     dfl* XY = pwd + (size_t)3 * kChunk * P1;
+    int2* abt = reinterpret_cast<int2*>(XY + (size_t)kChunk * nab);
+    for (int k = threadIdx.x; k < nab; k += blockDim.x) {
+        int aa = 0, kk = k;
+        while (kk > p - aa) {
+            kk -= p - aa + 1;
+            ++aa;
+        }
+        abt[k] = make_int2(aa, kk);
+    }
     int a = 0, b = 0, c = 0;
     const int t = threadIdx.x;
     if (t < nterms) decode_term(t, p, a, b, c);
@@ -503,12 +518,8 @@ __global__ void k_multipoles_df(const int* __restrict__ off, const float4* __res
             __syncthreads();
             for (int i = threadIdx.x; i < nq * nab; i += blockDim.x) {
                 const int q = i / nab, k = i - q * nab;
-                int aa = 0, kk = k;
-                while (kk > p - aa) {
-                    kk -= p - aa + 1;
-                    ++aa;
-                }
-                XY[(size_t)q * nab + k] = df_mul(pwd[(size_t)q * P1 + aa], pwd[((size_t)kChunk + q) * P1 + kk]);
+                const int2 ab2 = abt[k];
+                XY[(size_t)q * nab + k] = df_mul(pwd[(size_t)q * P1 + ab2.x], pwd[((size_t)kChunk + q) * P1 + ab2.y]);
             }
             __syncthreads();
             if (t < nterms) {
@@ -523,11 +534,10 @@ __global__ void k_multipoles_df(const int* __restrict__ off, const float4* __res
             }
         }
         if (t < nterms) {
-            // combine the partial sums in FP64 (exact for four double-floats to ~2^-48)
-            double m = 0.0;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) m += (double)acc[u].h + (double)acc[u].l;
-            M[(size_t)cell * nterms + t] = m;
+            // combine the partial sums in double-float; one conversion to FP64 (the FP64
+            // pipe is 1/64 of the FP32 rate, so it is kept out of the per-term work)
+            const dfl m = df_add(df_add(acc[0], acc[1]), df_add(acc[2], acc[3]));
+            M[(size_t)cell * nterms + t] = (double)m.h + (double)m.l;
         }
     }
 }
@@ -810,7 +820,8 @@ cudaError_t launch_multipoles_df(const int* off, const float4* rel, int C, int p
 {
     const int nterms = far_terms(p);
     const int threads = ((nterms + 31) / 32) * 32;
-    const size_t smem = ((size_t)3 * 64 * (p + 1) + (size_t)64 * (p + 1) * (p + 2) / 2) * sizeof(dfl);
+    const size_t nab = (size_t)(p + 1) * (p + 2) / 2;
+    const size_t smem = ((size_t)3 * 64 * (p + 1) + (size_t)64 * nab) * sizeof(dfl) + nab * sizeof(int2);
     cudaError_t e = ensure_smem((const void*)k_multipoles_df, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = C < device_sms() * 32 ? C : device_sms() * 32;
