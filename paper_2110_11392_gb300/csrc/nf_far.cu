@@ -55,7 +55,6 @@ namespace nf {
 namespace {
 
 constexpr int kDerivThreads = 256;
-constexpr int kTermsPerThread = (kMaxFarTerms + kDerivThreads - 1) / kDerivThreads;
 
 __host__ __device__ inline int far_terms(int p) { return (p + 3) * (p + 2) * (p + 1) / 6; }
 
@@ -131,89 +130,120 @@ __device__ void gm_erf(int p, double alpha, double r, double* gm)
     }
 }
 
-// Block-wide Hermite recursion for one point: adds scale * R^0_{abc} to the
-// calling thread's accumulators (terms threadIdx.x + j * blockDim.x).
-// lay: 2 * (p+1)^3 doubles of shared memory; gm: p+1 values in shared memory.
-__device__ void hermite_block(int p, int nt, double X, double Y, double Z, const double* gm, double scale,
-                              double* lay, double* acc)
+// Hermite recursion of one warp for one point: adds scale * R^0_{abc} of the
+// point to the warp's accumulators acc[nt] (shared memory).  The layers are
+// compact: the entry of (t, u, v) is its term index in the order-p basis
+// (enc maps (t, u, v) to it, dec back), so two layers take 2 nt doubles;
+// gm holds the p + 1 values g_m at the point.
+__device__ void hermite_warp(int p, int nt, double X, double Y, double Z, const double* gm, double scale,
+                             double* lay0, double* lay1, const short* enc, const char4* dec, double* acc)
 {
-    const int P1 = p + 1, cube = P1 * P1 * P1;
-    double* nxt = lay;
-    double* cur = lay + cube;
-    if (threadIdx.x == 0) nxt[0] = gm[p];
-    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int P1 = p + 1;
+    double* nxt = lay0;
+    double* cur = lay1;
+    if (lane == 0) nxt[0] = gm[p];  // layer p holds only (0, 0, 0), term 0
+    __syncwarp();
     for (int m = p - 1; m >= 0; --m) {
         const int top = p - m;
-        for (int e = threadIdx.x; e < cube; e += blockDim.x) {
-            const int t = e / (P1 * P1), u = (e / P1) % P1, v = e % P1;
+        for (int e = lane; e < nt; e += 32) {
+            const char4 d = dec[e];
+            const int t = d.x, u = d.y, v = d.z;
             if (t + u + v > top) continue;
             double r;
             if (t + u + v == 0)
                 r = gm[m];
             else if (t > 0)
-                r = (t >= 2 ? (t - 1) * nxt[e - 2 * P1 * P1] : 0.0) + X * nxt[e - P1 * P1];
+                r = (t >= 2 ? (t - 1) * nxt[enc[((t - 2) * P1 + u) * P1 + v]] : 0.0) +
+                    X * nxt[enc[((t - 1) * P1 + u) * P1 + v]];
             else if (u > 0)
-                r = (u >= 2 ? (u - 1) * nxt[e - 2 * P1] : 0.0) + Y * nxt[e - P1];
+                r = (u >= 2 ? (u - 1) * nxt[enc[(t * P1 + u - 2) * P1 + v]] : 0.0) +
+                    Y * nxt[enc[(t * P1 + u - 1) * P1 + v]];
             else
-                r = (v >= 2 ? (v - 1) * nxt[e - 2] : 0.0) + Z * nxt[e - 1];
+                r = (v >= 2 ? (v - 1) * nxt[enc[(t * P1 + u) * P1 + v - 2]] : 0.0) +
+                    Z * nxt[enc[(t * P1 + u) * P1 + v - 1]];
             cur[e] = r;
         }
-        __syncthreads();
+        __syncwarp();
         double* sw = cur;
         cur = nxt;
         nxt = sw;
     }
-    // layer 0 is in nxt
-#pragma unroll
-    for (int j = 0; j < kTermsPerThread; ++j) {
-        const int t = threadIdx.x + j * blockDim.x;
-        if (t < nt) {
-            int a, b, c;
-            decode_term(t, p, a, b, c);
-            acc[j] += scale * nxt[(a * P1 + b) * P1 + c];
-        }
-    }
-    __syncthreads();  // lay and gm are reused by the next point
+    // layer 0 (every term) is in nxt
+    for (int e = lane; e < nt; e += 32) acc[e] += scale * nxt[e];
+    __syncwarp();
+}
+
+constexpr int kDerivWarps = kDerivThreads / 32;
+
+size_t deriv_real_smem(int p)
+{
+    const int nt = far_terms(p), P1 = p + 1;
+    const size_t doubles = (size_t)kDerivWarps * (3 * nt + P1);  // accumulators, two layers, g_m per warp
+    const size_t shorts = (size_t)((P1 * P1 * P1 + 1) & ~1);
+    return doubles * sizeof(double) + shorts * sizeof(short) + (size_t)nt * sizeof(char4);
 }
 
 // Real-space part of D, one block per cell offset g: images n in [-nimg, nimg]^3
-// (the near image left out), minus the near image's erf part.  D is cell-major
-// [C][nt], the layout of the multipoles.
+// (the near image left out), minus the near image's erf part.  Each warp
+// takes its own images (one Hermite recursion per image, layers private to the
+// warp); the warps' sums are added in a fixed order at the end.  D is
+// cell-major [C][nt], the layout of the multipoles.
 __global__ void __launch_bounds__(kDerivThreads) k_deriv_real(int K, int R, int p, int nt, double box, double alpha,
                                                               int nimg, double* __restrict__ D)
 {
     extern __shared__ double sm[];
     const int P1 = p + 1;
-    double* lay = sm;
-    double* gm = sm + 2 * P1 * P1 * P1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double* acc_all = sm;                                  // [warps][nt]
+    double* lay_all = acc_all + (size_t)kDerivWarps * nt;  // [warps][2][nt]
+    double* gm_all = lay_all + (size_t)kDerivWarps * 2 * nt;  // [warps][P1]
+    short* enc = reinterpret_cast<short*>(gm_all + (size_t)kDerivWarps * P1);
+    char4* dec = reinterpret_cast<char4*>(enc + ((P1 * P1 * P1 + 1) & ~1));
+    for (int e = threadIdx.x; e < nt; e += blockDim.x) {
+        int a, b, c;
+        decode_term(e, p, a, b, c);
+        dec[e] = make_char4((char)a, (char)b, (char)c, 0);
+        enc[(a * P1 + b) * P1 + c] = (short)e;
+    }
+    __syncthreads();  // the tables are read by every warp
+    double* acc = acc_all + (size_t)warp * nt;
+    double* lay0 = lay_all + (size_t)warp * 2 * nt;
+    double* lay1 = lay0 + nt;
+    double* gm = gm_all + (size_t)warp * P1;
     const int C = K * K * K;
     const double w = box / K;
+    const int side = 2 * nimg + 1, nimages = side * side * side;
     for (int g = blockIdx.x; g < C; g += gridDim.x) {
         const int cx = centred(g / (K * K), K), cy = centred((g / K) % K, K), cz = centred(g % K, K);
         const bool near = abs(cx) <= R && abs(cy) <= R && abs(cz) <= R;
         const double dx = cx * w, dy = cy * w, dz = cz * w;
-        double acc[kTermsPerThread];
-#pragma unroll
-        for (int j = 0; j < kTermsPerThread; ++j) acc[j] = 0.0;
-        const int side = 2 * nimg + 1;
-        for (int n = 0; n < side * side * side; ++n) {
-            const int nx = n / (side * side) - nimg, ny = (n / side) % side - nimg, nz = n % side - nimg;
-            if (near && nx == 0 && ny == 0 && nz == 0) continue;
-            const double X = dx + nx * box, Y = dy + ny * box, Z = dz + nz * box;
-            if (threadIdx.x == 0) gm_erfc(p, alpha, sqrt(X * X + Y * Y + Z * Z), gm);
-            __syncthreads();
-            hermite_block(p, nt, X, Y, Z, gm, 1.0, lay, acc);
+        for (int e = lane; e < nt; e += 32) acc[e] = 0.0;
+        __syncwarp();
+        // images 0 .. nimages-1, and for a near offset one more item: its erf part
+        for (int n = warp; n < nimages + (near ? 1 : 0); n += kDerivWarps) {
+            double X = dx, Y = dy, Z = dz, scale = -1.0;
+            if (n < nimages) {
+                const int nx = n / (side * side) - nimg, ny = (n / side) % side - nimg, nz = n % side - nimg;
+                if (near && nx == 0 && ny == 0 && nz == 0) continue;
+                X = dx + nx * box;
+                Y = dy + ny * box;
+                Z = dz + nz * box;
+                scale = 1.0;
+                if (lane == 0) gm_erfc(p, alpha, sqrt(X * X + Y * Y + Z * Z), gm);
+            } else if (lane == 0) {
+                gm_erf(p, alpha, sqrt(dx * dx + dy * dy + dz * dz), gm);
+            }
+            __syncwarp();
+            hermite_warp(p, nt, X, Y, Z, gm, scale, lay0, lay1, enc, dec, acc);
         }
-        if (near) {
-            if (threadIdx.x == 0) gm_erf(p, alpha, sqrt(dx * dx + dy * dy + dz * dz), gm);
-            __syncthreads();
-            hermite_block(p, nt, dx, dy, dz, gm, -1.0, lay, acc);
+        __syncthreads();
+        for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+            double sum = 0.0;
+            for (int q = 0; q < kDerivWarps; ++q) sum += acc_all[(size_t)q * nt + t];
+            D[(size_t)g * nt + t] = sum;
         }
-#pragma unroll
-        for (int j = 0; j < kTermsPerThread; ++j) {
-            const int t = threadIdx.x + j * blockDim.x;
-            if (t < nt) D[(size_t)g * nt + t] = acc[j];
-        }
+        __syncthreads();
     }
 }
 
@@ -793,7 +823,7 @@ void far_release_plans()
 cudaError_t launch_deriv_real(int K, int R, int p, double box, double alpha, int nimg, double* D, cudaStream_t s)
 {
     const int nt = far_terms(p);
-    const size_t smem = (size_t)(2 * (p + 1) * (p + 1) * (p + 1) + (p + 1)) * sizeof(double);
+    const size_t smem = deriv_real_smem(p);
     cudaError_t e = ensure_smem((const void*)k_deriv_real, (int)smem);
     if (e != cudaSuccess) return e;
     const int C = K * K * K;
