@@ -43,7 +43,7 @@ def _dr_gpu(ff):
 
 
 @pytest.mark.parametrize("K,R,p,box", [(5, 2, 4, 1.0), (8, 2, 8, 1.0), (11, 2, 8, 1.0), (9, 3, 6, 3.0),
-                                       (6, 2, 12, 1.0)])
+                                       (6, 2, 12, 1.0), (4, 1, 6, 1.0)])
 def test_derivatives_match_oracle(K, R, p, box):
     import paper_2110_11392_gb300 as nf
     ff = nf.FarField(K, R, p, box)
@@ -61,7 +61,8 @@ def test_derivatives_match_oracle(K, R, p, box):
 
 @pytest.mark.parametrize("K,R,p,N,kind", [(5, 2, 4, 3000, "uniform"), (8, 2, 8, 20000, "clustered"),
                                           (11, 2, 8, 65536, "uniform"), (7, 3, 5, 9000, "clustered"),
-                                          (16, 2, 8, 40000, "clustered"), (6, 2, 1, 500, "uniform")])
+                                          (16, 2, 8, 40000, "clustered"), (6, 2, 1, 500, "uniform"),
+                                          (6, 1, 7, 8000, "clustered")])
 def test_far_forces_match_oracle(K, R, p, N, kind, arith):
     import torch
     import paper_2110_11392_gb300 as nf
