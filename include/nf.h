@@ -340,7 +340,7 @@ int nf_forces_total(const float *pos, int64_t N, double box, int K, int R, doubl
  * 1/64 of its FP32 rate.  NF_FAR_DOUBLE_FLOAT (the default) keeps each value
  * as an unevaluated sum of two FP32 numbers, held exact by error-free
  * transformations, on the FP32 pipe: about 48 significant bits.  Both modes
- * give the same far field to ~1e-13 relative.  The FFTs, the k-space
+ * give the same far field to 1e-12 of its largest value (tested).  The FFTs, the k-space
  * product and the derivatives are FP64 in both.  nf_far_set_arith returns
  * NF_ERR_ARG for another mode; calls already enqueued keep the mode they
  * were enqueued with. */
