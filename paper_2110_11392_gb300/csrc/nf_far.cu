@@ -34,12 +34,17 @@
 // theorem each term is a product in k-space (k_far_contract) between the
 // forward transforms of D and of the multipoles; the inverse transform gives
 // T in every cell.  The FFTs are cuFFT's (a plain library transform); every
-// other step is a kernel of this file.
+// other step is a kernel of this file.  The per-particle work runs in cell
+// units (multipoles of the stored offsets x / w, Taylors T'^n = T^n w^{|n|});
+// the factors w^{|n|+|k|} live in the convolution's coefficients.
 //
 // Acceleration.  The potential in a cell is -m sum_n T^n x^n (G = 1), so
-// a = m sum_n T^n grad(x^n), x the displacement from the cell centre (the
-// particle's FP32 cell-centred offset times w), evaluated by nested Horner
-// schemes in z, y and x (k_taylor_forces).  All far-field arithmetic is FP64.
+// a = m sum_n T^n grad(x^n) = (m / w) sum_n T'^n grad'(x'^n), x' the
+// particle's FP32 cell-centred offset, evaluated by nested Horner schemes in
+// z, y and x (k_taylor_forces).  The derivatives, FFTs and k-space product
+// are FP64; the per-particle kernels are FP64 (k_multipoles in
+// nf_multipole.cu, k_taylor_forces) or double-float on the FP32 pipe
+// (k_multipoles_df, k_taylor_forces_df), as the caller selects.
 #include <cuda_runtime.h>
 #include <cufft.h>
 
