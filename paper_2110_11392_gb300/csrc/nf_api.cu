@@ -308,12 +308,12 @@ int finish_call(void* ws, cudaStream_t s)
     return NF_OK;
 }
 
-int run_binning(const Plan& p, const float* pos, void* ws, int32_t* cell_off, float4* rel, int32_t* perm,
-                cudaStream_t s)
+// Clears the status header of a workspace and, in debug mode, fills its guard
+// blocks and records them in the header (every call that later runs
+// finish_call on the workspace starts with this).
+int init_ws(const Plan& p, void* ws, cudaStream_t s)
 {
-    WsHeader* hdr = at<WsHeader>(ws, 0);
-    BoxDev* boxes = at<BoxDev>(ws, p.o_boxes);
-    NF_CUDA(cudaMemsetAsync(hdr, 0, sizeof(WsHeader), s), "clear header");
+    NF_CUDA(cudaMemsetAsync(at<WsHeader>(ws, 0), 0, sizeof(WsHeader), s), "clear header");
     if (g_debug && !p.guards.empty()) {
         GuardList gl;
         std::memset(&gl, 0, sizeof gl);
@@ -323,6 +323,16 @@ int run_binning(const Plan& p, const float* pos, void* ws, int32_t* cell_off, fl
         count_launches(1);
         NF_CUDA(cudaGetLastError(), "guard setup");
     }
+    return NF_OK;
+}
+
+int run_binning(const Plan& p, const float* pos, void* ws, int32_t* cell_off, float4* rel, int32_t* perm,
+                cudaStream_t s)
+{
+    WsHeader* hdr = at<WsHeader>(ws, 0);
+    BoxDev* boxes = at<BoxDev>(ws, p.o_boxes);
+    int rc = init_ws(p, ws, s);
+    if (rc) return rc;
     NF_CUDA(cudaMemsetAsync(cell_off, 0, 4 * (size_t)(p.C + 1), s), "clear counts");
     for (int first = 0; first < p.nboxes; first += kMaxBoxesPerFill) {
         BoxFill f;
@@ -709,21 +719,28 @@ struct FarLayout {
     size_t o_M = 0, o_Mh = 0, o_Th = 0, o_work = 0, work = 0, total = 0;
 };
 
-FarLayout far_layout(const Plan& pl, int K, int p)
+// The far-field regions follow the binning plan's; in debug mode each is
+// followed by a guard block like the plan's regions (appended to guards).
+FarLayout far_layout(const Plan& pl, int K, int p, std::vector<size_t>* guards = nullptr)
 {
     FarLayout F;
     const int nt = far_terms_host(p);
     const size_t spec = 16 * (size_t)nt * K * K * (K / 2 + 1);
     size_t o = align_up(pl.total);
-    F.o_M = o;
-    o = align_up(o + 8 * (size_t)nt * K * K * K);
-    F.o_Mh = o;
-    o = align_up(o + spec);
-    F.o_Th = o;
-    o = align_up(o + spec);
-    F.o_work = o;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align_up(o + bytes);
+        if (g_debug) {
+            if (guards) guards->push_back(o);
+            o = align_up(o + kGuardBytes);
+        }
+        return at;
+    };
+    F.o_M = take(8 * (size_t)nt * K * K * K);
+    F.o_Mh = take(spec);
+    F.o_Th = take(spec);
     F.work = far_fft_work_bytes(K, nt);
-    o = align_up(o + F.work);
+    F.o_work = take(F.work);
     F.total = o;
     return F;
 }
@@ -882,7 +899,9 @@ int far_prepare(const float* pos, int64_t N, double box, int K, int R, int p, co
     nf_box b = one_box(N, box, K, 0, 0.0);
     rc = make_plan(&b, 1, false, 32, &fc->pl);
     if (rc) return rc;
-    fc->F = far_layout(fc->pl, K, p);
+    std::vector<size_t> far_guards;
+    fc->F = far_layout(fc->pl, K, p, &far_guards);
+    fc->pl.guards.insert(fc->pl.guards.end(), far_guards.begin(), far_guards.end());
     rc = check_ws(fc->pl, ws, ws_bytes);
     if (rc) return rc;
     if (ws_bytes < fc->F.total)
@@ -913,6 +932,9 @@ int run_far(const FarCall& fc, const float* pos, int64_t N, double box, int K, i
     if (!binned) {
         int rc = run_binning(pl, pos, ws, at<int32_t>(ws, pl.o_off), at<float4>(ws, pl.o_rel),
                              at<int32_t>(ws, pl.o_perm), s);
+        if (rc) return rc;
+    } else {
+        int rc = init_ws(pl, ws, s);  // status header and guards of the far workspace
         if (rc) return rc;
     }
     NF_CUDA(mark(1), "profile");
