@@ -300,8 +300,10 @@ size_t nf_far_workspace_bytes(int64_t N, int K, int p);
  * `stream`.  The first call for a (K, p) on a device creates its cuFFT plans
  * (cuFFT keeps its own small tables); make it before any graph capture.
  * Errors: NF_ERR_ARG for K < 2R+1, R outside 1..NF_MAX_R, p outside
- * 0..NF_MAX_FAR_ORDER, box <= 0 or NULL pointers; NF_ERR_WORKSPACE for a
- * short or misaligned buffer; NF_ERR_CUDA if a launch or transform fails. */
+ * 0..NF_MAX_FAR_ORDER, (p+3)(p+2)(p+1)/6 K^3 >= 2^31 (the FFT plans' 32-bit
+ * element offsets; e.g. K <= 232 at p = 8), box <= 0 or NULL pointers;
+ * NF_ERR_WORKSPACE for a short or misaligned buffer; NF_ERR_CUDA if a
+ * launch or transform fails. */
 int nf_derivatives(int K, int R, int p, double box, void *derivs, size_t derivs_bytes,
                    void *ws, size_t ws_bytes, void *stream);
 

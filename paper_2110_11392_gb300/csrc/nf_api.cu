@@ -694,9 +694,12 @@ struct DerivLayout {
     size_t o_seg = 0, o_pairs = 0, o_dh = 0, total = 0;
 };
 
+// K^3 and, for the cuFFT plans' 32-bit element offsets, n_t K^3 below 2^31
 bool far_args_ok(int K, int p)
 {
-    return K >= 1 && p >= 0 && p <= NF_MAX_FAR_ORDER && (int64_t)K * K * K < (int64_t(1) << 31);
+    if (K < 1 || p < 0 || p > NF_MAX_FAR_ORDER) return false;
+    const int64_t cells = (int64_t)K * K * K;
+    return cells < (int64_t(1) << 31) && (int64_t)far_terms_host(p) * cells < (int64_t(1) << 31);
 }
 
 DerivLayout deriv_layout(int K, int p)
@@ -757,7 +760,9 @@ std::map<const void*, DerivKey> g_derivs;
 
 int far_validate(int K, int R, int p, double box)
 {
-    if (!far_args_ok(K, p)) return fail(NF_ERR_ARG, "far field: K = %d or order p = %d out of range (p <= %d)", K, p, NF_MAX_FAR_ORDER);
+    if (!far_args_ok(K, p))
+        return fail(NF_ERR_ARG, "far field: K = %d or order p = %d out of range (p <= %d, (p+3)(p+2)(p+1)/6 K^3 < 2^31)",
+                    K, p, NF_MAX_FAR_ORDER);
     if (R < 1 || R > NF_MAX_R) return fail(NF_ERR_ARG, "R = %d out of [1, %d]", R, NF_MAX_R);
     if (K < 2 * R + 1) return fail(NF_ERR_ARG, "K = %d < 2R+1 = %d: the stencil would wrap onto itself", K, 2 * R + 1);
     if (!(box > 0.0) || !std::isfinite(box)) return fail(NF_ERR_ARG, "box = %g must be finite and > 0", box);
