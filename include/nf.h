@@ -301,7 +301,7 @@ size_t nf_far_workspace_bytes(int64_t N, int K, int p);
  * (cuFFT keeps its own small tables); make it before any graph capture.
  * Errors: NF_ERR_ARG for K < 2R+1, R outside 1..NF_MAX_R, p outside
  * 0..NF_MAX_FAR_ORDER, (p+3)(p+2)(p+1)/6 K^3 >= 2^31 (the FFT plans' 32-bit
- * element offsets; e.g. K <= 232 at p = 8), box <= 0 or NULL pointers;
+ * element offsets; K <= 235 at p = 8), box <= 0 or NULL pointers;
  * NF_ERR_WORKSPACE for a short or misaligned buffer; NF_ERR_CUDA if a
  * launch or transform fails. */
 int nf_derivatives(int K, int R, int p, double box, void *derivs, size_t derivs_bytes,

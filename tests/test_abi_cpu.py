@@ -138,8 +138,8 @@ def test_far_field_sizes_and_host_checks():
         assert b % 256 == 0
         assert _lib.nf_far_workspace_bytes(1000, K, p) > 8 * nt(p) * K ** 3
     assert _lib.nf_derivatives_bytes(8, 13) == 0 and _lib.nf_derivatives_bytes(0, 4) == 0
-    # 165 terms x 256^3 cells would overflow the FFT plans' 32-bit offsets; 232^3 does not
-    assert _lib.nf_derivatives_bytes(256, 8) == 0 and _lib.nf_derivatives_bytes(232, 8) > 0
+    # 165 terms x 236^3 cells would overflow the FFT plans' 32-bit offsets; 235^3 does not
+    assert _lib.nf_derivatives_bytes(236, 8) == 0 and _lib.nf_derivatives_bytes(235, 8) > 0
     assert _lib.nf_far_workspace_bytes(0, 8, 4) == 0
     big = 1 << 40
     # rejected on the host before anything is launched
