@@ -354,6 +354,7 @@ def run_native(args, rank, world, local):
                   "lane_utilisation": st["pairs"] / max(st["lane_pairs"], 1)},
     }
 
+    out["uniform"] = measure_uniform(w, dev, flush, fp32_peak)
     out["density"] = measure_density(w, pos, ws, acc, fwd_pair_ms, flush)
     out["kdk"] = measure_kdk(w, dev, flush)
     out["multipoles"] = measure_multipoles(w, pos, dev, flush)
@@ -409,6 +410,39 @@ def measure_fma_peak(dev, target_ms=40.0, reps=3):
     out["probe"] = ("nf_fma_probe: 4 x 256 threads per SM, 8 independent multiply-add chains per thread "
                     "(f32, f32x2, f64), best of 3")
     return out
+
+
+def measure_uniform(w, dev, flush, fp32_peak, reps=5):
+    """The forward on a uniform (i.i.d.) set of the same N, K, R and softening
+    as the workload (seed 101): pair kernel and whole call, pairs/s and the
+    fraction of the FP32 roofline."""
+    import torch
+    import workloads as W
+    from paper_2110_11392_gb300 import _lib
+    pos = torch.from_numpy(W.uniform_positions(w.N, 101, w.box)).to(dev)
+    ws = torch.empty(_lib.nf_workspace_bytes(w.N, w.K, w.R), dtype=torch.uint8, device=dev)
+    acc = torch.empty_like(pos)
+    _lib.nf_forces(pos, w.box, w.K, w.R, w.eps, acc, None, ws)
+    P = _lib.nf_stats_read(ws)["pairs"]
+    stream = torch.cuda.current_stream(dev)
+    _lib.nf_profile_enable(True)
+    call_ms, pair_ms = [], []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _lib.nf_forces(pos, w.box, w.K, w.R, w.eps, acc, None, ws)
+        b.record(stream)
+        b.synchronize()
+        call_ms.append(a.elapsed_time(b))
+        pair_ms.append(_lib.nf_profile_read(0)["pair_ms"])
+    _lib.nf_profile_enable(False)
+    t_call, t_pair = float(np.median(call_ms)), float(np.median(pair_ms))
+    achieved = FLOP_PER_PAIR * P / (t_pair / 1e3) / 1e12
+    return {"workload": f"uniform: N={w.N}, K={w.K}, R={w.R}, same softening, seed 101", "pairs_per_pass": P,
+            "pair_kernel_ms": t_pair, "ms": t_call, "pairs_per_s": P / (t_call / 1e3),
+            "pair_kernel_pairs_per_s": P / (t_pair / 1e3),
+            "particle_updates_per_s": w.N / (t_call / 1e3), "roofline_frac": achieved / fp32_peak}
 
 
 def measure_density(w, pos, ws, acc, fwd_pair_ms, flush):
