@@ -689,9 +689,9 @@ constexpr int kFarNimg = 1;
 constexpr int kFarHmax = 14;
 
 struct DerivLayout {
-    int nt = 0;
-    long long npairs = 0;
-    size_t o_seg = 0, o_pairs = 0, o_dh = 0, total = 0;
+    int nt = 0, nr = 0;
+    long long npairs = 0, nnz = 0;
+    size_t o_seg = 0, o_pairs = 0, o_dh = 0, o_rseg = 0, o_rk = 0, o_rcoef = 0, o_ops = 0, o_opf = 0, total = 0;
 };
 
 // K^3 and, for the cuFFT plans' 32-bit element offsets, n_t K^3 below 2^31
@@ -702,33 +702,65 @@ bool far_args_ok(int K, int p)
     return cells < (int64_t(1) << 31) && (int64_t)far_terms_host(p) * cells < (int64_t(1) << 31);
 }
 
+// Table sizes of order p (they do not depend on the cell width), cached.
+struct TableCounts {
+    int nr;
+    long long npairs, nnz;
+};
+TableCounts table_counts(int p)
+{
+    static std::mutex mu;
+    static std::map<int, TableCounts> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(p);
+    if (it != cache.end()) return it->second;
+    const FarTables tb = far_tables(p, 1.0);
+    const TableCounts c{tb.nr, (long long)tb.pairs.size(), (long long)tb.red_k.size()};
+    cache[p] = c;
+    return c;
+}
+
 DerivLayout deriv_layout(int K, int p)
 {
     DerivLayout L;
     L.nt = far_terms_host(p);
-    L.npairs = far_pairs_count(p);
+    const TableCounts c = table_counts(p);
+    L.nr = c.nr;
+    L.npairs = c.npairs;
+    L.nnz = c.nnz;
     size_t o = align_up(sizeof(DerivHeader));
-    L.o_seg = o;
-    o = align_up(o + 4 * (size_t)(L.nt + 1));
-    L.o_pairs = o;
-    o = align_up(o + sizeof(FarPair) * (size_t)L.npairs);
-    L.o_dh = o;
-    o = align_up(o + 8 * (size_t)L.nt * K * K * (K / 2 + 1));  // one real per (term, frequency)
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    L.o_seg = take(4 * (size_t)(L.nr + 1));
+    L.o_pairs = take(sizeof(FarPair) * (size_t)L.npairs);
+    L.o_rseg = take(4 * (size_t)(L.nr + 1));
+    L.o_rk = take(4 * (size_t)L.nnz);
+    L.o_rcoef = take(8 * (size_t)L.nnz);
+    L.o_ops = take(sizeof(int4) * (size_t)L.nt);
+    L.o_opf = take(sizeof(double2) * (size_t)L.nt);
+    L.o_dh = take(8 * (size_t)L.nt * K * K * (K / 2 + 1));  // one real per (term, frequency)
     L.total = o;
     return L;
 }
 
 struct FarLayout {
-    size_t o_M = 0, o_Mh = 0, o_Th = 0, o_work = 0, work = 0, total = 0;
+    size_t o_M = 0, o_Mr = 0, o_Mh = 0, o_Th = 0, o_Tdf = 0, o_s002 = 0, o_work = 0, work = 0, total = 0;
 };
 
 // The far-field regions follow the binning plan's; in debug mode each is
 // followed by a guard block like the plan's regions (appended to guards).
+// M: complete multipoles, later the rebuilt Taylors [C][nt]; Mr: reduced
+// multipoles, later the reduced Taylors [C][nr]; Mh, Th: spectra [nr][nq];
+// Tdf: double-float Taylor pairs [C][nt]; s002: one double.
 FarLayout far_layout(const Plan& pl, int K, int p, std::vector<size_t>* guards = nullptr)
 {
     FarLayout F;
-    const int nt = far_terms_host(p);
-    const size_t spec = 16 * (size_t)nt * K * K * (K / 2 + 1);
+    const int nt = far_terms_host(p), nr = table_counts(p).nr;
+    const size_t cells = (size_t)K * K * K;
+    const size_t spec = 16 * (size_t)nr * K * K * (K / 2 + 1);
     size_t o = align_up(pl.total);
     auto take = [&](size_t bytes) {
         const size_t at = o;
@@ -739,10 +771,15 @@ FarLayout far_layout(const Plan& pl, int K, int p, std::vector<size_t>* guards =
         }
         return at;
     };
-    F.o_M = take(8 * (size_t)nt * K * K * K);
+    F.o_M = take(8 * (size_t)nt * cells);
+    F.o_Mr = take(8 * (size_t)nr * cells);
     F.o_Mh = take(spec);
     F.o_Th = take(spec);
-    F.work = far_fft_work_bytes(K, nt);
+    F.o_Tdf = take(8 * (size_t)nt * cells);
+    F.o_s002 = take(8);
+    // the derivatives' transform (nt fields) and the far call's (nr fields) share the area
+    const size_t w1 = far_fft_work_bytes(K, nt), w2 = far_fft_work_bytes(K, nr);
+    F.work = w1 > w2 ? w1 : w2;
     F.o_work = take(F.work);
     F.total = o;
     return F;
@@ -839,15 +876,36 @@ int nf_derivatives(int K, int R, int p, double box, void* derivs, size_t derivs_
         return fail(NF_ERR_WORKSPACE, "workspace too small: %zu bytes given, %zu needed", ws_bytes, F.total);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const double alpha = kFarAlphaL / box;
+    // D (real, [C][nt]) in the multipole region; its spectrum ([nt][nq] complex) needs
+    // 16 nt nq bytes: the multipole, reduced and double-float regions that follow
+    // the first one are contiguous and large enough (checked below)
     double* D = at<double>(ws, F.o_M);
-    double2* Dh = at<double2>(ws, F.o_Mh);
+    double2* Dh = at<double2>(ws, F.o_Mr);
+    if (F.o_Mr + 16 * (size_t)L.nt * K * K * (K / 2 + 1) > F.o_work)
+        return fail(NF_ERR_WORKSPACE, "internal: derivative spectrum does not fit the far workspace");
     NF_CUDA(launch_deriv_real(K, R, p, box, alpha, kFarNimg, D, s), "derivatives (real space)");
     cudaError_t e = launch_far_fft(K, L.nt, true, D, Dh, at<void>(ws, F.o_work), F.work, s);
     if (e != cudaSuccess) return fft_fail(e, "derivatives (forward FFT)");
     NF_CUDA(launch_deriv_recip(K, p, box, alpha, kFarHmax, Dh, at<double>(derivs, L.o_dh), s),
             "derivatives (reciprocal space)");
-    NF_CUDA(launch_far_pairs(p, box / K, at<int>(derivs, L.o_seg), at<FarPair>(derivs, L.o_pairs), s),
-            "convolution pairs");
+    {
+        // the fold, reduced-pair and rebuild tables, built on the host (pageable copies:
+        // the call returns once the data is staged)
+        const FarTables tb = far_tables(p, box / K);
+        if ((long long)tb.pairs.size() != L.npairs || (long long)tb.red_k.size() != L.nnz || tb.nr != L.nr)
+            return fail(NF_ERR_ARG, "internal: far-field table sizes disagree");
+        auto up = [&](size_t off, const void* src, size_t bytes) {
+            return bytes ? cudaMemcpyAsync(at<char>(derivs, off), src, bytes, cudaMemcpyHostToDevice, s)
+                         : cudaSuccess;
+        };
+        NF_CUDA(up(L.o_seg, tb.pair_seg.data(), 4 * tb.pair_seg.size()), "far tables");
+        NF_CUDA(up(L.o_pairs, tb.pairs.data(), sizeof(FarPair) * tb.pairs.size()), "far tables");
+        NF_CUDA(up(L.o_rseg, tb.red_seg.data(), 4 * tb.red_seg.size()), "far tables");
+        NF_CUDA(up(L.o_rk, tb.red_k.data(), 4 * tb.red_k.size()), "far tables");
+        NF_CUDA(up(L.o_rcoef, tb.red_coef.data(), 8 * tb.red_coef.size()), "far tables");
+        NF_CUDA(up(L.o_ops, tb.ops.data(), sizeof(int4) * tb.ops.size()), "far tables");
+        NF_CUDA(up(L.o_opf, tb.opf.data(), sizeof(double2) * tb.opf.size()), "far tables");
+    }
     DerivHeader h;
     std::memset(&h, 0, sizeof h);
     h.magic = kDerivMagic;
@@ -859,10 +917,17 @@ int nf_derivatives(int K, int R, int p, double box, void* derivs, size_t derivs_
     h.nimg = kFarNimg;
     h.hmax = kFarHmax;
     h.nt = L.nt;
+    h.nr = L.nr;
     h.npairs = L.npairs;
+    h.nnz = L.nnz;
     h.o_seg = L.o_seg;
     h.o_pairs = L.o_pairs;
     h.o_dh = L.o_dh;
+    h.o_rseg = L.o_rseg;
+    h.o_rk = L.o_rk;
+    h.o_rcoef = L.o_rcoef;
+    h.o_ops = L.o_ops;
+    h.o_opf = L.o_opf;
     h.total = L.total;
     NF_CUDA(launch_deriv_header(h, derivs, s), "derivatives header");
     {
@@ -954,19 +1019,36 @@ int run_far(const FarCall& fc, const float* pos, int64_t N, double box, int K, i
     else
         NF_CUDA(launch_multipoles(off, rel, C, 1.0, p, M, s), "multipoles");
     NF_CUDA(mark(2), "profile");
-    cudaError_t e = launch_far_fft(K, L.nt, true, M, Mh, at<void>(ws, F.o_work), F.work, s);
+    // reduced basis: fold the multipoles, convolve (p+1)^2 fields, rebuild the complete Taylors
+    const double w = box / K, V = box * box * box;
+    double* Mr = at<double>(ws, F.o_Mr);
+    double* s002 = at<double>(ws, F.o_s002);
+    char* dv = static_cast<char*>(const_cast<void*>(derivs));
+    auto dat = [&](size_t off) { return static_cast<void*>(dv + off); };
+    NF_CUDA(launch_far_reduce(M, C, L.nt, L.nr, static_cast<const int*>(dat(L.o_rseg)),
+                              static_cast<const int*>(dat(L.o_rk)), static_cast<const double*>(dat(L.o_rcoef)), Mr,
+                              s),
+            "multipole fold");
+    const int i002 = p >= 2 ? 2 : -1;  // (0,0,2): the third term of the complete basis (a, then b, then c)
+    if (i002 >= 0) NF_CUDA(launch_far_sum_term(M, C, L.nt, i002, s002, s), "sum of the (0,0,2) multipoles");
+    cudaError_t e = launch_far_fft(K, L.nr, true, Mr, Mh, at<void>(ws, F.o_work), F.work, s);
     if (e != cudaSuccess) return fft_fail(e, "multipoles (forward FFT)");
-    NF_CUDA(launch_far_contract(K, p, at<const int>(const_cast<void*>(derivs), L.o_seg),
-                                at<const FarPair>(const_cast<void*>(derivs), L.o_pairs),
-                                at<const double>(const_cast<void*>(derivs), L.o_dh), Mh, Th, s),
+    NF_CUDA(launch_far_contract(K, L.nr, static_cast<const int*>(dat(L.o_seg)),
+                                static_cast<const FarPair*>(dat(L.o_pairs)), static_cast<const double*>(dat(L.o_dh)),
+                                Mh, Th, s),
             "convolution");
-    double* T = M;  // the multipoles are no longer needed
-    e = launch_far_fft(K, L.nt, false, Th, T, at<void>(ws, F.o_work), F.work, s);
+    e = launch_far_fft(K, L.nr, false, Th, Mr, at<void>(ws, F.o_work), F.work, s);
     if (e != cudaSuccess) return fft_fail(e, "Taylors (inverse FFT)");
+    double* T = M;  // the complete multipoles are no longer needed: the rebuilt Taylors go there
+    NF_CUDA(launch_far_rebuild(Mr, C, L.nt, L.nr, static_cast<const int4*>(dat(L.o_ops)),
+                               static_cast<const double2*>(dat(L.o_opf)), i002,
+                               4.0 * 3.14159265358979323846 * (double)N * w * w / V,
+                               2.0 * 3.14159265358979323846 * w * w / V, i002 >= 0 ? s002 : nullptr, T, s),
+            "Taylors (rebuild)");
     NF_CUDA(mark(3), "profile");
     const double scale = 1.0 / ((double)N * (box / K));  // m / w: cell-unit gradient to box units
-    if ((acc_far || acc_add) && dfl)  // the spectrum region is free again: it holds the coefficient pairs
-        NF_CUDA(launch_taylor_forces_df(p, off, rel, T, Th, (int)N, C, scale, acc_far, acc_add, s),
+    if ((acc_far || acc_add) && dfl)
+        NF_CUDA(launch_taylor_forces_df(p, off, rel, T, at<void>(ws, F.o_Tdf), (int)N, C, scale, acc_far, acc_add, s),
                 "Taylor forces (double-float)");
     else if (acc_far || acc_add)
         NF_CUDA(launch_taylor_forces(p, off, rel, T, (int)N, C, 1.0, scale, acc_far, acc_add, s), "Taylor forces");

@@ -298,42 +298,6 @@ __global__ void k_deriv_recip(int K, int p, int nt, double box, double alpha, in
     }
 }
 
-// The (n, k) pairs of the convolution, grouped by n: seg[n]..seg[n+1] index
-// pairs (k, n+k) with coefficient (-1)^{|k|} w^{|n|+|k|} / (n! k!); the sign
-// bit of j marks an odd total order.  The factor w^{|n|+|k|} makes the
-// convolution take multipoles in cell units (displacements / w) and give
-// Taylors in cell units, T'^n = T^n w^{|n|}, so the per-particle kernels
-// work on the stored cell-centred offsets directly.  One thread.
-__global__ void k_far_pairs(int p, double w, int* __restrict__ seg, FarPair* __restrict__ pairs)
-{
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    double fac[kMaxFarOrder + 1], wp[2 * kMaxFarOrder + 1];
-    fac[0] = 1.0;
-    for (int i = 1; i <= p; ++i) fac[i] = fac[i - 1] * i;
-    wp[0] = 1.0;
-    for (int i = 1; i <= p; ++i) wp[i] = wp[i - 1] * w;
-    int e = 0, n = 0;
-    for (int na = 0; na <= p; ++na)
-        for (int nb = 0; nb <= p - na; ++nb)
-            for (int nc = 0; nc <= p - na - nb; ++nc, ++n) {
-                seg[n] = e;
-                const int rem = p - na - nb - nc;
-                for (int ka = 0; ka <= rem; ++ka)
-                    for (int kb = 0; kb <= rem - ka; ++kb)
-                        for (int kc = 0; kc <= rem - ka - kb; ++kc) {
-                            FarPair pr;
-                            pr.k = encode_term(ka, kb, kc, p);
-                            pr.j = encode_term(na + ka, nb + kb, nc + kc, p);
-                            // odd total order: the transform of D^j is imaginary (sign bit of j)
-                            if ((na + nb + nc + ka + kb + kc) & 1) pr.j |= (int)0x80000000u;
-                            pr.coef = (((ka + kb + kc) & 1) ? -1.0 : 1.0) * wp[na + nb + nc + ka + kb + kc] /
-                                      (fac[na] * fac[nb] * fac[nc] * fac[ka] * fac[kb] * fac[kc]);
-                            pairs[e++] = pr;
-                        }
-            }
-    seg[n] = e;
-}
-
 // Th[n][q] = scale * sum_{pairs of n} coef * D^{n+k}(q) * Mh[k][q], one thread
 // per (n, q), q fastest: a warp shares n, so the pair list is a broadcast and
 // the Dr and Mh rows are read coalesced; one thread per q alone would leave
@@ -691,6 +655,71 @@ __global__ void k_unscale_taylors(const double* __restrict__ Tc, long long total
     }
 }
 
+// Fold of the complete multipoles onto the reduced ones: Mr[c][r] =
+// sum_{entries of r} coef * M[c][k]; one thread per (cell, reduced term).
+__global__ void k_far_reduce(const double* __restrict__ M, int C, int nt, int nr, const int* __restrict__ seg,
+                             const int* __restrict__ kidx, const double* __restrict__ coef, double* __restrict__ Mr)
+{
+    const long long total = (long long)C * nr;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long c = e / nr;
+        const int r = (int)(e - c * nr);
+        const double* m = M + c * nt;
+        double acc = 0.0;
+        for (int i = seg[r]; i < seg[r + 1]; ++i) acc = fma(coef[i], m[kidx[i]], acc);
+        Mr[e] = acc;
+    }
+}
+
+// out = sum over cells of M[c][term], one block, fixed order.
+__global__ void k_far_sum_term(const double* __restrict__ M, int C, int nt, int term, double* __restrict__ out)
+{
+    __shared__ double part[1024];
+    double acc = 0.0;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) acc += M[(size_t)c * nt + term];
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) part[threadIdx.x] += part[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = part[0];
+}
+
+// Complete Taylors of every cell from the reduced ones (the rebuild program
+// in shared memory; one thread per cell).  lap is the Laplacian of the
+// series (4 pi N w^2 / V in cell units), t0_per_s002 * (*s002) the constant
+// of T^0.
+__global__ void k_far_rebuild(const double* __restrict__ Tr, int C, int nt, int nr, const int4* __restrict__ ops,
+                              const double2* __restrict__ opf, int t002, double lap, double t0_per_s002,
+                              const double* __restrict__ s002, double* __restrict__ T)
+{
+    extern __shared__ int4 prog[];  // [nt] ops, then [nt] factors
+    double2* fs = reinterpret_cast<double2*>(prog + nt);
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+        prog[i] = ops[i];
+        fs[i] = opf[i];
+    }
+    __syncthreads();
+    const double t0 = (t002 >= 0 && s002) ? t0_per_s002 * (*s002) : 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+        const double* tr = Tr + (size_t)c * nr;
+        double* t = T + (size_t)c * nt;
+        for (int i = 0; i < nt; ++i) {
+            const int4 op = prog[i];
+            if (op.y >= 0) {
+                t[op.x] = tr[op.y];
+            } else {
+                double v = -fs[i].x * t[op.z] - fs[i].y * t[op.w];
+                if (op.x == t002) v += 0.5 * lap;  // m = 0: (2)(1) T^{002} = lap - ...
+                t[op.x] = v;
+            }
+        }
+        t[0] += t0;
+    }
+}
+
 __global__ void k_deriv_header(DerivHeader h, DerivHeader* dst)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) *dst = h;
@@ -760,12 +789,103 @@ cudaError_t get_plan(int K, int nt, bool forward, PlanEntry* out)
 
 int far_terms_host(int p) { return far_terms(p); }
 
-long long far_pairs_count(int p)
+// Reduced basis (Sec. "Far-field Computation": the paper converts the
+// multipoles to a reduced basis of (p+1)^2 values before the FFTs).  Away from
+// the lattice points every trace of the derivatives vanishes except the
+// second-order one, which is the background's 4 pi / V:
+//     D^{i+2ex} + D^{i+2ey} + D^{i+2ez} = (4 pi / V) [i = 0],
+// so D^{n+k} with k_z >= 2 equals -D^{n+k-2ez+2ex} - D^{n+k-2ez+2ey} (plus
+// 4 pi/V when n + k = 2ez, a constant potential in every cell).  Applied
+// repeatedly this folds every multipole onto the terms with k_z <= 1 (same
+// order |k|, so the truncation |n| + |k| <= p is kept): the convolution and
+// its FFTs run on (p+1)^2 fields.  The Taylors are computed for the reduced
+// n the same way and the rest rebuilt per cell from the Laplacian of the
+// truncated series, which is exactly 4 pi N / V (the same identity summed
+// over the sources):  (m_x+2)(m_x+1) T^{m+2ex} + (m_y+2)(m_y+1) T^{m+2ey}
+// + (m_z+2)(m_z+1) T^{m+2ez} = (4 pi N / V) [m = 0].  The constant the fold
+// drops from T^0 is added back from the sum of the (0,0,2) multipoles.
+FarTables far_tables(int p, double w)
 {
-    // 6-tuples of non-negative integers with sum <= p: C(p + 6, 6)
-    long long c = 1;
-    for (int i = 1; i <= 6; ++i) c = c * (p + i) / i;
-    return c;
+    FarTables tb;
+    const int nt = far_terms(p);
+    std::vector<int> ta(nt), tbv(nt), tc(nt), rindex(nt, -1);
+    {
+        int t = 0;
+        for (int a = 0; a <= p; ++a)
+            for (int b = 0; b <= p - a; ++b)
+                for (int c = 0; c <= p - a - b; ++c, ++t) {
+                    ta[t] = a;
+                    tbv[t] = b;
+                    tc[t] = c;
+                    if (c <= 1) rindex[t] = tb.nr++;
+                }
+    }
+    double fac[2 * kMaxFarOrder + 2];
+    fac[0] = 1.0;
+    for (int i = 1; i <= 2 * kMaxFarOrder + 1; ++i) fac[i] = fac[i - 1] * i;
+    // E(k): the reduced terms D^{n+k} folds onto, with integer coefficients
+    std::vector<std::map<int, double>> E(nt);
+    for (int c = 0; c <= p; ++c)  // by k_z, so the folded terms are known first
+        for (int t = 0; t < nt; ++t) {
+            if (tc[t] != c) continue;
+            if (c <= 1) {
+                E[t][rindex[t]] = 1.0;
+                continue;
+            }
+            const int s1 = encode_term(ta[t] + 2, tbv[t], c - 2, p), s2 = encode_term(ta[t], tbv[t] + 2, c - 2, p);
+            for (const auto& kv : E[s1]) E[t][kv.first] -= kv.second;
+            for (const auto& kv : E[s2]) E[t][kv.first] -= kv.second;
+        }
+    // the fold, grouped by reduced term: Mr^r = sum_k (-1)^{|k|} / k! E(k)_r M^k
+    std::vector<std::vector<std::pair<int, double>>> by_r(tb.nr);
+    for (int t = 0; t < nt; ++t) {
+        const double wk = (((ta[t] + tbv[t] + tc[t]) & 1) ? -1.0 : 1.0) / (fac[ta[t]] * fac[tbv[t]] * fac[tc[t]]);
+        for (const auto& kv : E[t])
+            if (kv.second != 0.0) by_r[kv.first].push_back({t, wk * kv.second});
+    }
+    tb.red_seg.push_back(0);
+    for (int r = 0; r < tb.nr; ++r) {
+        for (const auto& e : by_r[r]) {
+            tb.red_k.push_back(e.first);
+            tb.red_coef.push_back(e.second);
+        }
+        tb.red_seg.push_back((int)tb.red_k.size());
+    }
+    // reduced pairs: T^n = w^{|n|+|k|} / n! D^{n+k} Mr^k, n and k reduced, |n| + |k| <= p
+    std::vector<double> wp(2 * kMaxFarOrder + 1, 1.0);
+    for (int i = 1; i <= p; ++i) wp[i] = wp[i - 1] * w;
+    tb.pair_seg.push_back(0);
+    for (int n = 0; n < nt; ++n) {
+        if (rindex[n] < 0) continue;
+        for (int k = 0; k < nt; ++k) {
+            if (rindex[k] < 0) continue;
+            const int order = ta[n] + tbv[n] + tc[n] + ta[k] + tbv[k] + tc[k];
+            if (order > p) continue;
+            FarPair pr;
+            pr.k = rindex[k];
+            pr.j = encode_term(ta[n] + ta[k], tbv[n] + tbv[k], tc[n] + tc[k], p);
+            if (order & 1) pr.j |= (int)0x80000000u;
+            pr.coef = wp[order] / (fac[ta[n]] * fac[tbv[n]] * fac[tc[n]]);
+            tb.pairs.push_back(pr);
+        }
+        tb.pair_seg.push_back((int)tb.pairs.size());
+    }
+    // rebuild program, by z index: copies of the reduced Taylors, then the recursion
+    for (int c = 0; c <= p; ++c)
+        for (int t = 0; t < nt; ++t) {
+            if (tc[t] != c) continue;
+            if (c <= 1) {
+                tb.ops.push_back(make_int4(t, rindex[t], 0, 0));
+                tb.opf.push_back(make_double2(0.0, 0.0));
+                continue;
+            }
+            const int a = ta[t], b = tbv[t];
+            const double inv = 1.0 / (double)(c * (c - 1));
+            tb.ops.push_back(make_int4(t, -1, encode_term(a + 2, b, c - 2, p), encode_term(a, b + 2, c - 2, p)));
+            tb.opf.push_back(make_double2((a + 2) * (a + 1) * inv, (b + 2) * (b + 1) * inv));
+        }
+    tb.t002 = p >= 2 ? encode_term(0, 0, 2, p) : -1;
+    return tb;
 }
 
 size_t far_fft_work_bytes(int K, int nt)
@@ -916,6 +1036,39 @@ cudaError_t launch_unscale_taylors(const double* Tc, int C, int p, double w, dou
     return cudaGetLastError();
 }
 
+cudaError_t launch_far_reduce(const double* M, int C, int nt, int nr, const int* seg, const int* kidx,
+                              const double* coef, double* Mr, cudaStream_t s)
+{
+    const long long total = (long long)C * nr;
+    long long blocks = (total + 255) / 256;
+    const long long cap = (long long)device_sms() * 32;
+    if (blocks > cap) blocks = cap;
+    k_far_reduce<<<(int)blocks, 256, 0, s>>>(M, C, nt, nr, seg, kidx, coef, Mr);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_far_sum_term(const double* M, int C, int nt, int term, double* out, cudaStream_t s)
+{
+    k_far_sum_term<<<1, 1024, 0, s>>>(M, C, nt, term, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_far_rebuild(const double* Tr, int C, int nt, int nr, const int4* ops, const double2* opf, int t002,
+                               double lap, double t0_per_s002, const double* s002, double* T, cudaStream_t s)
+{
+    const size_t smem = (size_t)nt * (sizeof(int4) + sizeof(double2));
+    cudaError_t e = ensure_smem((const void*)k_far_rebuild, (int)smem);
+    if (e != cudaSuccess) return e;
+    int blocks = (C + 127) / 128;
+    const int cap = device_sms() * 16;
+    if (blocks > cap) blocks = cap;
+    k_far_rebuild<<<blocks, 128, smem, s>>>(Tr, C, nt, nr, ops, opf, t002, lap, t0_per_s002, s002, T);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_deriv_header(const DerivHeader& h, void* dst, cudaStream_t s)
 {
     k_deriv_header<<<1, 32, 0, s>>>(h, static_cast<DerivHeader*>(dst));
@@ -923,22 +1076,15 @@ cudaError_t launch_deriv_header(const DerivHeader& h, void* dst, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_far_pairs(int p, double w, int* seg, FarPair* pairs, cudaStream_t s)
-{
-    k_far_pairs<<<1, 32, 0, s>>>(p, w, seg, pairs);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_far_contract(int K, int p, const int* seg, const FarPair* pairs, const double* Dr,
+cudaError_t launch_far_contract(int K, int nout, const int* seg, const FarPair* pairs, const double* Dr,
                                 const double2* Mh, double2* Th, cudaStream_t s)
 {
     const long long nq = (long long)K * K * (K / 2 + 1);
-    long long blocks = (nq * far_terms(p) + 255) / 256;
+    long long blocks = (nq * nout + 255) / 256;
     const long long cap = (long long)device_sms() * 64;
     if (blocks > cap) blocks = cap;
     const double scale = 1.0 / ((double)K * K * K);  // the unnormalised inverse transform
-    k_far_contract<<<(int)blocks, 256, 0, s>>>(nq, far_terms(p), seg, pairs, Dr, Mh, Th, scale);
+    k_far_contract<<<(int)blocks, 256, 0, s>>>(nq, nout, seg, pairs, Dr, Mh, Th, scale);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -14,6 +14,9 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <map>
+#include <vector>
 #include <stdint.h>
 
 #include "../../include/nf.h"
@@ -98,16 +101,38 @@ struct DerivHeader {
     unsigned magic;
     int K, R, p;
     double box, alpha;
-    int nimg, hmax, nt, pad0;
+    int nimg, hmax, nt, nr;
     long long npairs;
-    unsigned long long o_seg, o_pairs, o_dh, total;
-    unsigned long long pad[21];
+    unsigned long long o_seg, o_pairs, o_dh, total;  // reduced pair segments and pairs, transformed derivatives
+    unsigned long long o_rseg, o_rk, o_rcoef, o_ops, o_opf;  // fold and rebuild tables
+    long long nnz;
+    unsigned long long pad[15];
 };
 static_assert(sizeof(DerivHeader) == 256, "derivatives header is 256 bytes");
 constexpr unsigned kDerivMagic = 0x4E464452u;
 cudaError_t launch_deriv_header(const DerivHeader& h, void* dst, cudaStream_t s);
 int far_terms_host(int p);
-long long far_pairs_count(int p);
+// Host-built tables of the reduced-basis convolution for order p (cell units,
+// cell width w): the fold of complete multipoles onto the (p+1)^2 reduced
+// ones (entries grouped by reduced term), the reduced (n, k) pairs, and the
+// rebuild program of the complete Taylors (one op per complete term, in an
+// order where every op's sources come first).
+struct FarTables {
+    int nr = 0;
+    std::vector<int> red_seg, red_k;
+    std::vector<double> red_coef;
+    std::vector<int> pair_seg;
+    std::vector<FarPair> pairs;
+    std::vector<int4> ops;       // (dst, reduced source or -1, s1, s2)
+    std::vector<double2> opf;    // (f1, f2): T[dst] = -f1 T[s1] - f2 T[s2] (+ the constant for (0,0,2))
+    int t002 = -1;               // complete index of (0,0,2), or -1 when p < 2
+};
+FarTables far_tables(int p, double w);
+cudaError_t launch_far_reduce(const double* M, int C, int nt, int nr, const int* seg, const int* kidx,
+                              const double* coef, double* Mr, cudaStream_t s);
+cudaError_t launch_far_sum_term(const double* M, int C, int nt, int term, double* out, cudaStream_t s);
+cudaError_t launch_far_rebuild(const double* Tr, int C, int nt, int nr, const int4* ops, const double2* opf, int t002,
+                               double lap, double t0_per_s002, const double* s002, double* T, cudaStream_t s);
 // cuFFT work-area bytes to reserve for the forward and inverse transforms of nt fields on K^3
 size_t far_fft_work_bytes(int K, int nt);
 // forward: real cell-major [K^3][nt] -> complex term-major [nt][K][K][K/2+1]; inverse the reverse
@@ -118,13 +143,13 @@ void far_release_plans();    // destroys every cached cuFFT plan
 cudaError_t launch_deriv_real(int K, int R, int p, double box, double alpha, int nimg, double* D, cudaStream_t s);
 cudaError_t launch_deriv_recip(int K, int p, double box, double alpha, int hmax, const double2* Dh, double* Dr,
                                cudaStream_t s);
-cudaError_t launch_far_pairs(int p, double w, int* seg, FarPair* pairs, cudaStream_t s);
 cudaError_t launch_unscale_taylors(const double* Tc, int C, int p, double w, double* T, cudaStream_t s);
 // double-float forms of the per-particle kernels (cell units); Tdf holds C * nt pairs of floats
 cudaError_t launch_multipoles_df(const int* off, const float4* rel, int C, int p, double* M, cudaStream_t s);
 cudaError_t launch_taylor_forces_df(int p, const int* off, const float4* rel, const double* T, void* Tdf, int N,
                                     int C, double scale, double* acc_far, float* acc_add, cudaStream_t s);
-cudaError_t launch_far_contract(int K, int p, const int* seg, const FarPair* pairs, const double* Dr,
+// Th[n][q] for nout output fields (the reduced Taylors) from the pair table
+cudaError_t launch_far_contract(int K, int nout, const int* seg, const FarPair* pairs, const double* Dr,
                                 const double2* Mh, double2* Th, cudaStream_t s);
 cudaError_t launch_taylor_forces(int p, const int* off, const float4* rel, const double* T, int N, int C, double w,
                                  double mass, double* acc_far, float* acc_add, cudaStream_t s);
