@@ -776,7 +776,7 @@ FarLayout far_layout(const Plan& pl, int K, int p, std::vector<size_t>* guards =
     F.o_Mh = take(spec);
     F.o_Th = take(spec);
     F.o_Tdf = take(8 * (size_t)nt * cells);
-    F.o_s002 = take(8);
+    F.o_s002 = take(8 * (size_t)far_sum_partials());
     // the derivatives' transform (nt fields) and the far call's (nr fields) share the area
     const size_t w1 = far_fft_work_bytes(K, nt), w2 = far_fft_work_bytes(K, nr);
     F.work = w1 > w2 ? w1 : w2;
@@ -1040,15 +1040,18 @@ int run_far(const FarCall& fc, const float* pos, int64_t N, double box, int K, i
     e = launch_far_fft(K, L.nr, false, Th, Mr, at<void>(ws, F.o_work), F.work, s);
     if (e != cudaSuccess) return fft_fail(e, "Taylors (inverse FFT)");
     double* T = M;  // the complete multipoles are no longer needed: the rebuilt Taylors go there
-    NF_CUDA(launch_far_rebuild(Mr, C, L.nt, L.nr, static_cast<const int4*>(dat(L.o_ops)),
+    const bool pairs_needed = dfl && (acc_far || acc_add);
+    NF_CUDA(launch_far_rebuild(Mr, C, p, L.nt, L.nr, static_cast<const int4*>(dat(L.o_ops)),
                                static_cast<const double2*>(dat(L.o_opf)), i002,
                                4.0 * 3.14159265358979323846 * (double)N * w * w / V,
-                               2.0 * 3.14159265358979323846 * w * w / V, i002 >= 0 ? s002 : nullptr, T, s),
+                               2.0 * 3.14159265358979323846 * w * w / V, i002 >= 0 ? s002 : nullptr,
+                               (taylors || !pairs_needed) ? T : nullptr, pairs_needed ? at<void>(ws, F.o_Tdf) : nullptr,
+                               s),
             "Taylors (rebuild)");
     NF_CUDA(mark(3), "profile");
     const double scale = 1.0 / ((double)N * (box / K));  // m / w: cell-unit gradient to box units
     if ((acc_far || acc_add) && dfl)
-        NF_CUDA(launch_taylor_forces_df(p, off, rel, T, at<void>(ws, F.o_Tdf), (int)N, C, scale, acc_far, acc_add, s),
+        NF_CUDA(launch_taylor_forces_df(p, off, rel, at<void>(ws, F.o_Tdf), (int)N, C, scale, acc_far, acc_add, s),
                 "Taylor forces (double-float)");
     else if (acc_far || acc_add)
         NF_CUDA(launch_taylor_forces(p, off, rel, T, (int)N, C, 1.0, scale, acc_far, acc_add, s), "Taylor forces");

@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(128) k_taylor_forces(const int* __restrict__ o
 // (Ogita, Rump & Oishi 2005), which carry about 48 significant bits on the
 // FP32 pipe.  The _rn intrinsics keep the compiler from fusing a product into
 // a following sum, which would break the exactness of the transformations.
-struct dfl {
+struct __align__(8) dfl {
     float h, l;
 };
 
@@ -541,14 +541,6 @@ __global__ void k_multipoles_df(const int* __restrict__ off, const float4* __res
     }
 }
 
-// FP64 Taylors [C][nt] -> double-float pairs, same layout.
-__global__ void k_taylors_to_df(const double* __restrict__ T, long long total, dfl* __restrict__ Td)
-{
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x)
-        Td[e] = df_from(T[e]);
-}
-
 // The Taylor evaluation of k_taylor_forces in double-float: cell units, the
 // particle's stored FP32 offsets as the float multipliers of the Horner steps.
 // Each thread evaluates two particles at once (binned slots i and i + half):
@@ -672,51 +664,134 @@ __global__ void k_far_reduce(const double* __restrict__ M, int C, int nt, int nr
     }
 }
 
-// out = sum over cells of M[c][term], one block, fixed order.
-__global__ void k_far_sum_term(const double* __restrict__ M, int C, int nt, int term, double* __restrict__ out)
+// Partial sums over cells of M[c][term], one per block (gridDim.x of them),
+// each in a fixed order; the rebuild adds the partials in order.
+constexpr int kSumBlocks = 64;
+__global__ void k_far_sum_term(const double* __restrict__ M, int C, int nt, int term, double* __restrict__ partial)
 {
-    __shared__ double part[1024];
+    __shared__ double part[256];
     double acc = 0.0;
-    for (int c = threadIdx.x; c < C; c += blockDim.x) acc += M[(size_t)c * nt + term];
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x)
+        acc += M[(size_t)c * nt + term];
     part[threadIdx.x] = acc;
     __syncthreads();
     for (int h = blockDim.x / 2; h > 0; h >>= 1) {
         if ((int)threadIdx.x < h) part[threadIdx.x] += part[threadIdx.x + h];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *out = part[0];
+    if (threadIdx.x == 0) partial[blockIdx.x] = part[0];
 }
 
-// Complete Taylors of every cell from the reduced ones (the rebuild program
-// in shared memory; one thread per cell).  lap is the Laplacian of the
-// series (4 pi N w^2 / V in cell units), t0_per_s002 * (*s002) the constant
-// of T^0.
-__global__ void k_far_rebuild(const double* __restrict__ Tr, int C, int nt, int nr, const int4* __restrict__ ops,
+// Complete Taylors of every cell from the reduced ones: one warp per cell,
+// the rebuild program in shared memory and the cell's Taylors staged in a
+// per-warp shared buffer.  The warp reads a cell's reduced Taylors in one
+// coalesced pass (fetching the next cell's into registers while it rebuilds
+// the current one) and drops each into its place in the complete basis: the
+// terms with z index 0 and 1 are the reduced ones.  The rest of the program
+// is ordered by the z index of its destination; ops of one z level are
+// independent (their sources have z - 2), so the lanes share a level and
+// sync between levels.  lap is the Laplacian of the series (4 pi N w^2 / V in
+// cell units); t0_per_s002 times the sum of the partials is the constant of
+// T^0.  F64 runs the recursion in FP64 and writes T; DF splits the reduced
+// Taylors into double-float pairs once and runs the recursion on the FP32
+// pipe, writing Tdf: the forces of the double-float kernels do not depend on
+// whether T is asked for too.
+constexpr int kRebuildWarps = 8;
+constexpr int kRebuildFetch = (kMaxFarOrder + 1) * (kMaxFarOrder + 1) / 32 + 1;  // reduced terms per lane
+template <bool F64, bool DF>
+__global__ void k_far_rebuild(const double* __restrict__ Tr, int C, int p, int nt, int nr, const int4* __restrict__ ops,
                               const double2* __restrict__ opf, int t002, double lap, double t0_per_s002,
-                              const double* __restrict__ s002, double* __restrict__ T)
+                              const double* __restrict__ partial, double* __restrict__ T, dfl* __restrict__ Tdf)
 {
-    extern __shared__ int4 prog[];  // [nt] ops, then [nt] factors
-    double2* fs = reinterpret_cast<double2*>(prog + nt);
+    extern __shared__ int4 smem_rb[];
+    int4* prog = smem_rb;                                     // [nt] ops
+    double2* fs = reinterpret_cast<double2*>(prog + nt);      // [nt] factors
+    float4* fd = reinterpret_cast<float4*>(fs + nt);          // [nt] factors as double-float pairs
+    int* level = reinterpret_cast<int*>(fd + nt);             // [16] level starts
+    int* rmap = level + 16;                                   // [nr] place of each reduced term
+    double* stage = reinterpret_cast<double*>(rmap + ((nr + 3) & ~3));  // per warp: [nt] FP64, [nt] pairs
     for (int i = threadIdx.x; i < nt; i += blockDim.x) {
-        prog[i] = ops[i];
-        fs[i] = opf[i];
+        const int4 op = ops[i];
+        prog[i] = op;
+        if (op.y >= 0) rmap[op.y] = op.x;
+        const double2 f = opf[i];
+        fs[i] = f;
+        const dfl x = df_from(f.x), y = df_from(f.y);
+        fd[i] = make_float4(x.h, x.l, y.h, y.l);
     }
     __syncthreads();
-    const double t0 = (t002 >= 0 && s002) ? t0_per_s002 * (*s002) : 0.0;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
-        const double* tr = Tr + (size_t)c * nr;
-        double* t = T + (size_t)c * nt;
-        for (int i = 0; i < nt; ++i) {
-            const int4 op = prog[i];
-            if (op.y >= 0) {
-                t[op.x] = tr[op.y];
-            } else {
-                double v = -fs[i].x * t[op.z] - fs[i].y * t[op.w];
-                if (op.x == t002) v += 0.5 * lap;  // m = 0: (2)(1) T^{002} = lap - ...
-                t[op.x] = v;
+    if (threadIdx.x == 0) {
+        int i = 0;
+        for (int c = 0; c <= p; ++c) {
+            level[c] = i;
+            while (i < nt) {
+                int a, b, cz;
+                decode_term(prog[i].x, p, a, b, cz);
+                if (cz != c) break;
+                ++i;
             }
         }
-        t[0] += t0;
+        level[p + 1] = nt;
+    }
+    __syncthreads();
+    double t0 = 0.0;
+    if (t002 >= 0 && partial)
+        for (int q = 0; q < kSumBlocks; ++q) t0 += partial[q];
+    t0 *= t0_per_s002;
+    const dfl t0d = df_from(t0), lapd = df_from(0.5 * lap);
+    const int lane = threadIdx.x & 31;
+    double* t = stage + (size_t)(threadIdx.x >> 5) * ((F64 ? 1 : 0) + (DF ? 1 : 0)) * nt;
+    dfl* td = reinterpret_cast<dfl*>(t + (F64 ? nt : 0));
+    int rdst[kRebuildFetch];
+#pragma unroll
+    for (int k = 0; k < kRebuildFetch; ++k) rdst[k] = lane + 32 * k < nr ? rmap[lane + 32 * k] : -1;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    double nx[kRebuildFetch];
+    int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+#pragma unroll
+    for (int k = 0; k < kRebuildFetch; ++k) {
+        const int i = lane + 32 * k;
+        nx[k] = (c < C && i < nr) ? Tr[(size_t)c * nr + i] : 0.0;
+    }
+    for (; c < C; c += warps) {
+#pragma unroll
+        for (int k = 0; k < kRebuildFetch; ++k) {
+            const int d = rdst[k];
+            if (d >= 0) {
+                if (F64) t[d] = d == 0 ? nx[k] + t0 : nx[k];
+                if (DF) td[d] = d == 0 ? df_add(df_from(nx[k]), t0d) : df_from(nx[k]);
+            }
+        }
+        __syncwarp();
+        const int cn = c + warps;
+#pragma unroll
+        for (int k = 0; k < kRebuildFetch; ++k) {
+            const int i = lane + 32 * k;
+            nx[k] = (cn < C && i < nr) ? Tr[(size_t)cn * nr + i] : 0.0;
+        }
+        for (int L = 2; L <= p; ++L) {
+            for (int i = level[L] + lane; i < level[L + 1]; i += 32) {
+                const int4 op = prog[i];
+                if (F64) {
+                    double v = -fs[i].x * t[op.z] - fs[i].y * t[op.w];
+                    if (op.x == t002) v += 0.5 * lap;  // m = 0: (2)(1) T^{002} = lap - ...
+                    t[op.x] = v;
+                }
+                if (DF) {
+                    const float4 f = fd[i];
+                    dfl v = df_fma(dfl{f.x, f.y}, td[op.z], df_mul(dfl{f.z, f.w}, td[op.w]));
+                    v = dfl{-v.h, -v.l};
+                    if (op.x == t002) v = df_add(v, lapd);
+                    td[op.x] = v;
+                }
+            }
+            __syncwarp();
+        }
+        if (F64)
+            for (int i = lane; i < nt; i += 32) T[(size_t)c * nt + i] = t[i];
+        if (DF)
+            for (int i = lane; i < nt; i += 32) Tdf[(size_t)c * nt + i] = td[i];
+        __syncwarp();  // the buffers are reused by the next cell
     }
 }
 
@@ -985,18 +1060,10 @@ cudaError_t launch_multipoles_df(const int* off, const float4* rel, int C, int p
     return cudaGetLastError();
 }
 
-cudaError_t launch_taylor_forces_df(int p, const int* off, const float4* rel, const double* T, void* Tdf, int N,
-                                    int C, double scale, double* acc_far, float* acc_add, cudaStream_t s)
+cudaError_t launch_taylor_forces_df(int p, const int* off, const float4* rel, const void* Tdf, int N, int C,
+                                    double scale, double* acc_far, float* acc_add, cudaStream_t s)
 {
-    const long long total = (long long)C * far_terms(p);
-    long long blocks = (total + 255) / 256;
-    const long long cap = (long long)device_sms() * 16;
-    if (blocks > cap) blocks = cap;
-    dfl* Td = static_cast<dfl*>(Tdf);
-    k_taylors_to_df<<<(int)blocks, 256, 0, s>>>(T, total, Td);
-    count_launches(1);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    const dfl* Td = static_cast<const dfl*>(Tdf);
     const int need = ((N + 1) / 2 + 127) / 128;
     const int grid = need < device_sms() * 16 ? need : device_sms() * 16;
     switch (p) {
@@ -1048,23 +1115,44 @@ cudaError_t launch_far_reduce(const double* M, int C, int nt, int nr, const int*
     return cudaGetLastError();
 }
 
-cudaError_t launch_far_sum_term(const double* M, int C, int nt, int term, double* out, cudaStream_t s)
+cudaError_t launch_far_sum_term(const double* M, int C, int nt, int term, double* partial, cudaStream_t s)
 {
-    k_far_sum_term<<<1, 1024, 0, s>>>(M, C, nt, term, out);
+    k_far_sum_term<<<kSumBlocks, 256, 0, s>>>(M, C, nt, term, partial);
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_far_rebuild(const double* Tr, int C, int nt, int nr, const int4* ops, const double2* opf, int t002,
-                               double lap, double t0_per_s002, const double* s002, double* T, cudaStream_t s)
+int far_sum_partials() { return kSumBlocks; }
+
+cudaError_t launch_far_rebuild(const double* Tr, int C, int p, int nt, int nr, const int4* ops, const double2* opf,
+                               int t002, double lap, double t0_per_s002, const double* partial, double* T, void* Tdf,
+                               cudaStream_t s)
 {
-    const size_t smem = (size_t)nt * (sizeof(int4) + sizeof(double2));
-    cudaError_t e = ensure_smem((const void*)k_far_rebuild, (int)smem);
+    if (!T && !Tdf) return cudaSuccess;
+    const void* fn = T && Tdf ? (const void*)k_far_rebuild<true, true>
+                     : T      ? (const void*)k_far_rebuild<true, false>
+                              : (const void*)k_far_rebuild<false, true>;
+    const int slots = (T ? 1 : 0) + (Tdf ? 1 : 0);
+    const size_t smem = (size_t)nt * (sizeof(int4) + sizeof(double2) + sizeof(float4)) +
+                        (16 + (size_t)((nr + 3) & ~3)) * sizeof(int) + (size_t)kRebuildWarps * slots * nt * sizeof(double);
+    cudaError_t e = ensure_smem(fn, (int)smem);
     if (e != cudaSuccess) return e;
-    int blocks = (C + 127) / 128;
-    const int cap = device_sms() * 16;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kRebuildWarps * 32, smem);
+    if (e != cudaSuccess) return e;
+    long long blocks = ((long long)C + kRebuildWarps - 1) / kRebuildWarps;  // one warp per cell
+    const long long cap = (long long)device_sms() * (per_sm > 0 ? per_sm : 1);  // one wave, all resident
     if (blocks > cap) blocks = cap;
-    k_far_rebuild<<<blocks, 128, smem, s>>>(Tr, C, nt, nr, ops, opf, t002, lap, t0_per_s002, s002, T);
+    dfl* td = static_cast<dfl*>(Tdf);
+    if (T && Tdf)
+        k_far_rebuild<true, true><<<(int)blocks, kRebuildWarps * 32, smem, s>>>(Tr, C, p, nt, nr, ops, opf, t002, lap,
+                                                                              t0_per_s002, partial, T, td);
+    else if (T)
+        k_far_rebuild<true, false><<<(int)blocks, kRebuildWarps * 32, smem, s>>>(Tr, C, p, nt, nr, ops, opf, t002, lap,
+                                                                               t0_per_s002, partial, T, td);
+    else
+        k_far_rebuild<false, true><<<(int)blocks, kRebuildWarps * 32, smem, s>>>(Tr, C, p, nt, nr, ops, opf, t002, lap,
+                                                                               t0_per_s002, partial, T, td);
     count_launches(1);
     return cudaGetLastError();
 }

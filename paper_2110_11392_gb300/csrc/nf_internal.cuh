@@ -130,9 +130,13 @@ struct FarTables {
 FarTables far_tables(int p, double w);
 cudaError_t launch_far_reduce(const double* M, int C, int nt, int nr, const int* seg, const int* kidx,
                               const double* coef, double* Mr, cudaStream_t s);
-cudaError_t launch_far_sum_term(const double* M, int C, int nt, int term, double* out, cudaStream_t s);
-cudaError_t launch_far_rebuild(const double* Tr, int C, int nt, int nr, const int4* ops, const double2* opf, int t002,
-                               double lap, double t0_per_s002, const double* s002, double* T, cudaStream_t s);
+// per-block partial sums over cells of M[c][term] (far_sum_partials() of them)
+cudaError_t launch_far_sum_term(const double* M, int C, int nt, int term, double* partial, cudaStream_t s);
+int far_sum_partials();
+// complete Taylors T [C][nt] (and, with Tdf, their double-float pairs) from the reduced ones
+cudaError_t launch_far_rebuild(const double* Tr, int C, int p, int nt, int nr, const int4* ops, const double2* opf,
+                               int t002, double lap, double t0_per_s002, const double* partial, double* T, void* Tdf,
+                               cudaStream_t s);
 // cuFFT work-area bytes to reserve for the forward and inverse transforms of nt fields on K^3
 size_t far_fft_work_bytes(int K, int nt);
 // forward: real cell-major [K^3][nt] -> complex term-major [nt][K][K][K/2+1]; inverse the reverse
@@ -144,10 +148,10 @@ cudaError_t launch_deriv_real(int K, int R, int p, double box, double alpha, int
 cudaError_t launch_deriv_recip(int K, int p, double box, double alpha, int hmax, const double2* Dh, double* Dr,
                                cudaStream_t s);
 cudaError_t launch_unscale_taylors(const double* Tc, int C, int p, double w, double* T, cudaStream_t s);
-// double-float forms of the per-particle kernels (cell units); Tdf holds C * nt pairs of floats
+// double-float forms of the per-particle kernels (cell units); Tdf holds C * nt pairs of floats (from the rebuild)
 cudaError_t launch_multipoles_df(const int* off, const float4* rel, int C, int p, double* M, cudaStream_t s);
-cudaError_t launch_taylor_forces_df(int p, const int* off, const float4* rel, const double* T, void* Tdf, int N,
-                                    int C, double scale, double* acc_far, float* acc_add, cudaStream_t s);
+cudaError_t launch_taylor_forces_df(int p, const int* off, const float4* rel, const void* Tdf, int N, int C,
+                                    double scale, double* acc_far, float* acc_add, cudaStream_t s);
 // Th[n][q] for nout output fields (the reduced Taylors) from the pair table
 cudaError_t launch_far_contract(int K, int nout, const int* seg, const FarPair* pairs, const double* Dr,
                                 const double2* Mh, double2* Th, cudaStream_t s);

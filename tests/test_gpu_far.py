@@ -245,11 +245,14 @@ def test_the_two_arithmetics_agree():
         a64, t64 = ff(pos, want_taylors=True)
         _lib.nf_far_set_arith(_lib.NF_FAR_DOUBLE_FLOAT)
         adf, tdf = ff(pos, want_taylors=True)
+        adf_only = ff(pos)  # forces alone: the Taylors are rebuilt in double-float only
         torch.cuda.synchronize()
     finally:
         _lib.nf_far_set_arith(before)
     scale = a64.abs().max().item()
     assert (a64 - adf).abs().max().item() < 1e-12 * scale
+    # the double-float forces do not depend on whether the FP64 Taylors are asked for
+    assert torch.equal(adf_only, adf)
     tscale = t64.abs().amax(dim=0) + 1e-300
     assert ((t64 - tdf).abs().amax(dim=0) / tscale).max().item() < 1e-12
     with pytest.raises(_lib.NFError):
