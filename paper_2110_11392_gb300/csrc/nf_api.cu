@@ -747,14 +747,15 @@ DerivLayout deriv_layout(int K, int p)
 }
 
 struct FarLayout {
-    size_t o_M = 0, o_Mr = 0, o_Mh = 0, o_Th = 0, o_Tdf = 0, o_s002 = 0, o_work = 0, work = 0, total = 0;
+    size_t o_M = 0, o_Mr = 0, o_Mh = 0, o_Th = 0, o_Tdf = 0, o_m002 = 0, o_s002 = 0, o_work = 0, work = 0, total = 0;
 };
 
 // The far-field regions follow the binning plan's; in debug mode each is
 // followed by a guard block like the plan's regions (appended to guards).
 // M: complete multipoles, later the rebuilt Taylors [C][nt]; Mr: reduced
 // multipoles, later the reduced Taylors [C][nr]; Mh, Th: spectra [nr][nq];
-// Tdf: double-float Taylor pairs [C][nt]; s002: one double.
+// Tdf: double-float Taylor pairs [C][nt]; m002: each cell's (0,0,2) multipole
+// [C]; s002: partial sums of the (0,0,2) multipoles.
 FarLayout far_layout(const Plan& pl, int K, int p, std::vector<size_t>* guards = nullptr)
 {
     FarLayout F;
@@ -776,6 +777,7 @@ FarLayout far_layout(const Plan& pl, int K, int p, std::vector<size_t>* guards =
     F.o_Mh = take(spec);
     F.o_Th = take(spec);
     F.o_Tdf = take(8 * (size_t)nt * cells);
+    F.o_m002 = take(8 * cells);
     F.o_s002 = take(8 * (size_t)far_sum_partials());
     // the derivatives' transform (nt fields) and the far call's (nr fields) share the area
     const size_t w1 = far_fft_work_bytes(K, nt), w2 = far_fft_work_bytes(K, nr);
@@ -1014,23 +1016,29 @@ int run_far(const FarCall& fc, const float* pos, int64_t N, double box, int K, i
     double2* Th = at<double2>(ws, F.o_Th);
     // cell units throughout: displacements / w (the stored offsets), T'^n = T^n w^{|n|}
     const bool dfl = g_far_arith.load() == NF_FAR_DOUBLE_FLOAT;
-    if (dfl)
-        NF_CUDA(launch_multipoles_df(off, rel, C, p, M, s), "multipoles (double-float)");
-    else
-        NF_CUDA(launch_multipoles(off, rel, C, 1.0, p, M, s), "multipoles");
-    NF_CUDA(mark(2), "profile");
     // reduced basis: fold the multipoles, convolve (p+1)^2 fields, rebuild the complete Taylors
     const double w = box / K, V = box * box * box;
     double* Mr = at<double>(ws, F.o_Mr);
     double* s002 = at<double>(ws, F.o_s002);
     char* dv = static_cast<char*>(const_cast<void*>(derivs));
     auto dat = [&](size_t off) { return static_cast<void*>(dv + off); };
-    NF_CUDA(launch_far_reduce(M, C, L.nt, L.nr, static_cast<const int*>(dat(L.o_rseg)),
-                              static_cast<const int*>(dat(L.o_rk)), static_cast<const double*>(dat(L.o_rcoef)), Mr,
-                              s),
-            "multipole fold");
+    const int* rseg = static_cast<const int*>(dat(L.o_rseg));
+    const int* rk = static_cast<const int*>(dat(L.o_rk));
+    const double* rcoef = static_cast<const double*>(dat(L.o_rcoef));
     const int i002 = p >= 2 ? 2 : -1;  // (0,0,2): the third term of the complete basis (a, then b, then c)
-    if (i002 >= 0) NF_CUDA(launch_far_sum_term(M, C, L.nt, i002, s002, s), "sum of the (0,0,2) multipoles");
+    if (dfl) {
+        // the fold runs inside the multipole kernel; each cell's (0,0,2) term is kept for its sum
+        double* m002 = at<double>(ws, F.o_m002);
+        NF_CUDA(launch_multipoles_red_df(off, rel, C, p, rseg, rk, rcoef, L.nnz, Mr, m002, s),
+                "multipoles (double-float)");
+        NF_CUDA(mark(2), "profile");
+        if (i002 >= 0) NF_CUDA(launch_far_sum_term(m002, C, 1, 0, s002, s), "sum of the (0,0,2) multipoles");
+    } else {
+        NF_CUDA(launch_multipoles(off, rel, C, 1.0, p, M, s), "multipoles");
+        NF_CUDA(mark(2), "profile");
+        NF_CUDA(launch_far_reduce(M, C, L.nt, L.nr, rseg, rk, rcoef, Mr, s), "multipole fold");
+        if (i002 >= 0) NF_CUDA(launch_far_sum_term(M, C, L.nt, i002, s002, s), "sum of the (0,0,2) multipoles");
+    }
     cudaError_t e = launch_far_fft(K, L.nr, true, Mr, Mh, at<void>(ws, F.o_work), F.work, s);
     if (e != cudaSuccess) return fft_fail(e, "multipoles (forward FFT)");
     NF_CUDA(launch_far_contract(K, L.nr, static_cast<const int*>(dat(L.o_seg)),

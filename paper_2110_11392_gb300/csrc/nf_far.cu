@@ -61,7 +61,7 @@ namespace {
 
 constexpr int kDerivThreads = 256;
 
-__host__ __device__ inline int far_terms(int p) { return (p + 3) * (p + 2) * (p + 1) / 6; }
+__host__ __device__ constexpr int far_terms(int p) { return (p + 3) * (p + 2) * (p + 1) / 6; }
 
 // (a, b, c) of term t in the complete-basis order of order p
 __device__ inline void decode_term(int t, int p, int& a, int& b, int& c)
@@ -457,6 +457,15 @@ __device__ __forceinline__ dfl df_mul(dfl a, dfl b)
     return df_fast(p, e);
 }
 
+// a * z for a float z
+__device__ __forceinline__ dfl df_mul_f(dfl a, float z)
+{
+    const float p = __fmul_rn(a.h, z);
+    float e = __fmaf_rn(a.h, z, -p);
+    e = __fmaf_rn(a.l, z, e);
+    return df_fast(p, e);
+}
+
 __device__ __forceinline__ dfl df_add(dfl a, dfl b)
 {
     const dfl s = df_two_sum(a.h, b.h);
@@ -469,75 +478,100 @@ __device__ __forceinline__ dfl df_from(double v)
     return {h, __double2float_rn(v - (double)h)};
 }
 
-// Cell multipoles in cell units, double-float: the structure of k_multipoles
-// (one block per cell, one thread per term, 64 particles at a time with
-// their powers and x^a y^b products in shared memory), each term accumulated
-// as a double-float; the result is written as FP64.
-__global__ void k_multipoles_df(const int* __restrict__ off, const float4* __restrict__ rel, int C, int p,
-                                int nterms, double* __restrict__ M)
+// Cell multipoles in cell units, double-float, folded onto the reduced basis
+// in the same kernel.  One block per cell and one thread per complete term:
+// kMpChunk particles at a time the block builds their powers x^e, y^e, z^e
+// (one thread per particle and axis) and the products x^a y^b (one per
+// particle and (a, b) pair) in shared memory, and each term thread adds
+// (x^a y^b) z^c to two double-float partial sums.  The cell's complete
+// multipoles then go through the fold of k_far_reduce, Mr^r = sum_k
+// f_{r,k} M^k, with its coefficients as double-float pairs, and are written
+// as FP64, with the cell's (0,0,2) term for its sum over cells.  (The
+// error-free transformations stay on scalar FP32 instructions: in probes the
+// packed .f32x2 form of the same sequence did not always keep the product's
+// rounding error, depending on the surrounding code.)
+constexpr int kMpChunk = 32;
+template <int P>
+__global__ void k_multipoles_red_df(const int* __restrict__ off, const float4* __restrict__ rel, int C,
+                                    const int* __restrict__ rseg, const int* __restrict__ rk,
+                                    const double* __restrict__ rcoef, double* __restrict__ Mr,
+                                    double* __restrict__ m002)
 {
-    constexpr int kChunk = 64;
-    extern __shared__ dfl pwd[];  // powers [3][kChunk][p + 1], products [kChunk][nab], (a, b) table [nab]
-    const int P1 = p + 1;
-    const int nab = (p + 1) * (p + 2) / 2;
-    dfl* XY = pwd + (size_t)3 * kChunk * P1;
-    int2* abt = reinterpret_cast<int2*>(XY + (size_t)kChunk * nab);
-    for (int k = threadIdx.x; k < nab; k += blockDim.x) {
+    constexpr int P1 = P + 1, NAB = P1 * (P + 2) / 2, NT = far_terms(P), NR = P1 * P1;
+    extern __shared__ dfl smem_mp[];
+    const int nnz = rseg[NR];
+    dfl* pw = smem_mp;                                  // powers [3][kMpChunk][P1]
+    dfl* XY = pw + 3 * kMpChunk * P1;                   // products [kMpChunk][NAB]
+    dfl* Ms = XY + kMpChunk * NAB;                      // the cell's complete multipoles [NT]
+    dfl* cf = Ms + NT;                                  // fold coefficients [nnz]
+    int2* abt = reinterpret_cast<int2*>(cf + nnz);      // (a, b) of each product [NAB]
+    int* ck = reinterpret_cast<int*>(abt + NAB);        // complete term of each coefficient [nnz]
+    int* sg = ck + nnz;                                 // segment of each reduced term [NR + 1]
+    for (int i = threadIdx.x; i < nnz; i += blockDim.x) {
+        cf[i] = df_from(rcoef[i]);
+        ck[i] = rk[i];
+    }
+    for (int i = threadIdx.x; i <= NR; i += blockDim.x) sg[i] = rseg[i];
+    for (int k = threadIdx.x; k < NAB; k += blockDim.x) {
         int aa = 0, kk = k;
-        while (kk > p - aa) {
-            kk -= p - aa + 1;
+        while (kk > P - aa) {
+            kk -= P - aa + 1;
             ++aa;
         }
         abt[k] = make_int2(aa, kk);
     }
     int a = 0, b = 0, c = 0;
     const int t = threadIdx.x;
-    if (t < nterms) decode_term(t, p, a, b, c);
-    const int ab = a * (p + 1) - a * (a - 1) / 2 + b;
+    if (t < NT) decode_term(t, P, a, b, c);
+    const int ab = a * P1 - a * (a - 1) / 2 + b;
+    const dfl* Z = pw + 2 * kMpChunk * P1;
     for (int cell = blockIdx.x; cell < C; cell += gridDim.x) {
         const int s0 = off[cell], s1 = off[cell + 1];
-        // four independent partial sums: each double-float update is a chain of
-        // dependent FP32 operations, so one accumulator would wait on latency
-        dfl acc[4] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
-        for (int q0 = s0; q0 < s1; q0 += kChunk) {
-            const int nq = min(kChunk, s1 - q0);
-            __syncthreads();
+        // two independent partial sums: a double-float update is a chain of
+        // dependent FP32 operations
+        dfl acc0 = {0.0f, 0.0f}, acc1 = {0.0f, 0.0f};
+        for (int q0 = s0; q0 < s1; q0 += kMpChunk) {
+            const int nq = min(kMpChunk, s1 - q0);
+            __syncthreads();  // the previous chunk (or the tables) are in place and read
             for (int i = threadIdx.x; i < 3 * nq; i += blockDim.x) {
                 const int q = i / 3, d = i - 3 * q;
                 const float4 r4 = rel[q0 + q];
                 const float x = d == 0 ? r4.x : (d == 1 ? r4.y : r4.z);
-                dfl* row = pwd + ((size_t)d * kChunk + q) * P1;
-                dfl v = {1.0f, 0.0f};
-                row[0] = v;
-                for (int e = 1; e <= p; ++e) {
-                    v = df_fma_f(v, x, dfl{0.0f, 0.0f});
+                dfl* row = pw + (d * kMpChunk + q) * P1;
+                dfl v = {x, 0.0f};
+                row[0] = dfl{1.0f, 0.0f};
+                if (P >= 1) row[1] = v;
+#pragma unroll
+                for (int e = 2; e <= P; ++e) {
+                    v = df_mul_f(v, x);
                     row[e] = v;
                 }
             }
             __syncthreads();
-            for (int i = threadIdx.x; i < nq * nab; i += blockDim.x) {
-                const int q = i / nab, k = i - q * nab;
+            for (int i = threadIdx.x; i < nq * NAB; i += blockDim.x) {
+                const int q = i / NAB, k = i - q * NAB;
                 const int2 ab2 = abt[k];
-                XY[(size_t)q * nab + k] = df_mul(pwd[(size_t)q * P1 + ab2.x], pwd[((size_t)kChunk + q) * P1 + ab2.y]);
+                XY[q * NAB + k] = df_mul(pw[q * P1 + ab2.x], pw[(kMpChunk + q) * P1 + ab2.y]);
             }
             __syncthreads();
-            if (t < nterms) {
-                const dfl* Z = pwd + (size_t)2 * kChunk * P1;
+            if (t < NT) {
                 int q = 0;
-                for (; q + 4 <= nq; q += 4) {
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        acc[u] = df_fma(XY[(size_t)(q + u) * nab + ab], Z[(q + u) * P1 + c], acc[u]);
+                for (; q + 2 <= nq; q += 2) {
+                    acc0 = df_fma(XY[q * NAB + ab], Z[q * P1 + c], acc0);
+                    acc1 = df_fma(XY[(q + 1) * NAB + ab], Z[(q + 1) * P1 + c], acc1);
                 }
-                for (; q < nq; ++q) acc[0] = df_fma(XY[(size_t)q * nab + ab], Z[q * P1 + c], acc[0]);
+                if (q < nq) acc0 = df_fma(XY[q * NAB + ab], Z[q * P1 + c], acc0);
             }
         }
-        if (t < nterms) {
-            // combine the partial sums in double-float; one conversion to FP64 (the FP64
-            // pipe is 1/64 of the FP32 rate, so it is kept out of the per-term work)
-            const dfl m = df_add(df_add(acc[0], acc[1]), df_add(acc[2], acc[3]));
-            M[(size_t)cell * nterms + t] = (double)m.h + (double)m.l;
+        if (t < NT) Ms[t] = df_add(acc0, acc1);
+        __syncthreads();
+        for (int r = threadIdx.x; r < NR; r += blockDim.x) {
+            dfl m = {0.0f, 0.0f};
+            for (int i = sg[r]; i < sg[r + 1]; ++i) m = df_fma(cf[i], Ms[ck[i]], m);
+            Mr[(size_t)cell * NR + r] = (double)m.h + (double)m.l;
         }
+        if (P >= 2 && t == 2) m002[cell] = (double)Ms[2].h + (double)Ms[2].l;  // term 2 is (0,0,2)
+        __syncthreads();  // Ms is rewritten for the next cell
     }
 }
 
@@ -1046,16 +1080,40 @@ cudaError_t launch_deriv_recip(int K, int p, double box, double alpha, int hmax,
     return cudaGetLastError();
 }
 
-cudaError_t launch_multipoles_df(const int* off, const float4* rel, int C, int p, double* M, cudaStream_t s)
+cudaError_t launch_multipoles_red_df(const int* off, const float4* rel, int C, int p, const int* rseg,
+                                     const int* rk, const double* rcoef, long long nnz, double* Mr, double* m002,
+                                     cudaStream_t s)
 {
-    const int nterms = far_terms(p);
-    const int threads = ((nterms + 31) / 32) * 32;
-    const size_t nab = (size_t)(p + 1) * (p + 2) / 2;
-    const size_t smem = ((size_t)3 * 64 * (p + 1) + (size_t)64 * nab) * sizeof(dfl) + nab * sizeof(int2);
-    cudaError_t e = ensure_smem((const void*)k_multipoles_df, (int)smem);
-    if (e != cudaSuccess) return e;
+    const int nt = far_terms(p), nr = (p + 1) * (p + 1), nab = (p + 1) * (p + 2) / 2;
+    const int threads = ((nt + 31) / 32) * 32;
+    const size_t smem = ((size_t)3 * kMpChunk * (p + 1) + (size_t)kMpChunk * nab + nt + nnz) * sizeof(dfl) +
+                        (size_t)nab * sizeof(int2) + ((size_t)nnz + nr + 1) * sizeof(int);
     const int grid = C < device_sms() * 32 ? C : device_sms() * 32;
-    k_multipoles_df<<<grid, threads, smem, s>>>(off, rel, C, p, nterms, M);
+    switch (p) {
+#define NF_MP_RED_CASE(P)                                                                              \
+    case P: {                                                                                          \
+        cudaError_t e = ensure_smem((const void*)k_multipoles_red_df<P>, (int)smem);                   \
+        if (e != cudaSuccess) return e;                                                                \
+        k_multipoles_red_df<P><<<grid, threads, smem, s>>>(off, rel, C, rseg, rk, rcoef, Mr, m002);    \
+        break;                                                                                         \
+    }
+        NF_MP_RED_CASE(0)
+        NF_MP_RED_CASE(1)
+        NF_MP_RED_CASE(2)
+        NF_MP_RED_CASE(3)
+        NF_MP_RED_CASE(4)
+        NF_MP_RED_CASE(5)
+        NF_MP_RED_CASE(6)
+        NF_MP_RED_CASE(7)
+        NF_MP_RED_CASE(8)
+        NF_MP_RED_CASE(9)
+        NF_MP_RED_CASE(10)
+        NF_MP_RED_CASE(11)
+        NF_MP_RED_CASE(12)
+#undef NF_MP_RED_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
     count_launches(1);
     return cudaGetLastError();
 }

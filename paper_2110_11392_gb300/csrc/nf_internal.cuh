@@ -149,7 +149,11 @@ cudaError_t launch_deriv_recip(int K, int p, double box, double alpha, int hmax,
                                cudaStream_t s);
 cudaError_t launch_unscale_taylors(const double* Tc, int C, int p, double w, double* T, cudaStream_t s);
 // double-float forms of the per-particle kernels (cell units); Tdf holds C * nt pairs of floats (from the rebuild)
-cudaError_t launch_multipoles_df(const int* off, const float4* rel, int C, int p, double* M, cudaStream_t s);
+// reduced multipoles Mr [C][(p+1)^2] (the fold of the double-float complete ones) and
+// each cell's (0,0,2) multipole m002 [C]; rseg/rk/rcoef: the fold table, nnz entries
+cudaError_t launch_multipoles_red_df(const int* off, const float4* rel, int C, int p, const int* rseg,
+                                     const int* rk, const double* rcoef, long long nnz, double* Mr, double* m002,
+                                     cudaStream_t s);
 cudaError_t launch_taylor_forces_df(int p, const int* off, const float4* rel, const void* Tdf, int N, int C,
                                     double scale, double* acc_far, float* acc_add, cudaStream_t s);
 // Th[n][q] for nout output fields (the reduced Taylors) from the pair table
