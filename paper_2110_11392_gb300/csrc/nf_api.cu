@@ -692,6 +692,7 @@ struct DerivLayout {
     int nt = 0, nr = 0;
     long long npairs = 0, nnz = 0;
     size_t o_seg = 0, o_pairs = 0, o_dh = 0, o_rseg = 0, o_rk = 0, o_rcoef = 0, o_ops = 0, o_opf = 0, total = 0;
+    size_t o_drdf = 0, o_pcdf = 0, o_tw = 0;  // double-float transform path (power-of-two K) only
 };
 
 // K^3 and, for the cuFFT plans' 32-bit element offsets, n_t K^3 below 2^31
@@ -742,6 +743,11 @@ DerivLayout deriv_layout(int K, int p)
     L.o_ops = take(sizeof(int4) * (size_t)L.nt);
     L.o_opf = take(sizeof(double2) * (size_t)L.nt);
     L.o_dh = take(8 * (size_t)L.nt * K * K * (K / 2 + 1));  // one real per (term, frequency)
+    if (far_df_fft(K)) {
+        L.o_drdf = take(8 * (size_t)L.nt * K * K * (K / 2 + 1));  // the same as double-float pairs
+        L.o_pcdf = take(8 * (size_t)L.npairs);
+        L.o_tw = take(16 * (size_t)(K / 2));
+    }
     L.total = o;
     return L;
 }
@@ -907,6 +913,14 @@ int nf_derivatives(int K, int R, int p, double box, void* derivs, size_t derivs_
         NF_CUDA(up(L.o_rcoef, tb.red_coef.data(), 8 * tb.red_coef.size()), "far tables");
         NF_CUDA(up(L.o_ops, tb.ops.data(), sizeof(int4) * tb.ops.size()), "far tables");
         NF_CUDA(up(L.o_opf, tb.opf.data(), sizeof(double2) * tb.opf.size()), "far tables");
+        if (L.o_drdf) {
+            const std::vector<float4> tw = far_twiddles(K);
+            NF_CUDA(up(L.o_pcdf, tb.pair_cdf.data(), sizeof(float2) * tb.pair_cdf.size()), "far tables");
+            NF_CUDA(up(L.o_tw, tw.data(), sizeof(float4) * tw.size()), "far tables");
+            NF_CUDA(launch_to_df(at<double>(derivs, L.o_dh), (long long)L.nt * K * K * (K / 2 + 1),
+                                 at<void>(derivs, L.o_drdf), s),
+                    "derivatives (double-float copy)");
+        }
     }
     DerivHeader h;
     std::memset(&h, 0, sizeof h);
@@ -930,6 +944,9 @@ int nf_derivatives(int K, int R, int p, double box, void* derivs, size_t derivs_
     h.o_rcoef = L.o_rcoef;
     h.o_ops = L.o_ops;
     h.o_opf = L.o_opf;
+    h.o_drdf = L.o_drdf;
+    h.o_pcdf = L.o_pcdf;
+    h.o_tw = L.o_tw;
     h.total = L.total;
     NF_CUDA(launch_deriv_header(h, derivs, s), "derivatives header");
     {
@@ -1026,10 +1043,13 @@ int run_far(const FarCall& fc, const float* pos, int64_t N, double box, int K, i
     const int* rk = static_cast<const int*>(dat(L.o_rk));
     const double* rcoef = static_cast<const double*>(dat(L.o_rcoef));
     const int i002 = p >= 2 ? 2 : -1;  // (0,0,2): the third term of the complete basis (a, then b, then c)
+    // double-float mode, power-of-two K: the transforms and the k-space product in double-float too
+    const bool dft = dfl && L.o_drdf != 0;
     if (dfl) {
         // the fold runs inside the multipole kernel; each cell's (0,0,2) term is kept for its sum
         double* m002 = at<double>(ws, F.o_m002);
-        NF_CUDA(launch_multipoles_red_df(off, rel, C, p, rseg, rk, rcoef, L.nnz, Mr, m002, s),
+        NF_CUDA(launch_multipoles_red_df(off, rel, C, p, rseg, rk, rcoef, L.nnz, Mr, dft ? (void*)Mr : nullptr,
+                                         m002, s),
                 "multipoles (double-float)");
         NF_CUDA(mark(2), "profile");
         if (i002 >= 0) NF_CUDA(launch_far_sum_term(m002, C, 1, 0, s002, s), "sum of the (0,0,2) multipoles");
@@ -1039,17 +1059,27 @@ int run_far(const FarCall& fc, const float* pos, int64_t N, double box, int K, i
         NF_CUDA(launch_far_reduce(M, C, L.nt, L.nr, rseg, rk, rcoef, Mr, s), "multipole fold");
         if (i002 >= 0) NF_CUDA(launch_far_sum_term(M, C, L.nt, i002, s002, s), "sum of the (0,0,2) multipoles");
     }
-    cudaError_t e = launch_far_fft(K, L.nr, true, Mr, Mh, at<void>(ws, F.o_work), F.work, s);
-    if (e != cudaSuccess) return fft_fail(e, "multipoles (forward FFT)");
-    NF_CUDA(launch_far_contract(K, L.nr, static_cast<const int*>(dat(L.o_seg)),
-                                static_cast<const FarPair*>(dat(L.o_pairs)), static_cast<const double*>(dat(L.o_dh)),
-                                Mh, Th, s),
-            "convolution");
-    e = launch_far_fft(K, L.nr, false, Th, Mr, at<void>(ws, F.o_work), F.work, s);
-    if (e != cudaSuccess) return fft_fail(e, "Taylors (inverse FFT)");
+    if (dft) {
+        const void* tw = dat(L.o_tw);
+        NF_CUDA(launch_far_fft_df(K, L.nr, true, Mr, Mh, nullptr, tw, s), "multipoles (forward transform)");
+        NF_CUDA(launch_far_contract_df(K, L.nr, static_cast<const int*>(dat(L.o_seg)),
+                                       static_cast<const FarPair*>(dat(L.o_pairs)), dat(L.o_pcdf), dat(L.o_drdf), Mh,
+                                       Th, s),
+                "convolution");
+        NF_CUDA(launch_far_fft_df(K, L.nr, false, nullptr, Th, Mr, tw, s), "Taylors (inverse transform)");
+    } else {
+        cudaError_t e = launch_far_fft(K, L.nr, true, Mr, Mh, at<void>(ws, F.o_work), F.work, s);
+        if (e != cudaSuccess) return fft_fail(e, "multipoles (forward FFT)");
+        NF_CUDA(launch_far_contract(K, L.nr, static_cast<const int*>(dat(L.o_seg)),
+                                    static_cast<const FarPair*>(dat(L.o_pairs)),
+                                    static_cast<const double*>(dat(L.o_dh)), Mh, Th, s),
+                "convolution");
+        e = launch_far_fft(K, L.nr, false, Th, Mr, at<void>(ws, F.o_work), F.work, s);
+        if (e != cudaSuccess) return fft_fail(e, "Taylors (inverse FFT)");
+    }
     double* T = M;  // the complete multipoles are no longer needed: the rebuilt Taylors go there
     const bool pairs_needed = dfl && (acc_far || acc_add);
-    NF_CUDA(launch_far_rebuild(Mr, C, p, L.nt, L.nr, static_cast<const int4*>(dat(L.o_ops)),
+    NF_CUDA(launch_far_rebuild(Mr, dft, C, p, L.nt, L.nr, static_cast<const int4*>(dat(L.o_ops)),
                                static_cast<const double2*>(dat(L.o_opf)), i002,
                                4.0 * 3.14159265358979323846 * (double)N * w * w / V,
                                2.0 * 3.14159265358979323846 * w * w / V, i002 >= 0 ? s002 : nullptr,

@@ -48,6 +48,7 @@
 #include <cuda_runtime.h>
 #include <cufft.h>
 
+#include <cmath>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -478,6 +479,204 @@ __device__ __forceinline__ dfl df_from(double v)
     return {h, __double2float_rn(v - (double)h)};
 }
 
+// ---- double-float transforms and k-space product ---------------------------
+// GB300's FP64 pipe makes cuFFT's double-precision transforms and the FP64
+// k-space product the slow part of the convolution.  For power-of-two K they
+// run here in double-float on the FP32 pipe instead: a complex value is a
+// float4 {re.h, re.l, im.h, im.l}.  The 3-D real transform is three passes of
+// 1-D radix-2 transforms over lines held in shared memory (bit-reversed on
+// load, one __syncthreads per stage, twiddles e^{-2 pi i j/K} as double-float
+// pairs built on the host from FP64 cos/sin).  Layouts are cuFFT's: the real
+// side is cell-major [x][y][z][field], the spectrum term-major
+// [field][x][y][kz] with kz in 0..K/2; forward is e^{-i...}, the inverse is
+// unnormalised (the 1/K^3 sits in the k-space product).
+struct cdf {
+    dfl re, im;
+};
+__device__ __forceinline__ cdf cdf_ld(float4 v) { return {dfl{v.x, v.y}, dfl{v.z, v.w}}; }
+__device__ __forceinline__ float4 cdf_st(cdf v) { return make_float4(v.re.h, v.re.l, v.im.h, v.im.l); }
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ cdf cdf_mul(cdf w, cdf x)
+{
+    return {df_fma(w.re, x.re, df_neg(df_mul(w.im, x.im))), df_fma(w.re, x.im, df_mul(w.im, x.re))};
+}
+__device__ __forceinline__ cdf cdf_add(cdf a, cdf b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ cdf cdf_sub(cdf a, cdf b) { return {df_add(a.re, df_neg(b.re)), df_add(a.im, df_neg(b.im))}; }
+
+constexpr int kFftThreads = 256;
+constexpr int kFftPoints = 2048;  // complex points of one block's lines in shared memory
+
+__host__ __device__ inline int fft_lines_per_block(int K) { return K >= kFftPoints ? 1 : kFftPoints / K; }
+
+// The radix-2 stages over nl lines of K points in shared memory (bit-reversed
+// order in, natural order out).  tw: e^{-2 pi i j / K}, j < K/2; INV uses the
+// conjugates.
+template <bool INV>
+__device__ __forceinline__ void fft_stages(float4* line, int nl, int K, int logK, const float4* tw)
+{
+    const int half = K >> 1;
+    for (int lh = 0; lh < logK; ++lh) {
+        const int h = 1 << lh, sh = logK - 1 - lh;
+        for (int b = threadIdx.x; b < nl * half; b += blockDim.x) {
+            const int l = b >> (logK - 1), j = b & (half - 1);
+            const int pos = j & (h - 1);
+            const int i0 = ((j - pos) << 1) + pos, i1 = i0 + h;
+            float4 w4 = tw[pos << sh];
+            if (INV) {
+                w4.z = -w4.z;
+                w4.w = -w4.w;
+            }
+            float4* L = line + (size_t)l * K;
+            const cdf u = cdf_ld(L[i0]);
+            const cdf t = cdf_mul(cdf_ld(w4), cdf_ld(L[i1]));
+            L[i0] = cdf_st(cdf_add(u, t));
+            L[i1] = cdf_st(cdf_sub(u, t));
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ int fft_rev(int i, int logK) { return logK ? (int)(__brev((unsigned)i) >> (32 - logK)) : 0; }
+
+// Forward z pass: real double-float fields, cell-major [x][y][z][nf], to the
+// spectrum S [nf][x][y][kz].  Block: one (x, y) and a chunk of fields; each
+// field's z line is transformed as a complex line with zero imaginary part.
+__global__ void __launch_bounds__(kFftThreads) k_fft_z_fwd(const dfl* __restrict__ R, int K, int logK, int nf,
+                                                           int nchunk, const float4* __restrict__ twg,
+                                                           float4* __restrict__ S)
+{
+    extern __shared__ float4 fsm[];
+    float4* tw = fsm;
+    float4* line = fsm + K / 2;
+    const int H = K / 2 + 1;
+    const int FB = fft_lines_per_block(K);
+    const int chunk = blockIdx.x % nchunk;
+    const long long xy = blockIdx.x / nchunk;
+    const int f0 = chunk * FB, nfc = min(FB, nf - f0);
+    for (int j = threadIdx.x; j < K / 2; j += blockDim.x) tw[j] = twg[j];
+    const dfl* src = R + (size_t)xy * K * nf + f0;
+    for (int idx = threadIdx.x; idx < K * nfc; idx += blockDim.x) {
+        const int z = idx / nfc, fl = idx - z * nfc;
+        const dfl v = src[(size_t)z * nf + fl];
+        line[(size_t)fl * K + fft_rev(z, logK)] = make_float4(v.h, v.l, 0.0f, 0.0f);
+    }
+    __syncthreads();
+    fft_stages<false>(line, nfc, K, logK, tw);
+    const size_t fstride = (size_t)K * K * H;
+    for (int idx = threadIdx.x; idx < nfc * H; idx += blockDim.x) {
+        const int fl = idx / H, kz = idx - fl * H;
+        S[(size_t)(f0 + fl) * fstride + (size_t)xy * H + kz] = line[(size_t)fl * K + kz];
+    }
+}
+
+// Complex passes along y or x, in place on the spectrum S [nf][x][y][kz]:
+// lines of K points at stride pstride, W consecutive kz per block.  Block:
+// one (field, other index, kz chunk).
+template <bool INV>
+__global__ void __launch_bounds__(kFftThreads) k_fft_lines(float4* __restrict__ S, int K, int logK, int nA,
+                                                           long long astride, long long pstride, int nchunk,
+                                                           const float4* __restrict__ twg)
+{
+    extern __shared__ float4 fsm[];
+    float4* tw = fsm;
+    float4* line = fsm + K / 2;
+    const int H = K / 2 + 1;
+    const int W = fft_lines_per_block(K);
+    const int chunk = blockIdx.x % nchunk;
+    const long long fa = blockIdx.x / nchunk;
+    const long long f = fa / nA, a = fa - f * nA;
+    const int k0 = chunk * W, wc = min(W, H - k0);
+    for (int j = threadIdx.x; j < K / 2; j += blockDim.x) tw[j] = twg[j];
+    float4* base = S + f * (long long)K * K * H + a * astride + k0;
+    for (int idx = threadIdx.x; idx < K * wc; idx += blockDim.x) {
+        const int pt = idx / wc, w = idx - pt * wc;
+        line[(size_t)w * K + fft_rev(pt, logK)] = base[pt * pstride + w];
+    }
+    __syncthreads();
+    fft_stages<INV>(line, wc, K, logK, tw);
+    for (int idx = threadIdx.x; idx < K * wc; idx += blockDim.x) {
+        const int pt = idx / wc, w = idx - pt * wc;
+        base[pt * pstride + w] = line[(size_t)w * K + pt];
+    }
+}
+
+// Inverse z pass: spectrum S [nf][x][y][kz] (kz <= K/2, the rest by Hermitian
+// symmetry) to real double-float fields, cell-major [x][y][z][nf].
+__global__ void __launch_bounds__(kFftThreads) k_fft_z_inv(const float4* __restrict__ S, int K, int logK, int nf,
+                                                           int nchunk, const float4* __restrict__ twg,
+                                                           dfl* __restrict__ R)
+{
+    extern __shared__ float4 fsm[];
+    float4* tw = fsm;
+    float4* line = fsm + K / 2;
+    const int H = K / 2 + 1;
+    const int FB = fft_lines_per_block(K);
+    const int chunk = blockIdx.x % nchunk;
+    const long long xy = blockIdx.x / nchunk;
+    const int f0 = chunk * FB, nfc = min(FB, nf - f0);
+    for (int j = threadIdx.x; j < K / 2; j += blockDim.x) tw[j] = twg[j];
+    const size_t fstride = (size_t)K * K * H;
+    for (int idx = threadIdx.x; idx < nfc * K; idx += blockDim.x) {
+        const int fl = idx / K, k = idx - fl * K;
+        const float4* row = S + (size_t)(f0 + fl) * fstride + (size_t)xy * H;
+        float4 v;
+        if (k < H) {
+            v = row[k];
+        } else {
+            v = row[K - k];
+            v.z = -v.z;
+            v.w = -v.w;
+        }
+        line[(size_t)fl * K + fft_rev(k, logK)] = v;
+    }
+    __syncthreads();
+    fft_stages<true>(line, nfc, K, logK, tw);
+    dfl* dst = R + (size_t)xy * K * nf + f0;
+    for (int idx = threadIdx.x; idx < K * nfc; idx += blockDim.x) {
+        const int z = idx / nfc, fl = idx - z * nfc;
+        const float4 v = line[(size_t)fl * K + z];
+        dst[(size_t)z * nf + fl] = dfl{v.x, v.y};
+    }
+}
+
+// The k-space product of k_far_contract in double-float: derivatives and
+// pair coefficients as double-float pairs, spectra as double-float complex;
+// scale (1/K^3, a power of two) is exact on both halves.
+__global__ void __launch_bounds__(256) k_far_contract_df(long long nq, int nout, const int* __restrict__ seg,
+                                                         const FarPair* __restrict__ pairs,
+                                                         const float2* __restrict__ pcoef,
+                                                         const dfl* __restrict__ Dr, const float4* __restrict__ Mh,
+                                                         float4* __restrict__ Th, float scale)
+{
+    const long long total = nq * nout;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int n = (int)(e / nq);
+        const long long q = e - (long long)n * nq;
+        dfl re = {0.0f, 0.0f}, im = {0.0f, 0.0f};
+        const int e1 = seg[n + 1];
+        for (int i = seg[n]; i < e1; ++i) {
+            const FarPair pr = pairs[i];
+            const float2 c = pcoef[i];
+            const dfl cd = df_mul(dfl{c.x, c.y}, Dr[(size_t)(pr.j & 0x7fffffff) * nq + q]);
+            const float4 m = Mh[(size_t)pr.k * nq + q];
+            // odd |j|: i cd m = (-cd m.im, cd m.re)
+            const bool odd = pr.j < 0;
+            const dfl mr = odd ? dfl{m.z, m.w} : dfl{m.x, m.y}, mi = odd ? dfl{m.x, m.y} : dfl{m.z, m.w};
+            re = df_fma(odd ? df_neg(cd) : cd, mr, re);
+            im = df_fma(cd, mi, im);
+        }
+        Th[e] = make_float4(re.h * scale, re.l * scale, im.h * scale, im.l * scale);
+    }
+}
+
+// FP64 -> double-float pairs, elementwise.
+__global__ void k_to_df(const double* __restrict__ src, long long n, dfl* __restrict__ dst)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = df_from(src[i]);
+}
+
 // Cell multipoles in cell units, double-float, folded onto the reduced basis
 // in the same kernel.  One block per cell and one thread per complete term:
 // kMpChunk particles at a time the block builds their powers x^e, y^e, z^e
@@ -486,7 +685,8 @@ __device__ __forceinline__ dfl df_from(double v)
 // (x^a y^b) z^c to two double-float partial sums.  The cell's complete
 // multipoles then go through the fold of k_far_reduce, Mr^r = sum_k
 // f_{r,k} M^k, with its coefficients as double-float pairs, and are written
-// as FP64, with the cell's (0,0,2) term for its sum over cells.  (The
+// as FP64 (Mr) or as double-float pairs (Mrd, for the double-float
+// transforms), with the cell's (0,0,2) term for its sum over cells.  (The
 // error-free transformations stay on scalar FP32 instructions: in probes the
 // packed .f32x2 form of the same sequence did not always keep the product's
 // rounding error, depending on the surrounding code.)
@@ -495,7 +695,7 @@ template <int P>
 __global__ void k_multipoles_red_df(const int* __restrict__ off, const float4* __restrict__ rel, int C,
                                     const int* __restrict__ rseg, const int* __restrict__ rk,
                                     const double* __restrict__ rcoef, double* __restrict__ Mr,
-                                    double* __restrict__ m002)
+                                    dfl* __restrict__ Mrd, double* __restrict__ m002)
 {
     constexpr int P1 = P + 1, NAB = P1 * (P + 2) / 2, NT = far_terms(P), NR = P1 * P1;
     extern __shared__ dfl smem_mp[];
@@ -568,7 +768,10 @@ __global__ void k_multipoles_red_df(const int* __restrict__ off, const float4* _
         for (int r = threadIdx.x; r < NR; r += blockDim.x) {
             dfl m = {0.0f, 0.0f};
             for (int i = sg[r]; i < sg[r + 1]; ++i) m = df_fma(cf[i], Ms[ck[i]], m);
-            Mr[(size_t)cell * NR + r] = (double)m.h + (double)m.l;
+            if (Mrd)
+                Mrd[(size_t)cell * NR + r] = m;  // the double-float transforms take the pairs as they are
+            else
+                Mr[(size_t)cell * NR + r] = (double)m.h + (double)m.l;
         }
         if (P >= 2 && t == 2) m002[cell] = (double)Ms[2].h + (double)Ms[2].l;  // term 2 is (0,0,2)
         __syncthreads();  // Ms is rewritten for the next cell
@@ -729,11 +932,12 @@ __global__ void k_far_sum_term(const double* __restrict__ M, int C, int nt, int 
 // T^0.  F64 runs the recursion in FP64 and writes T; DF splits the reduced
 // Taylors into double-float pairs once and runs the recursion on the FP32
 // pipe, writing Tdf: the forces of the double-float kernels do not depend on
-// whether T is asked for too.
+// whether T is asked for too.  DIN: the reduced Taylors arrive as
+// double-float pairs (from the double-float transforms) instead of FP64.
 constexpr int kRebuildWarps = 8;
 constexpr int kRebuildFetch = (kMaxFarOrder + 1) * (kMaxFarOrder + 1) / 32 + 1;  // reduced terms per lane
-template <bool F64, bool DF>
-__global__ void k_far_rebuild(const double* __restrict__ Tr, int C, int p, int nt, int nr, const int4* __restrict__ ops,
+template <bool F64, bool DF, bool DIN>
+__global__ void k_far_rebuild(const void* __restrict__ Trv, int C, int p, int nt, int nr, const int4* __restrict__ ops,
                               const double2* __restrict__ opf, int t002, double lap, double t0_per_s002,
                               const double* __restrict__ partial, double* __restrict__ T, dfl* __restrict__ Tdf)
 {
@@ -780,20 +984,25 @@ __global__ void k_far_rebuild(const double* __restrict__ Tr, int C, int p, int n
 #pragma unroll
     for (int k = 0; k < kRebuildFetch; ++k) rdst[k] = lane + 32 * k < nr ? rmap[lane + 32 * k] : -1;
     const int warps = (gridDim.x * blockDim.x) >> 5;
-    double nx[kRebuildFetch];
+    // the reduced Taylors as raw 8-byte words: an FP64 value, or a double-float pair (DIN)
+    const unsigned long long* __restrict__ Tr = static_cast<const unsigned long long*>(Trv);
+    unsigned long long nx[kRebuildFetch];
     int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
 #pragma unroll
     for (int k = 0; k < kRebuildFetch; ++k) {
         const int i = lane + 32 * k;
-        nx[k] = (c < C && i < nr) ? Tr[(size_t)c * nr + i] : 0.0;
+        nx[k] = (c < C && i < nr) ? Tr[(size_t)c * nr + i] : 0ull;
     }
     for (; c < C; c += warps) {
 #pragma unroll
         for (int k = 0; k < kRebuildFetch; ++k) {
             const int d = rdst[k];
             if (d >= 0) {
-                if (F64) t[d] = d == 0 ? nx[k] + t0 : nx[k];
-                if (DF) td[d] = d == 0 ? df_add(df_from(nx[k]), t0d) : df_from(nx[k]);
+                const dfl vd = DIN ? dfl{__uint_as_float((unsigned)nx[k]), __uint_as_float((unsigned)(nx[k] >> 32))}
+                                   : df_from(__longlong_as_double((long long)nx[k]));
+                const double v = DIN ? (double)vd.h + (double)vd.l : __longlong_as_double((long long)nx[k]);
+                if (F64) t[d] = d == 0 ? v + t0 : v;
+                if (DF) td[d] = d == 0 ? df_add(vd, t0d) : vd;
             }
         }
         __syncwarp();
@@ -801,7 +1010,7 @@ __global__ void k_far_rebuild(const double* __restrict__ Tr, int C, int p, int n
 #pragma unroll
         for (int k = 0; k < kRebuildFetch; ++k) {
             const int i = lane + 32 * k;
-            nx[k] = (cn < C && i < nr) ? Tr[(size_t)cn * nr + i] : 0.0;
+            nx[k] = (cn < C && i < nr) ? Tr[(size_t)cn * nr + i] : 0ull;
         }
         for (int L = 2; L <= p; ++L) {
             for (int i = level[L] + lane; i < level[L + 1]; i += 32) {
@@ -976,6 +1185,8 @@ FarTables far_tables(int p, double w)
             if (order & 1) pr.j |= (int)0x80000000u;
             pr.coef = wp[order] / (fac[ta[n]] * fac[tbv[n]] * fac[tc[n]]);
             tb.pairs.push_back(pr);
+            const float ch = (float)pr.coef;
+            tb.pair_cdf.push_back(make_float2(ch, (float)(pr.coef - (double)ch)));
         }
         tb.pair_seg.push_back((int)tb.pairs.size());
     }
@@ -1080,9 +1291,85 @@ cudaError_t launch_deriv_recip(int K, int p, double box, double alpha, int hmax,
     return cudaGetLastError();
 }
 
+bool far_df_fft(int K) { return K >= 4 && K <= 256 && (K & (K - 1)) == 0; }
+
+std::vector<float4> far_twiddles(int K)
+{
+    std::vector<float4> tw(K / 2);
+    for (int j = 0; j < K / 2; ++j) {
+        const double th = 2.0 * 3.14159265358979323846 * j / K;
+        const double c = std::cos(th), sn = -std::sin(th);
+        const float ch = (float)c, sh = (float)sn;
+        tw[j] = make_float4(ch, (float)(c - (double)ch), sh, (float)(sn - (double)sh));
+    }
+    return tw;
+}
+
+cudaError_t launch_far_fft_df(int K, int nf, bool forward, const void* real_in, void* spec, void* real_out,
+                              const void* tw, cudaStream_t s)
+{
+    if (!far_df_fft(K)) return cudaErrorInvalidValue;
+    int logK = 0;
+    while ((1 << logK) < K) ++logK;
+    const int H = K / 2 + 1, FB = fft_lines_per_block(K);
+    const size_t smem = ((size_t)K / 2 + (size_t)FB * K) * sizeof(float4);
+    const float4* twg = static_cast<const float4*>(tw);
+    float4* S = static_cast<float4*>(spec);
+    const int zchunks = (nf + FB - 1) / FB, lchunks = (H + FB - 1) / FB;
+    const long long zblocks = (long long)K * K * zchunks, lblocks = (long long)nf * K * lchunks;
+    const long long KH = (long long)K * H;
+    cudaError_t e;
+    if (forward) {
+        e = ensure_smem((const void*)k_fft_z_fwd, (int)smem);
+        if (e == cudaSuccess) e = ensure_smem((const void*)k_fft_lines<false>, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_fft_z_fwd<<<(unsigned)zblocks, kFftThreads, smem, s>>>(static_cast<const dfl*>(real_in), K, logK, nf,
+                                                                  zchunks, twg, S);
+        // y lines: per (field, x), points H apart; x lines: per (field, y), points K H apart
+        k_fft_lines<false><<<(unsigned)lblocks, kFftThreads, smem, s>>>(S, K, logK, K, KH, H, lchunks, twg);
+        k_fft_lines<false><<<(unsigned)lblocks, kFftThreads, smem, s>>>(S, K, logK, K, H, KH, lchunks, twg);
+    } else {
+        e = ensure_smem((const void*)k_fft_z_inv, (int)smem);
+        if (e == cudaSuccess) e = ensure_smem((const void*)k_fft_lines<true>, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_fft_lines<true><<<(unsigned)lblocks, kFftThreads, smem, s>>>(S, K, logK, K, H, KH, lchunks, twg);
+        k_fft_lines<true><<<(unsigned)lblocks, kFftThreads, smem, s>>>(S, K, logK, K, KH, H, lchunks, twg);
+        k_fft_z_inv<<<(unsigned)zblocks, kFftThreads, smem, s>>>(S, K, logK, nf, zchunks, twg,
+                                                                  static_cast<dfl*>(real_out));
+    }
+    count_launches(3);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_far_contract_df(int K, int nout, const int* seg, const FarPair* pairs, const void* pcoef,
+                                   const void* Dr, const void* Mh, void* Th, cudaStream_t s)
+{
+    const long long nq = (long long)K * K * (K / 2 + 1);
+    long long blocks = (nq * nout + 255) / 256;
+    const long long cap = (long long)device_sms() * 64;
+    if (blocks > cap) blocks = cap;
+    const float scale = 1.0f / ((float)K * K * K);  // the unnormalised inverse transform; exact for K = 2^n
+    k_far_contract_df<<<(int)blocks, 256, 0, s>>>(nq, nout, seg, pairs, static_cast<const float2*>(pcoef),
+                                                  static_cast<const dfl*>(Dr), static_cast<const float4*>(Mh),
+                                                  static_cast<float4*>(Th), scale);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_df(const double* src, long long n, void* dst, cudaStream_t s)
+{
+    long long blocks = (n + 255) / 256;
+    const long long cap = (long long)device_sms() * 32;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) return cudaSuccess;
+    k_to_df<<<(int)blocks, 256, 0, s>>>(src, n, static_cast<dfl*>(dst));
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_multipoles_red_df(const int* off, const float4* rel, int C, int p, const int* rseg,
-                                     const int* rk, const double* rcoef, long long nnz, double* Mr, double* m002,
-                                     cudaStream_t s)
+                                     const int* rk, const double* rcoef, long long nnz, double* Mr, void* Mrd,
+                                     double* m002, cudaStream_t s)
 {
     const int nt = far_terms(p), nr = (p + 1) * (p + 1), nab = (p + 1) * (p + 2) / 2;
     const int threads = ((nt + 31) / 32) * 32;
@@ -1094,7 +1381,8 @@ cudaError_t launch_multipoles_red_df(const int* off, const float4* rel, int C, i
     case P: {                                                                                          \
         cudaError_t e = ensure_smem((const void*)k_multipoles_red_df<P>, (int)smem);                   \
         if (e != cudaSuccess) return e;                                                                \
-        k_multipoles_red_df<P><<<grid, threads, smem, s>>>(off, rel, C, rseg, rk, rcoef, Mr, m002);    \
+        k_multipoles_red_df<P><<<grid, threads, smem, s>>>(off, rel, C, rseg, rk, rcoef, Mr,          \
+                                                           static_cast<dfl*>(Mrd), m002);              \
         break;                                                                                         \
     }
         NF_MP_RED_CASE(0)
@@ -1182,14 +1470,20 @@ cudaError_t launch_far_sum_term(const double* M, int C, int nt, int term, double
 
 int far_sum_partials() { return kSumBlocks; }
 
-cudaError_t launch_far_rebuild(const double* Tr, int C, int p, int nt, int nr, const int4* ops, const double2* opf,
-                               int t002, double lap, double t0_per_s002, const double* partial, double* T, void* Tdf,
-                               cudaStream_t s)
+cudaError_t launch_far_rebuild(const void* Tr, bool df_in, int C, int p, int nt, int nr, const int4* ops,
+                               const double2* opf, int t002, double lap, double t0_per_s002, const double* partial,
+                               double* T, void* Tdf, cudaStream_t s)
 {
     if (!T && !Tdf) return cudaSuccess;
-    const void* fn = T && Tdf ? (const void*)k_far_rebuild<true, true>
-                     : T      ? (const void*)k_far_rebuild<true, false>
-                              : (const void*)k_far_rebuild<false, true>;
+    const void* fn;
+    if (df_in)
+        fn = T && Tdf ? (const void*)k_far_rebuild<true, true, true>
+             : T      ? (const void*)k_far_rebuild<true, false, true>
+                      : (const void*)k_far_rebuild<false, true, true>;
+    else
+        fn = T && Tdf ? (const void*)k_far_rebuild<true, true, false>
+             : T      ? (const void*)k_far_rebuild<true, false, false>
+                      : (const void*)k_far_rebuild<false, true, false>;
     const int slots = (T ? 1 : 0) + (Tdf ? 1 : 0);
     const size_t smem = (size_t)nt * (sizeof(int4) + sizeof(double2) + sizeof(float4)) +
                         (16 + (size_t)((nr + 3) & ~3)) * sizeof(int) + (size_t)kRebuildWarps * slots * nt * sizeof(double);
@@ -1202,15 +1496,25 @@ cudaError_t launch_far_rebuild(const double* Tr, int C, int p, int nt, int nr, c
     const long long cap = (long long)device_sms() * (per_sm > 0 ? per_sm : 1);  // one wave, all resident
     if (blocks > cap) blocks = cap;
     dfl* td = static_cast<dfl*>(Tdf);
-    if (T && Tdf)
-        k_far_rebuild<true, true><<<(int)blocks, kRebuildWarps * 32, smem, s>>>(Tr, C, p, nt, nr, ops, opf, t002, lap,
-                                                                              t0_per_s002, partial, T, td);
-    else if (T)
-        k_far_rebuild<true, false><<<(int)blocks, kRebuildWarps * 32, smem, s>>>(Tr, C, p, nt, nr, ops, opf, t002, lap,
-                                                                               t0_per_s002, partial, T, td);
-    else
-        k_far_rebuild<false, true><<<(int)blocks, kRebuildWarps * 32, smem, s>>>(Tr, C, p, nt, nr, ops, opf, t002, lap,
-                                                                               t0_per_s002, partial, T, td);
+#define NF_REBUILD_LAUNCH(A, B, D)                                                                           \
+    k_far_rebuild<A, B, D><<<(int)blocks, kRebuildWarps * 32, smem, s>>>(Tr, C, p, nt, nr, ops, opf, t002, lap, \
+                                                                        t0_per_s002, partial, T, td)
+    if (df_in) {
+        if (T && Tdf)
+            NF_REBUILD_LAUNCH(true, true, true);
+        else if (T)
+            NF_REBUILD_LAUNCH(true, false, true);
+        else
+            NF_REBUILD_LAUNCH(false, true, true);
+    } else {
+        if (T && Tdf)
+            NF_REBUILD_LAUNCH(true, true, false);
+        else if (T)
+            NF_REBUILD_LAUNCH(true, false, false);
+        else
+            NF_REBUILD_LAUNCH(false, true, false);
+    }
+#undef NF_REBUILD_LAUNCH
     count_launches(1);
     return cudaGetLastError();
 }

@@ -106,7 +106,8 @@ struct DerivHeader {
     unsigned long long o_seg, o_pairs, o_dh, total;  // reduced pair segments and pairs, transformed derivatives
     unsigned long long o_rseg, o_rk, o_rcoef, o_ops, o_opf;  // fold and rebuild tables
     long long nnz;
-    unsigned long long pad[15];
+    unsigned long long o_drdf, o_pcdf, o_tw;  // double-float derivatives, pair coefficients, twiddles (K = 2^n)
+    unsigned long long pad[12];
 };
 static_assert(sizeof(DerivHeader) == 256, "derivatives header is 256 bytes");
 constexpr unsigned kDerivMagic = 0x4E464452u;
@@ -123,6 +124,7 @@ struct FarTables {
     std::vector<double> red_coef;
     std::vector<int> pair_seg;
     std::vector<FarPair> pairs;
+    std::vector<float2> pair_cdf;  // the pairs' coefficients as double-float pairs
     std::vector<int4> ops;       // (dst, reduced source or -1, s1, s2)
     std::vector<double2> opf;    // (f1, f2): T[dst] = -f1 T[s1] - f2 T[s2] (+ the constant for (0,0,2))
     int t002 = -1;               // complete index of (0,0,2), or -1 when p < 2
@@ -134,9 +136,10 @@ cudaError_t launch_far_reduce(const double* M, int C, int nt, int nr, const int*
 cudaError_t launch_far_sum_term(const double* M, int C, int nt, int term, double* partial, cudaStream_t s);
 int far_sum_partials();
 // complete Taylors T [C][nt] (and, with Tdf, their double-float pairs) from the reduced ones
-cudaError_t launch_far_rebuild(const double* Tr, int C, int p, int nt, int nr, const int4* ops, const double2* opf,
-                               int t002, double lap, double t0_per_s002, const double* partial, double* T, void* Tdf,
-                               cudaStream_t s);
+// Tr: FP64, or double-float pairs with df_in
+cudaError_t launch_far_rebuild(const void* Tr, bool df_in, int C, int p, int nt, int nr, const int4* ops,
+                               const double2* opf, int t002, double lap, double t0_per_s002, const double* partial,
+                               double* T, void* Tdf, cudaStream_t s);
 // cuFFT work-area bytes to reserve for the forward and inverse transforms of nt fields on K^3
 size_t far_fft_work_bytes(int K, int nt);
 // forward: real cell-major [K^3][nt] -> complex term-major [nt][K][K][K/2+1]; inverse the reverse
@@ -151,9 +154,21 @@ cudaError_t launch_unscale_taylors(const double* Tc, int C, int p, double w, dou
 // double-float forms of the per-particle kernels (cell units); Tdf holds C * nt pairs of floats (from the rebuild)
 // reduced multipoles Mr [C][(p+1)^2] (the fold of the double-float complete ones) and
 // each cell's (0,0,2) multipole m002 [C]; rseg/rk/rcoef: the fold table, nnz entries
+// (Mrd non-null: the reduced multipoles as double-float pairs there instead of FP64 in Mr)
 cudaError_t launch_multipoles_red_df(const int* off, const float4* rel, int C, int p, const int* rseg,
-                                     const int* rk, const double* rcoef, long long nnz, double* Mr, double* m002,
-                                     cudaStream_t s);
+                                     const int* rk, const double* rcoef, long long nnz, double* Mr, void* Mrd,
+                                     double* m002, cudaStream_t s);
+// Double-float transforms for power-of-two K (4..256): forward, real cell-major
+// pairs [C][nf] -> spectrum [nf][K][K][K/2+1] of float4 {re.h, re.l, im.h, im.l};
+// inverse (unnormalised), spectrum (overwritten) -> real pairs [C][nf].
+bool far_df_fft(int K);
+std::vector<float4> far_twiddles(int K);  // e^{-2 pi i j/K}, j < K/2, as double-float pairs
+cudaError_t launch_far_fft_df(int K, int nf, bool forward, const void* real_in, void* spec, void* real_out,
+                              const void* tw, cudaStream_t s);
+// the k-space product on double-float spectra (pcoef: the pairs' coefficients as float2 pairs)
+cudaError_t launch_far_contract_df(int K, int nout, const int* seg, const FarPair* pairs, const void* pcoef,
+                                   const void* Dr, const void* Mh, void* Th, cudaStream_t s);
+cudaError_t launch_to_df(const double* src, long long n, void* dst, cudaStream_t s);
 cudaError_t launch_taylor_forces_df(int p, const int* off, const float4* rel, const void* Tdf, int N, int C,
                                     double scale, double* acc_far, float* acc_add, cudaStream_t s);
 // Th[n][q] for nout output fields (the reduced Taylors) from the pair table

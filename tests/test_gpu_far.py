@@ -65,6 +65,24 @@ def test_derivatives_match_oracle(K, R, p, box):
     assert (np.abs(got - kept) / scale).max() < 1e-10
 
 
+@pytest.mark.parametrize("K,R,p", [(8, 2, 8), (5, 2, 4), (16, 3, 6)])
+def test_double_float_copy_of_derivatives(K, R, p):
+    """For power-of-two K the buffer also holds the transformed derivatives as
+    double-float pairs: hi = fp32(D), lo = fp32(D - hi); other K have none."""
+    import paper_2110_11392_gb300 as nf
+    ff = nf.FarField(K, R, p)
+    head = ff.derivs[:256].cpu().numpy()
+    o_drdf = int(np.frombuffer(head[136:144].tobytes(), np.uint64)[0])   # DerivHeader.o_drdf
+    if K & (K - 1):
+        assert o_drdf == 0
+        return
+    D = _dr_gpu(ff).ravel()
+    pairs = ff.derivs[o_drdf:o_drdf + 8 * D.size].cpu().numpy().view(np.float32).reshape(-1, 2)
+    hi = D.astype(np.float32)
+    assert np.array_equal(pairs[:, 0], hi)
+    assert np.array_equal(pairs[:, 1], (D - hi.astype(np.float64)).astype(np.float32))
+
+
 @pytest.mark.parametrize("K,R,p,N,kind", [(5, 2, 4, 3000, "uniform"), (8, 2, 8, 20000, "clustered"),
                                           (11, 2, 8, 65536, "uniform"), (7, 3, 5, 9000, "clustered"),
                                           (16, 2, 8, 40000, "clustered"), (6, 2, 1, 500, "uniform"),
@@ -174,7 +192,7 @@ def test_argument_errors():
         nf.FarField(4, 2, 4)            # K < 2R + 1 is caught by the library
 
 
-@pytest.mark.parametrize("K,p", [(6, 12), (5, 10)])
+@pytest.mark.parametrize("K,p", [(6, 12), (5, 10), (8, 12)])
 def test_highest_orders_match_oracle(K, p, arith):
     import torch
     import paper_2110_11392_gb300 as nf
@@ -233,12 +251,16 @@ def test_total_force_call_equals_near_plus_far():
     assert torch.equal(tot, ref)
 
 
-def test_the_two_arithmetics_agree():
+@pytest.mark.parametrize("K", [12, 16, 32])
+def test_the_two_arithmetics_agree(K):
+    """K = 12: cuFFT and the FP64 product in both modes; K = 16, 32 (powers of
+    two): the double-float mode runs its own double-float transforms and
+    product, the FP64 mode cuFFT's."""
     import torch
     import paper_2110_11392_gb300 as nf
     from paper_2110_11392_gb300 import _lib
-    pos = to_dev(_clustered(60000, 12, 13))
-    ff = nf.FarField(12, 2, 8)
+    pos = to_dev(_clustered(60000, K, 13))
+    ff = nf.FarField(K, 2, 8)
     before = _lib.nf_far_get_arith()
     try:
         _lib.nf_far_set_arith(_lib.NF_FAR_FP64)
