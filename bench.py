@@ -627,8 +627,9 @@ def measure_far(w, pos, dev, flush, fma, fwd_ms, p=8, reps=5):
             "kdk_total_force_particle_updates_per_s": w.N / (float(np.median(step_ms)) / 1e3),
             "arith": names[arith], "other_arith": {"arith": names[other], "ms": other_ms},
             "taylor_roofline": taylor_roof,
-            "note": "derivatives, FFTs and k-space product in FP64; multipoles and Taylors in the stated "
-                    "arithmetic; derivatives once per (K, R, p, box); Ewald-summed periodic force = near + far"}
+            "note": "derivatives in FP64, once per (K, R, p, box); in double-float mode (K a power of two) the "
+                    "multipoles, transforms, k-space product, rebuild and Taylors are double-float on the FP32 "
+                    "pipe; in FP64 mode cuFFT and FP64 kernels; Ewald-summed periodic force = near + far"}
 
 
 def measure_multipoles(w, pos, dev, flush, p=8, reps=3):

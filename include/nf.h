@@ -275,15 +275,18 @@ int nf_multipoles(const float *pos, int64_t N, double box, int K, int p, double 
  * Taylor index n and multipole index k with |n| + |k| <= p, both in the
  * complete basis of (p+3)(p+2)(p+1)/6 terms (ordered as in nf_multipoles).
  * The uniform background of Ewald summation is included (the mean density
- * exerts no force).  Arithmetic: FP64 for the derivatives, FFTs and k-space
- * product; FP64 or double-float for the per-particle kernels (see
- * nf_far_set_arith).  The FFTs are cuFFT's. */
+ * exerts no force).  Arithmetic: FP64 for the derivatives; double-float or
+ * FP64 for the rest (see nf_far_set_arith).  The transforms are this
+ * library's double-float kernels for a power-of-two K in double-float mode,
+ * cuFFT's FP64 transforms otherwise. */
 #define NF_MAX_FAR_ORDER 12
 
 /* Bytes of a derivatives buffer for grid K and order p (0 if out of range):
- * a 256-byte header, the convolution's coefficient table and the transformed
- * derivatives, (p+3)(p+2)(p+1)/6 FP64 fields of K*K*(K/2+1) values.  The
- * transform of a term of even order is real and of odd order imaginary (the
+ * a 256-byte header, the convolution's tables and the transformed
+ * derivatives, (p+3)(p+2)(p+1)/6 FP64 fields of K*K*(K/2+1) values (for a
+ * power-of-two K a second copy as double-float pairs, with the pairs'
+ * coefficients and the transforms' twiddles in that form).  The transform
+ * of a term of even order is real and of odd order imaginary (the
  * derivatives have definite parity, Sec. "Far-field Computation"), so one
  * real number per term and frequency is kept. */
 size_t nf_derivatives_bytes(int K, int p);
@@ -335,15 +338,18 @@ int nf_forces_total(const float *pos, int64_t N, double box, int K, int R, doubl
                     const void *derivs, size_t derivs_bytes, float *acc, void *ws, size_t ws_bytes,
                     void *ws_far, size_t ws_far_bytes, void *stream);
 
-/* Arithmetic of the per-particle far-field kernels (the multipoles and the
- * Taylor evaluation), process-wide.  The paper keeps every internal
+/* Arithmetic of the far-field call (multipoles, convolution, Taylor
+ * evaluation), process-wide.  The paper keeps every internal
  * far-field computation in double precision to avoid round-off build-up.
  * NF_FAR_FP64 does so with IEEE binary64 arithmetic, which GB300 runs at
  * 1/64 of its FP32 rate.  NF_FAR_DOUBLE_FLOAT (the default) keeps each value
  * as an unevaluated sum of two FP32 numbers, held exact by error-free
  * transformations, on the FP32 pipe: about 48 significant bits.  Both modes
- * give the same far field to 1e-12 of its largest value (tested).  The FFTs, the k-space
- * product and the derivatives are FP64 in both.  nf_far_set_arith returns
+ * give the same far field to 1e-12 of its largest value (tested).  In
+ * double-float mode with K a power of two the transforms and the k-space
+ * product are double-float too; otherwise (and in FP64 mode) they are
+ * cuFFT's FP64 transforms and an FP64 product.  The derivatives are FP64
+ * in both.  nf_far_set_arith returns
  * NF_ERR_ARG for another mode; calls already enqueued keep the mode they
  * were enqueued with. */
 #define NF_FAR_FP64 0
