@@ -509,11 +509,12 @@ def taylor_flop_per_particle(p: int) -> int:
 
 def taylor_df_ops_per_particle(p: int) -> int:
     """FP32 instructions of the double-float Taylor evaluation at one particle:
-    the Horner steps of taylor_flop_per_particle, 14 FP32 instructions each
-    (product with its FMA error terms, TwoSum, two adds, FastTwoSum)."""
+    the Horner steps of taylor_flop_per_particle, 11 FP32 instructions each
+    (product with its FMA error terms, TwoSum, two adds; the steps skip the
+    renormalisation)."""
     nt = (p + 3) * (p + 2) * (p + 1) // 6
     nab = (p + 2) * (p + 1) // 2
-    return 14 * (2 * nt + 3 * nab + 4 * (p + 1))
+    return 11 * (2 * nt + 3 * nab + 4 * (p + 1))
 
 
 def measure_far(w, pos, dev, flush, fma, fwd_ms, p=8, reps=5):
