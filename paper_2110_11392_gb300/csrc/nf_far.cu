@@ -533,33 +533,74 @@ constexpr int kFftPoints = 2048;  // complex points of one block's lines in shar
 
 __host__ __device__ inline int fft_lines_per_block(int K) { return K >= kFftPoints ? 1 : kFftPoints / K; }
 
-// The radix-2 stages over nl lines of K points in shared memory (bit-reversed
-// order in, natural order out).  tw: e^{-2 pi i j / K}, j < K/2; INV uses the
-// conjugates.
+// The stages over nl lines of K points in shared memory (bit-reversed order
+// in, natural order out), two radix-2 stages at a time: a thread loads four
+// points i0 + {0, h, 2h, 3h}, applies stage h (twiddle W_2h^pos on both
+// pairs) and stage 2h (W_4h^pos, and W_4h^{pos+h} = W_4h^pos * (-i)), and
+// stores them; a last radix-2 stage when log2 K is odd.  tw: e^{-2 pi i j / K},
+// j < K/2; INV uses the conjugates (and +i).
+__device__ __forceinline__ cdf cdf_tw(const float4* tw, int j, bool inv)
+{
+    float4 w4 = tw[j];
+    if (inv) {
+        w4.z = -w4.z;
+        w4.w = -w4.w;
+    }
+    return cdf_ld(w4);
+}
+
 template <bool INV>
 __device__ __forceinline__ void fft_stages(float4* line, int nl, int K, int logK, const float4* tw)
 {
-    const int half = K >> 1;
-    for (int lh = 0; lh < logK; ++lh) {
+    int lh = 0;
+    for (; lh + 1 < logK; lh += 2) {
+        const int h = 1 << lh, s1 = logK - 1 - lh, s2 = logK - 2 - lh;
+        const int quarter = K >> 2;
+        for (int b = threadIdx.x; b < nl * quarter; b += blockDim.x) {
+            const int l = b >> (logK - 2), j = b & (quarter - 1);
+            const int pos = j & (h - 1);
+            const int i0 = ((j - pos) << 2) + pos;
+            float4* L = line + (size_t)l * K;
+            const cdf x0 = cdf_ld(L[i0]), x1 = cdf_ld(L[i0 + h]), x2 = cdf_ld(L[i0 + 2 * h]), x3 = cdf_ld(L[i0 + 3 * h]);
+            const cdf w1 = cdf_tw(tw, pos << s1, INV), w2 = cdf_tw(tw, pos << s2, INV);
+            const cdf t1 = cdf_mul(w1, x1), t3 = cdf_mul(w1, x3);
+            const cdf a0 = cdf_add(x0, t1), a1 = cdf_sub(x0, t1), a2 = cdf_add(x2, t3), a3 = cdf_sub(x2, t3);
+            const cdf u2 = cdf_mul(w2, a2);
+            const cdf v = cdf_mul(w2, a3);
+            // times -i (forward) or +i (inverse)
+            const cdf u3 = INV ? cdf{df_neg(v.im), v.re} : cdf{v.im, df_neg(v.re)};
+            L[i0] = cdf_st(cdf_add(a0, u2));
+            L[i0 + 2 * h] = cdf_st(cdf_sub(a0, u2));
+            L[i0 + h] = cdf_st(cdf_add(a1, u3));
+            L[i0 + 3 * h] = cdf_st(cdf_sub(a1, u3));
+        }
+        __syncthreads();
+    }
+    if (lh < logK) {  // the last stage, radix 2
         const int h = 1 << lh, sh = logK - 1 - lh;
+        const int half = K >> 1;
         for (int b = threadIdx.x; b < nl * half; b += blockDim.x) {
             const int l = b >> (logK - 1), j = b & (half - 1);
             const int pos = j & (h - 1);
             const int i0 = ((j - pos) << 1) + pos, i1 = i0 + h;
-            float4 w4 = tw[pos << sh];
-            if (INV) {
-                w4.z = -w4.z;
-                w4.w = -w4.w;
-            }
             float4* L = line + (size_t)l * K;
             const cdf u = cdf_ld(L[i0]);
-            const cdf t = cdf_mul(cdf_ld(w4), cdf_ld(L[i1]));
+            const cdf t = cdf_mul(cdf_tw(tw, pos << sh, INV), cdf_ld(L[i1]));
             L[i0] = cdf_st(cdf_add(u, t));
             L[i1] = cdf_st(cdf_sub(u, t));
         }
         __syncthreads();
     }
 }
+
+// x / d for a block-invariant d by a multiply-high with m = ceil(2^32 / d):
+// exact for x < 2^32 / d (here x < 2^20, d <= 2^11).
+struct FastDiv {
+    unsigned long long m;
+    int d;
+    __device__ explicit FastDiv(int dv) : m(((1ull << 32) + (unsigned long long)dv - 1) / (unsigned long long)dv), d(dv) {}
+    __device__ __forceinline__ int div(int x) const { return (int)(((unsigned long long)(unsigned)x * m) >> 32); }
+};
 
 __device__ __forceinline__ int fft_rev(int i, int logK) { return logK ? (int)(__brev((unsigned)i) >> (32 - logK)) : 0; }
 
@@ -580,8 +621,9 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_z_fwd(const dfl* __restrict
     const int f0 = chunk * FB, nfc = min(FB, nf - f0);
     for (int j = threadIdx.x; j < K / 2; j += blockDim.x) tw[j] = twg[j];
     const dfl* src = R + (size_t)xy * K * nf + f0;
+    const FastDiv by_nfc(nfc), by_H(H);
     for (int idx = threadIdx.x; idx < K * nfc; idx += blockDim.x) {
-        const int z = idx / nfc, fl = idx - z * nfc;
+        const int z = by_nfc.div(idx), fl = idx - z * nfc;
         const dfl v = src[(size_t)z * nf + fl];
         line[(size_t)fl * K + fft_rev(z, logK)] = make_float4(v.h, v.l, 0.0f, 0.0f);
     }
@@ -589,7 +631,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_z_fwd(const dfl* __restrict
     fft_stages<false>(line, nfc, K, logK, tw);
     const size_t fstride = (size_t)K * K * H;
     for (int idx = threadIdx.x; idx < nfc * H; idx += blockDim.x) {
-        const int fl = idx / H, kz = idx - fl * H;
+        const int fl = by_H.div(idx), kz = idx - fl * H;
         S[(size_t)(f0 + fl) * fstride + (size_t)xy * H + kz] = line[(size_t)fl * K + kz];
     }
 }
@@ -613,14 +655,15 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_lines(float4* __restrict__ 
     const int k0 = chunk * W, wc = min(W, H - k0);
     for (int j = threadIdx.x; j < K / 2; j += blockDim.x) tw[j] = twg[j];
     float4* base = S + f * (long long)K * K * H + a * astride + k0;
+    const FastDiv by_wc(wc);
     for (int idx = threadIdx.x; idx < K * wc; idx += blockDim.x) {
-        const int pt = idx / wc, w = idx - pt * wc;
+        const int pt = by_wc.div(idx), w = idx - pt * wc;
         line[(size_t)w * K + fft_rev(pt, logK)] = base[pt * pstride + w];
     }
     __syncthreads();
     fft_stages<INV>(line, wc, K, logK, tw);
     for (int idx = threadIdx.x; idx < K * wc; idx += blockDim.x) {
-        const int pt = idx / wc, w = idx - pt * wc;
+        const int pt = by_wc.div(idx), w = idx - pt * wc;
         base[pt * pstride + w] = line[(size_t)w * K + pt];
     }
 }
@@ -642,7 +685,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_z_inv(const float4* __restr
     for (int j = threadIdx.x; j < K / 2; j += blockDim.x) tw[j] = twg[j];
     const size_t fstride = (size_t)K * K * H;
     for (int idx = threadIdx.x; idx < nfc * K; idx += blockDim.x) {
-        const int fl = idx / K, k = idx - fl * K;
+        const int fl = idx >> logK, k = idx - (fl << logK);
         const float4* row = S + (size_t)(f0 + fl) * fstride + (size_t)xy * H;
         float4 v;
         if (k < H) {
@@ -657,8 +700,9 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_z_inv(const float4* __restr
     __syncthreads();
     fft_stages<true>(line, nfc, K, logK, tw);
     dfl* dst = R + (size_t)xy * K * nf + f0;
+    const FastDiv by_nfc(nfc);
     for (int idx = threadIdx.x; idx < K * nfc; idx += blockDim.x) {
-        const int z = idx / nfc, fl = idx - z * nfc;
+        const int z = by_nfc.div(idx), fl = idx - z * nfc;
         const float4 v = line[(size_t)fl * K + z];
         dst[(size_t)z * nf + fl] = dfl{v.x, v.y};
     }

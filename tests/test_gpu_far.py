@@ -251,11 +251,13 @@ def test_total_force_call_equals_near_plus_far():
     assert torch.equal(tot, ref)
 
 
-@pytest.mark.parametrize("K", [12, 16, 32])
+@pytest.mark.parametrize("K", [12, 16, 32, 64])
 def test_the_two_arithmetics_agree(K):
-    """K = 12: cuFFT and the FP64 product in both modes; K = 16, 32 (powers of
-    two): the double-float mode runs its own double-float transforms and
-    product, the FP64 mode cuFFT's."""
+    """K = 12: cuFFT and the FP64 product in both modes; K = 16, 32, 64 (powers
+    of two): the double-float mode runs its own double-float transforms and
+    product, the FP64 mode cuFFT's.  K = 64 splits each line pass into two
+    blocks per row (33 frequencies, 32 per block) and the z pass into three
+    field chunks."""
     import torch
     import paper_2110_11392_gb300 as nf
     from paper_2110_11392_gb300 import _lib
