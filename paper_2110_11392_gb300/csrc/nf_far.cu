@@ -33,18 +33,23 @@
 // source displacements about the cell-centre separation.  By the convolution
 // theorem each term is a product in k-space (k_far_contract) between the
 // forward transforms of D and of the multipoles; the inverse transform gives
-// T in every cell.  The FFTs are cuFFT's (a plain library transform); every
-// other step is a kernel of this file.  The per-particle work runs in cell
-// units (multipoles of the stored offsets x / w, Taylors T'^n = T^n w^{|n|});
-// the factors w^{|n|+|k|} live in the convolution's coefficients.
+// T in every cell.  The convolution runs on the (p+1)^2 reduced terms (see
+// far_tables) and the complete Taylors are rebuilt per cell
+// (k_far_rebuild).  The transforms are this file's double-float kernels
+// (k_fft_*) for a power-of-two K in double-float mode, cuFFT's FP64
+// transforms (a plain library transform) otherwise; every other step is a
+// kernel of this file.  The per-particle work runs in cell units
+// (multipoles of the stored offsets x / w, Taylors T'^n = T^n w^{|n|}); the
+// factors w^{|n|+|k|} live in the convolution's coefficients.
 //
 // Acceleration.  The potential in a cell is -m sum_n T^n x^n (G = 1), so
 // a = m sum_n T^n grad(x^n) = (m / w) sum_n T'^n grad'(x'^n), x' the
 // particle's FP32 cell-centred offset, evaluated by nested Horner schemes in
-// z, y and x (k_taylor_forces).  The derivatives, FFTs and k-space product
-// are FP64; the per-particle kernels are FP64 (k_multipoles in
-// nf_multipole.cu, k_taylor_forces) or double-float on the FP32 pipe
-// (k_multipoles_df, k_taylor_forces_df), as the caller selects.
+// z, y and x (k_taylor_forces).  The derivatives are FP64.  The rest is
+// FP64 (k_multipoles in nf_multipole.cu, k_far_reduce, cuFFT,
+// k_far_contract, k_taylor_forces) or double-float on the FP32 pipe
+// (k_multipoles_red_df, k_fft_*, k_far_contract_df, k_taylor_forces_df), as
+// the caller selects.
 #include <cuda_runtime.h>
 #include <cufft.h>
 
@@ -426,16 +431,6 @@ __device__ __forceinline__ dfl df_two_sum(float a, float b)
     const float s = __fadd_rn(a, b);
     const float bb = __fsub_rn(s, a);
     return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
-}
-
-// a * z + t for a float z
-__device__ __forceinline__ dfl df_fma_f(dfl a, float z, dfl t)
-{
-    const float p = __fmul_rn(a.h, z);
-    float e = __fmaf_rn(a.h, z, -p);
-    e = __fmaf_rn(a.l, z, e);
-    const dfl s = df_two_sum(p, t.h);
-    return df_fast(s.h, __fadd_rn(s.l, __fadd_rn(e, t.l)));
 }
 
 // a * z + t for a float z, without the final renormalisation: the result is
