@@ -86,7 +86,7 @@ def test_double_float_copy_of_derivatives(K, R, p):
 @pytest.mark.parametrize("K,R,p,N,kind", [(5, 2, 4, 3000, "uniform"), (8, 2, 8, 20000, "clustered"),
                                           (11, 2, 8, 65536, "uniform"), (7, 3, 5, 9000, "clustered"),
                                           (16, 2, 8, 40000, "clustered"), (6, 2, 1, 500, "uniform"),
-                                          (6, 1, 7, 8000, "clustered")])
+                                          (6, 1, 7, 8000, "clustered"), (4, 1, 6, 2000, "uniform")])
 def test_far_forces_match_oracle(K, R, p, N, kind, arith):
     import torch
     import paper_2110_11392_gb300 as nf
@@ -251,13 +251,14 @@ def test_total_force_call_equals_near_plus_far():
     assert torch.equal(tot, ref)
 
 
-@pytest.mark.parametrize("K", [12, 16, 32, 64])
+@pytest.mark.parametrize("K", [12, 16, 32, 64, 128])
 def test_the_two_arithmetics_agree(K):
-    """K = 12: cuFFT and the FP64 product in both modes; K = 16, 32, 64 (powers
-    of two): the double-float mode runs its own double-float transforms and
-    product, the FP64 mode cuFFT's.  K = 64 splits each line pass into two
-    blocks per row (33 frequencies, 32 per block) and the z pass into three
-    field chunks."""
+    """K = 12: cuFFT and the FP64 product in both modes; K = 16, 32, 64, 128
+    (powers of two): the double-float mode runs its own double-float
+    transforms and product, the FP64 mode cuFFT's.  K = 64 splits each line
+    pass into two blocks per row (33 frequencies, 32 per block) and the z
+    pass into three field chunks; K = 128 (the grid of the 512^3 box) into
+    five and six."""
     import torch
     import paper_2110_11392_gb300 as nf
     from paper_2110_11392_gb300 import _lib
