@@ -758,10 +758,13 @@ struct FarLayout {
 
 // The far-field regions follow the binning plan's; in debug mode each is
 // followed by a guard block like the plan's regions (appended to guards).
-// M: complete multipoles, later the rebuilt Taylors [C][nt]; Mr: reduced
-// multipoles, later the reduced Taylors [C][nr]; Mh, Th: spectra [nr][nq];
-// Tdf: double-float Taylor pairs [C][nt]; m002: each cell's (0,0,2) multipole
-// [C]; s002: partial sums of the (0,0,2) multipoles.
+// M: complete multipoles (FP64 mode), later the rebuilt FP64 Taylors [C][nt];
+// Mr: reduced multipoles, later the reduced Taylors [C][nr], 8 bytes each
+// (FP64, or a double-float pair on the double-float transform path); Mh, Th:
+// spectra [nr][nq], 16 bytes each (FP64 complex or double-float complex);
+// Tdf: double-float Taylor pairs [C][nt]; m002: each cell's (0,0,2)
+// multipole [C]; s002: partial sums of the (0,0,2) multipoles; then the
+// cuFFT work area (unused on the double-float transform path).
 FarLayout far_layout(const Plan& pl, int K, int p, std::vector<size_t>* guards = nullptr)
 {
     FarLayout F;
