@@ -504,9 +504,10 @@ __device__ __forceinline__ dfl df_from(double v)
 // k-space product the slow part of the convolution.  For power-of-two K they
 // run here in double-float on the FP32 pipe instead: a complex value is a
 // float4 {re.h, re.l, im.h, im.l}.  The 3-D real transform is three passes of
-// 1-D radix-2 transforms over lines held in shared memory (bit-reversed on
-// load, one __syncthreads per stage, twiddles e^{-2 pi i j/K} as double-float
-// pairs built on the host from FP64 cos/sin).  Layouts are cuFFT's: the real
+// 1-D transforms over lines held in shared memory (bit-reversed on load,
+// pairs of radix-2 stages done as one radix-4 step with one __syncthreads,
+// twiddles e^{-2 pi i j/K} as double-float pairs built on the host from FP64
+// cos/sin).  Layouts are cuFFT's: the real
 // side is cell-major [x][y][z][field], the spectrum term-major
 // [field][x][y][kz] with kz in 0..K/2; forward is e^{-i...}, the inverse is
 // unnormalised (the 1/K^3 sits in the k-space product).
