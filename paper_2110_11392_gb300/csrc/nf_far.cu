@@ -517,6 +517,7 @@ struct cdf {
 __device__ __forceinline__ cdf cdf_ld(float4 v) { return {dfl{v.x, v.y}, dfl{v.z, v.w}}; }
 __device__ __forceinline__ float4 cdf_st(cdf v) { return make_float4(v.re.h, v.re.l, v.im.h, v.im.l); }
 __device__ __forceinline__ dfl df_neg(dfl a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ dfl df_half(dfl a) { return {0.5f * a.h, 0.5f * a.l}; }  // exact
 __device__ __forceinline__ cdf cdf_mul(cdf w, cdf x)
 {
     return {df_fma(w.re, x.re, df_neg(df_mul(w.im, x.im))), df_fma(w.re, x.im, df_mul(w.im, x.re))};
@@ -533,8 +534,9 @@ __host__ __device__ inline int fft_lines_per_block(int K) { return K >= kFftPoin
 // in, natural order out), two radix-2 stages at a time: a thread loads four
 // points i0 + {0, h, 2h, 3h}, applies stage h (twiddle W_2h^pos on both
 // pairs) and stage 2h (W_4h^pos, and W_4h^{pos+h} = W_4h^pos * (-i)), and
-// stores them; a last radix-2 stage when log2 K is odd.  tw: e^{-2 pi i j / K},
-// j < K/2; INV uses the conjugates (and +i).
+// stores them; a last radix-2 stage when log2 K is odd.  tw: a table of
+// e^{-2 pi i j / (K 2^tws)}, j < K 2^tws / 2 (tws = 1: a K-point transform
+// using the table of twice its length); INV uses the conjugates (and +i).
 __device__ __forceinline__ cdf cdf_tw(const float4* tw, int j, bool inv)
 {
     float4 w4 = tw[j];
@@ -546,11 +548,11 @@ __device__ __forceinline__ cdf cdf_tw(const float4* tw, int j, bool inv)
 }
 
 template <bool INV>
-__device__ __forceinline__ void fft_stages(float4* line, int nl, int K, int logK, const float4* tw)
+__device__ __forceinline__ void fft_stages(float4* line, int nl, int K, int logK, const float4* tw, int tws)
 {
     int lh = 0;
     for (; lh + 1 < logK; lh += 2) {
-        const int h = 1 << lh, s1 = logK - 1 - lh, s2 = logK - 2 - lh;
+        const int h = 1 << lh, s1 = logK - 1 - lh + tws, s2 = logK - 2 - lh + tws;
         const int quarter = K >> 2;
         for (int b = threadIdx.x; b < nl * quarter; b += blockDim.x) {
             const int l = b >> (logK - 2), j = b & (quarter - 1);
@@ -573,7 +575,7 @@ __device__ __forceinline__ void fft_stages(float4* line, int nl, int K, int logK
         __syncthreads();
     }
     if (lh < logK) {  // the last stage, radix 2
-        const int h = 1 << lh, sh = logK - 1 - lh;
+        const int h = 1 << lh, sh = logK - 1 - lh + tws;
         const int half = K >> 1;
         for (int b = threadIdx.x; b < nl * half; b += blockDim.x) {
             const int l = b >> (logK - 1), j = b & (half - 1);
@@ -601,8 +603,12 @@ struct FastDiv {
 __device__ __forceinline__ int fft_rev(int i, int logK) { return logK ? (int)(__brev((unsigned)i) >> (32 - logK)) : 0; }
 
 // Forward z pass: real double-float fields, cell-major [x][y][z][nf], to the
-// spectrum S [nf][x][y][kz].  Block: one (x, y) and a chunk of fields; each
-// field's z line is transformed as a complex line with zero imaginary part.
+// spectrum S [nf][x][y][kz].  Block: one (x, y) and a chunk of fields.  Each
+// real line of K points is transformed as a complex line of M = K/2 points,
+// z[m] = x[2m] + i x[2m+1] (same line, so no mixing of fields of different
+// size); with Z its transform, the even- and odd-sample transforms are
+// E = (Z[k] + conj Z[M-k]) / 2 and O = (Z[k] - conj Z[M-k]) / 2i, and
+// X[k] = E[k] + W^k O[k], W = e^{-2 pi i/K}, for k = 0..M.
 __global__ void __launch_bounds__(kFftThreads) k_fft_z_fwd(const dfl* __restrict__ R, int K, int logK, int nf,
                                                            int nchunk, const float4* __restrict__ twg,
                                                            float4* __restrict__ S)
@@ -610,25 +616,31 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_z_fwd(const dfl* __restrict
     extern __shared__ float4 fsm[];
     float4* tw = fsm;
     float4* line = fsm + K / 2;
-    const int H = K / 2 + 1;
+    const int M = K / 2, logM = logK - 1, H = M + 1;
     const int FB = fft_lines_per_block(K);
     const int chunk = blockIdx.x % nchunk;
     const long long xy = blockIdx.x / nchunk;
     const int f0 = chunk * FB, nfc = min(FB, nf - f0);
-    for (int j = threadIdx.x; j < K / 2; j += blockDim.x) tw[j] = twg[j];
+    for (int j = threadIdx.x; j < M; j += blockDim.x) tw[j] = twg[j];
     const dfl* src = R + (size_t)xy * K * nf + f0;
+    float2* halves = reinterpret_cast<float2*>(line);  // a point's real pair, then its imaginary pair
     const FastDiv by_nfc(nfc), by_H(H);
     for (int idx = threadIdx.x; idx < K * nfc; idx += blockDim.x) {
         const int z = by_nfc.div(idx), fl = idx - z * nfc;
         const dfl v = src[(size_t)z * nf + fl];
-        line[(size_t)fl * K + fft_rev(z, logK)] = make_float4(v.h, v.l, 0.0f, 0.0f);
+        halves[2 * ((size_t)fl * M + fft_rev(z >> 1, logM)) + (z & 1)] = make_float2(v.h, v.l);
     }
     __syncthreads();
-    fft_stages<false>(line, nfc, K, logK, tw);
+    fft_stages<false>(line, nfc, M, logM, tw, 1);
     const size_t fstride = (size_t)K * K * H;
     for (int idx = threadIdx.x; idx < nfc * H; idx += blockDim.x) {
-        const int fl = by_H.div(idx), kz = idx - fl * H;
-        S[(size_t)(f0 + fl) * fstride + (size_t)xy * H + kz] = line[(size_t)fl * K + kz];
+        const int fl = by_H.div(idx), k = idx - fl * H;
+        const float4* L = line + (size_t)fl * M;
+        const cdf a = cdf_ld(L[k & (M - 1)]), b = cdf_ld(L[(M - k) & (M - 1)]);
+        const cdf e = {df_half(df_add(a.re, b.re)), df_half(df_add(a.im, df_neg(b.im)))};
+        const cdf o = {df_half(df_add(a.im, b.im)), df_half(df_add(b.re, df_neg(a.re)))};
+        const cdf x = k < M ? cdf_add(e, cdf_mul(cdf_ld(tw[k]), o)) : cdf_sub(e, o);  // W^M = -1
+        S[(size_t)(f0 + fl) * fstride + (size_t)xy * H + k] = cdf_st(x);
     }
 }
 
@@ -657,7 +669,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_lines(float4* __restrict__ 
         line[(size_t)w * K + fft_rev(pt, logK)] = base[pt * pstride + w];
     }
     __syncthreads();
-    fft_stages<INV>(line, wc, K, logK, tw);
+    fft_stages<INV>(line, wc, K, logK, tw, 0);
     for (int idx = threadIdx.x; idx < K * wc; idx += blockDim.x) {
         const int pt = by_wc.div(idx), w = idx - pt * wc;
         base[pt * pstride + w] = line[(size_t)w * K + pt];
@@ -665,7 +677,12 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_lines(float4* __restrict__ 
 }
 
 // Inverse z pass: spectrum S [nf][x][y][kz] (kz <= K/2, the rest by Hermitian
-// symmetry) to real double-float fields, cell-major [x][y][z][nf].
+// symmetry) to real double-float fields, cell-major [x][y][z][nf], through a
+// complex transform of M = K/2 points: with X[k+M] = conj X[M-k],
+// A = X[k] + X[k+M] and B = (X[k] - X[k+M]) W^{-k} are the transforms of the
+// even and odd samples, and the inverse of Z = A + i B is x[2m] + i x[2m+1]
+// (unnormalised, like the K-point inverse).  The imaginary parts at kz = 0
+// and K/2 are ignored, as a complex-to-real transform does.
 __global__ void __launch_bounds__(kFftThreads) k_fft_z_inv(const float4* __restrict__ S, int K, int logK, int nf,
                                                            int nchunk, const float4* __restrict__ twg,
                                                            dfl* __restrict__ R)
@@ -673,34 +690,40 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_z_inv(const float4* __restr
     extern __shared__ float4 fsm[];
     float4* tw = fsm;
     float4* line = fsm + K / 2;
-    const int H = K / 2 + 1;
+    const int M = K / 2, logM = logK - 1, H = M + 1;
     const int FB = fft_lines_per_block(K);
     const int chunk = blockIdx.x % nchunk;
     const long long xy = blockIdx.x / nchunk;
     const int f0 = chunk * FB, nfc = min(FB, nf - f0);
-    for (int j = threadIdx.x; j < K / 2; j += blockDim.x) tw[j] = twg[j];
+    for (int j = threadIdx.x; j < M; j += blockDim.x) tw[j] = twg[j];
+    __syncthreads();  // the pre-processing below reads the twiddles
     const size_t fstride = (size_t)K * K * H;
-    for (int idx = threadIdx.x; idx < nfc * K; idx += blockDim.x) {
-        const int fl = idx >> logK, k = idx - (fl << logK);
+    for (int idx = threadIdx.x; idx < nfc * M; idx += blockDim.x) {
+        const int fl = idx >> logM, k = idx - (fl << logM);
         const float4* row = S + (size_t)(f0 + fl) * fstride + (size_t)xy * H;
-        float4 v;
-        if (k < H) {
-            v = row[k];
-        } else {
-            v = row[K - k];
-            v.z = -v.z;
-            v.w = -v.w;
+        float4 xk = row[k], xm = row[M - k];
+        if (k == 0) {
+            xk.z = xk.w = 0.0f;
+            xm.z = xm.w = 0.0f;
         }
-        line[(size_t)fl * K + fft_rev(k, logK)] = v;
+        const cdf a = cdf_ld(xk);
+        const cdf bc = {dfl{xm.x, xm.y}, dfl{-xm.z, -xm.w}};  // X[k+M] = conj X[M-k]
+        const cdf sum = cdf_add(a, bc), dif = cdf_sub(a, bc);
+        float4 w4 = tw[k];
+        w4.z = -w4.z;
+        w4.w = -w4.w;
+        const cdf bb = cdf_mul(cdf_ld(w4), dif);
+        const cdf zz = {df_add(sum.re, df_neg(bb.im)), df_add(sum.im, bb.re)};
+        line[(size_t)fl * M + fft_rev(k, logM)] = cdf_st(zz);
     }
     __syncthreads();
-    fft_stages<true>(line, nfc, K, logK, tw);
+    fft_stages<true>(line, nfc, M, logM, tw, 1);
     dfl* dst = R + (size_t)xy * K * nf + f0;
     const FastDiv by_nfc(nfc);
     for (int idx = threadIdx.x; idx < K * nfc; idx += blockDim.x) {
         const int z = by_nfc.div(idx), fl = idx - z * nfc;
-        const float4 v = line[(size_t)fl * K + z];
-        dst[(size_t)z * nf + fl] = dfl{v.x, v.y};
+        const float4 v = line[(size_t)fl * M + (z >> 1)];
+        dst[(size_t)z * nf + fl] = (z & 1) ? dfl{v.z, v.w} : dfl{v.x, v.y};
     }
 }
 
