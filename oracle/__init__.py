@@ -18,6 +18,8 @@ binning's rounding.  Each function below cites what it follows in the paper
   Sec. "GPU Near-Field Computation").
 * :func:`adjoint` - gradient of L = sum_i g_i . a_i (not in the paper; the
   derivative of the sum above).
+* :class:`Grid` - the same two sums on a particle set binned once, for
+  several sink samples of one large set.
 * :func:`local_energy` - the part of L that depends on one particle, for
   finite differences with frozen cell assignment.
 * :func:`timestep` - the global time step of Eq. (timestep), Sec. "Time
@@ -107,6 +109,16 @@ def _load():
     lib.oracle_taylor_forces.argtypes = [P, i64, f64, i32, i32, P, P]
     lib.oracle_ewald_forces.restype = i32
     lib.oracle_ewald_forces.argtypes = [P, i64, f64, f64, i32, i32, P, i64, P]
+    lib.oracle_grid_new.restype = P
+    lib.oracle_grid_new.argtypes = [P, i64, f64, i32, i32, f64]
+    lib.oracle_grid_delete.restype = None
+    lib.oracle_grid_delete.argtypes = [P]
+    lib.oracle_grid_binning.restype = None
+    lib.oracle_grid_binning.argtypes = [P, P, P]
+    lib.oracle_grid_forces.restype = None
+    lib.oracle_grid_forces.argtypes = [P, P, i64, P, i32]
+    lib.oracle_grid_adjoint.restype = None
+    lib.oracle_grid_adjoint.argtypes = [P, P, P, i64, P, i32]
     _lib = lib
     return lib
 
@@ -188,6 +200,53 @@ def adjoint(pos, g, box: float, K: int, R: int, eps: float,
     if rc:
         raise ValueError("non-finite coordinates")
     return out[:n]
+
+
+class Grid:
+    """One particle set binned once for several sink samples.
+
+    ``Grid(pos, box, K, R, eps).forces(sinks)`` equals ``forces(pos, box, K,
+    R, eps, sinks=sinks)`` exactly (the same set-up and the same sums), and
+    likewise :meth:`adjoint`; the binning of all particles, which those
+    functions repeat on every call, is done once here.
+    """
+
+    def __init__(self, pos, box: float, K: int, R: int, eps: float):
+        self.pos = _pos(pos)
+        self.N = self.pos.shape[0]
+        self.K = int(K)
+        lib = _load()
+        self._h = lib.oracle_grid_new(_p(self.pos), self.N, float(box), self.K, int(R), float(eps))
+        if not self._h:
+            raise ValueError("non-finite coordinates (or out of memory)")
+
+    def binning(self):
+        """(cell_offsets int32[K^3+1], perm int32[N]) of the stable binning."""
+        off = np.zeros(self.K ** 3 + 1, np.int32)
+        perm = np.zeros(max(self.N, 1), np.int32)
+        _load().oracle_grid_binning(self._h, _p(off), _p(perm))
+        return off, perm[:self.N]
+
+    def forces(self, sinks: np.ndarray, threads: int = 0) -> np.ndarray:
+        s = np.ascontiguousarray(np.asarray(sinks, np.int64))
+        out = np.zeros((max(s.shape[0], 1), 3), np.float64)
+        _load().oracle_grid_forces(self._h, _p(s), s.shape[0], _p(out), int(threads))
+        return out[:s.shape[0]]
+
+    def adjoint(self, g, sinks: np.ndarray, threads: int = 0) -> np.ndarray:
+        gg = np.ascontiguousarray(np.asarray(g, np.float64).reshape(self.N, 3))
+        s = np.ascontiguousarray(np.asarray(sinks, np.int64))
+        out = np.zeros((max(s.shape[0], 1), 3), np.float64)
+        _load().oracle_grid_adjoint(self._h, _p(gg), _p(s), s.shape[0], _p(out), int(threads))
+        return out[:s.shape[0]]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _load().oracle_grid_delete(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
 
 
 def multipole_terms(p: int) -> int:

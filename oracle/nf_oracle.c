@@ -273,6 +273,18 @@ static void force_on(const oracle_grid *g, int64_t i, double out[3])
     out[2] = g->m * ctx.a[2];
 }
 
+/* Near-field accelerations of the listed sinks on a binned grid. */
+static void grid_forces(const oracle_grid *g, const int64_t *sinks, int64_t n, double *out, int nthreads)
+{
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
+#endif
+    for (int64_t q = 0; q < n; ++q) {
+        int64_t i = sinks ? sinks[q] : q;
+        force_on(g, i, &out[3 * q]);
+    }
+}
+
 /* Near-field accelerations of the `nsinks` particles listed in `sinks`
  * (or of all N particles when sinks == NULL), FP64 out[nsinks][3].
  * nthreads <= 0 uses every OpenMP thread.  Returns 0, or 1 on non-finite input. */
@@ -284,14 +296,7 @@ int oracle_forces(const float *pos, int64_t N, double box, int K, int R, double 
         oracle_grid_free(&g);
         return 1;
     }
-    int64_t n = sinks ? nsinks : N;
-#ifdef _OPENMP
-#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
-#endif
-    for (int64_t q = 0; q < n; ++q) {
-        int64_t i = sinks ? sinks[q] : q;
-        force_on(&g, i, &out[3 * q]);
-    }
+    grid_forces(&g, sinks, sinks ? nsinks : N, out, nthreads);
     oracle_grid_free(&g);
     return 0;
 }
@@ -320,6 +325,27 @@ static void adj_visit(void *vctx, int64_t j, const double d[3])
     for (int k = 0; k < 3; ++k) ctx->out[k] += f * v[k] + fr * dv * d[k];
 }
 
+/* dL/dx at the listed sinks on a binned grid. */
+static void grid_adjoint(const oracle_grid *g, const double *gvec, const int64_t *sinks, int64_t n, double *out,
+                         int nthreads)
+{
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
+#endif
+    for (int64_t q = 0; q < n; ++q) {
+        int64_t i = sinks ? sinks[q] : q;
+        adj_ctx ctx;
+        ctx.eps_s = g->eps_s;
+        ctx.g = gvec;
+        for (int k = 0; k < 3; ++k) {
+            ctx.gi[k] = gvec[3 * i + k];
+            ctx.out[k] = 0.0;
+        }
+        visit_neighbours(g, &g->cell[3 * i], &g->xw[3 * i], adj_visit, &ctx);
+        for (int k = 0; k < 3; ++k) out[3 * q + k] = g->m * ctx.out[k];
+    }
+}
+
 /* dL/dx for L = sum_i g_i . a_i, at the listed particles (or all).  g is FP64
  * [N][3] in input order; out is FP64 [nsinks][3]. */
 int oracle_adjoint(const float *pos, const double *gvec, int64_t N, double box, int K,
@@ -331,24 +357,56 @@ int oracle_adjoint(const float *pos, const double *gvec, int64_t N, double box, 
         oracle_grid_free(&g);
         return 1;
     }
-    int64_t n = sinks ? nsinks : N;
-#ifdef _OPENMP
-#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
-#endif
-    for (int64_t q = 0; q < n; ++q) {
-        int64_t i = sinks ? sinks[q] : q;
-        adj_ctx ctx;
-        ctx.eps_s = g.eps_s;
-        ctx.g = gvec;
-        for (int k = 0; k < 3; ++k) {
-            ctx.gi[k] = gvec[3 * i + k];
-            ctx.out[k] = 0.0;
-        }
-        visit_neighbours(&g, &g.cell[3 * i], &g.xw[3 * i], adj_visit, &ctx);
-        for (int k = 0; k < 3; ++k) out[3 * q + k] = g.m * ctx.out[k];
-    }
+    grid_adjoint(&g, gvec, sinks, sinks ? nsinks : N, out, nthreads);
     oracle_grid_free(&g);
     return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* A binned grid kept between calls                                           */
+/* ------------------------------------------------------------------------- */
+
+/* The same set-up as oracle_forces/oracle_adjoint (binning, cell coordinates,
+ * wrapped positions), done once so that several sink samples of one particle
+ * set can be evaluated without binning it again.  Returns NULL on non-finite
+ * input or when memory runs out. */
+void *oracle_grid_new(const float *pos, int64_t N, double box, int K, int R, double eps_p)
+{
+    oracle_grid *g = (oracle_grid *)malloc(sizeof(oracle_grid));
+    if (!g) return NULL;
+    if (oracle_grid_init(g, pos, N, box, K, R, eps_p) || !g->offsets || !g->order || !g->cell || !g->xw) {
+        oracle_grid_free(g);
+        free(g);
+        return NULL;
+    }
+    return g;
+}
+
+void oracle_grid_delete(void *g)
+{
+    if (!g) return;
+    oracle_grid_free((oracle_grid *)g);
+    free(g);
+}
+
+/* Cell offsets [K^3 + 1] and sorted slot -> original index [N] of the grid. */
+void oracle_grid_binning(const void *vg, int32_t *offsets, int32_t *order)
+{
+    const oracle_grid *g = (const oracle_grid *)vg;
+    const int64_t ncell = (int64_t)g->K * g->K * g->K;
+    memcpy(offsets, g->offsets, sizeof(int32_t) * (size_t)(ncell + 1));
+    memcpy(order, g->order, sizeof(int32_t) * (size_t)g->N);
+}
+
+void oracle_grid_forces(const void *g, const int64_t *sinks, int64_t nsinks, double *out, int nthreads)
+{
+    grid_forces((const oracle_grid *)g, sinks, nsinks, out, nthreads);
+}
+
+void oracle_grid_adjoint(const void *g, const double *gvec, const int64_t *sinks, int64_t nsinks, double *out,
+                         int nthreads)
+{
+    grid_adjoint((const oracle_grid *)g, gvec, sinks, nsinks, out, nthreads);
 }
 
 /* ------------------------------------------------------------------------- */

@@ -556,3 +556,24 @@ def test_multipoles_match_numpy_powers():
         ref = np.bincount(cid, weights=mono, minlength=K ** 3)
         scale = np.bincount(cid, weights=np.abs(mono), minlength=K ** 3) + 1e-300
         assert np.all(np.abs(M[:, t] - ref) <= 1e-13 * scale)
+
+
+def test_grid_equals_the_one_shot_functions():
+    # oracle.Grid bins once and reuses the binning; its sums must be the one-shot
+    # functions' exactly (same set-up, same arithmetic), and its binning the
+    # stable binning of bin_particles.
+    from workloads import config_plain, upstream_gradient
+    w = config_plain(N=6000, K=6)
+    g = upstream_gradient(w.N, 5)
+    grid = oracle.Grid(w.pos, w.box, w.K, w.R, w.eps)
+    sk = np.arange(0, w.N, 5)
+    assert np.array_equal(grid.forces(sk), oracle.forces(w.pos, w.box, w.K, w.R, w.eps, sinks=sk))
+    assert np.array_equal(grid.adjoint(g, sk), oracle.adjoint(w.pos, g, w.box, w.K, w.R, w.eps, sinks=sk))
+    off, perm = grid.binning()
+    off_o, _, perm_o = oracle.bin_particles(w.pos, w.box, w.K)
+    assert np.array_equal(off, off_o) and np.array_equal(perm, perm_o)
+    grid.close()
+    bad = w.pos.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(ValueError):
+        oracle.Grid(bad, w.box, w.K, w.R, w.eps)
