@@ -185,3 +185,71 @@ def test_paper_ewald_configuration():
     med, p99 = np.median(fe), np.percentile(fe, 99)
     assert _paper("ewald_median_err") / 2 < med < 2 * 1.2e-5
     assert _paper("ewald_p99_err") / 2 < p99 < 2 * 1.6e-4
+
+
+def _closed_form_coulomb(r, a, b, c):
+    """d^a/dx^a d^b/dy^b d^c/dz^c of 1/|r| for a + b + c <= 3, from the
+    textbook tensors: 1/r; -x_i/r^3; 3 x_i x_j/r^5 - delta_ij/r^3;
+    -15 x_i x_j x_k/r^7 + 3 (delta_ij x_k + delta_ik x_j + delta_jk x_i)/r^5."""
+    x = np.asarray(r, np.float64)
+    d = float(np.linalg.norm(x))
+    ax = [0] * a + [1] * b + [2] * c
+    dl = lambda i, j: 1.0 if i == j else 0.0
+    if len(ax) == 0:
+        return 1.0 / d
+    if len(ax) == 1:
+        return -x[ax[0]] / d ** 3
+    if len(ax) == 2:
+        i, j = ax
+        return 3 * x[i] * x[j] / d ** 5 - dl(i, j) / d ** 3
+    i, j, k = ax
+    return (-15 * x[i] * x[j] * x[k] / d ** 7
+            + 3 * (dl(i, j) * x[k] + dl(i, k) * x[j] + dl(j, k) * x[i]) / d ** 5)
+
+
+POINTS = [(0.7, -0.4, 0.3), (-1.3, 0.2, 2.1), (0.05, 0.9, -0.6)]
+
+
+@pytest.mark.parametrize("r", POINTS)
+def test_coulomb_derivatives_low_orders_equal_closed_forms(r):
+    # Orders 0..3 of the derivatives of 1/r against the textbook tensors
+    # (a route that shares nothing with the Hermite recursion).
+    p = 3
+    D = oracle.coulomb_derivatives(p, r)
+    for q, (a, b, c) in enumerate(oracle.multipole_index(p)):
+        ref = _closed_form_coulomb(r, a, b, c)
+        assert abs(D[q] - ref) <= 1e-13 * max(1.0, abs(ref)) * np.linalg.norm(r) ** -(1 + a + b + c), \
+            ((a, b, c), D[q], ref)
+
+
+@pytest.mark.parametrize("r", POINTS)
+def test_coulomb_derivatives_each_order_differentiates_the_one_below(r):
+    # Orders 4..p: every term must be the derivative, along one of its axes, of
+    # the term one order below, taken by fourth-order central differences of
+    # the oracle's own lower-order values.  With orders <= 3 pinned to the
+    # closed forms this pins every order of the recursion.
+    p = 10
+    h = 1e-3
+    wh_lo = _where(p - 1)
+    idx = oracle.multipole_index(p)
+    D = oracle.coulomb_derivatives(p, r)
+    x = np.asarray(r, np.float64)
+    steps = {}
+    for ax in range(3):
+        e = np.zeros(3)
+        e[ax] = h
+        steps[ax] = [oracle.coulomb_derivatives(p - 1, x + s * e) for s in (2, 1, -1, -2)]
+    d = float(np.linalg.norm(x))
+    for q, t in enumerate(idx):
+        m = sum(t)
+        if m < 4:
+            continue
+        for ax in range(3):
+            if t[ax] == 0:
+                continue
+            lo = list(t)
+            lo[ax] -= 1
+            f2, f1, m1, m2 = (v[wh_lo[tuple(lo)]] for v in steps[ax])
+            fd = (-f2 + 8 * f1 - 8 * m1 + m2) / (12 * h)
+            scale = d ** -(m + 1) * np.prod([float(k) for k in range(1, m + 1)])  # |D^m| <= m!/r^(m+1)
+            assert abs(D[q] - fd) <= 2e-7 * scale, (t, ax, D[q], fd)
