@@ -4,7 +4,9 @@ blocks per SM).
 Each candidate is timed on the caller's workload through ``nf_forces_batched``
 (or its adjoint) with CUDA events on the current stream; the fastest one is
 returned and cached in a JSON file keyed by GPU name, direction and a coarse
-problem class (particles per box and boxes), so later runs reuse it.
+problem class (particles per box and boxes), so later runs reuse it.  A cached
+record is used only when it was measured over the same candidate list.
+``BatchedNearField(tune="auto")`` runs this search before its first launch.
 """
 from __future__ import annotations
 
@@ -53,12 +55,13 @@ def tune(boxes: Sequence[dict], pos: torch.Tensor, adjoint: bool = False, g: Opt
     """Best tuning for this batch (pos packed as in nf_forces_batched) and the timings (ms)."""
     dev = pos.device
     key = f"{torch.cuda.get_device_name(dev)}|{problem_class(boxes, adjoint)}"
+    cand_list = [list(map(int, t)) for t in candidates]
     if cache and not refresh and os.path.exists(cache):
         try:
             rec = json.load(open(cache)).get(key)
-            if rec:
+            if rec and rec.get("candidates") == cand_list:
                 return tuple(rec["best"]), rec["ms"]
-        except (OSError, ValueError):
+        except (OSError, ValueError, AttributeError):
             pass
     arr = _lib.make_boxes(boxes)
     ws = torch.empty(_lib.nf_workspace_bytes_batched(boxes), dtype=torch.uint8, device=dev)
@@ -80,7 +83,7 @@ def tune(boxes: Sequence[dict], pos: torch.Tensor, adjoint: bool = False, g: Opt
             data = json.load(open(cache)) if os.path.exists(cache) else {}
         except (OSError, ValueError):
             data = {}
-        data[key] = {"best": list(best_t), "ms": timings}
+        data[key] = {"best": list(best_t), "ms": timings, "candidates": cand_list}
         try:
             with open(cache, "w") as fh:
                 json.dump(data, fh, indent=1)

@@ -197,15 +197,25 @@ class BatchedNearField:
     """Many independent boxes in one pass (nf_forces_batched), optionally as a CUDA graph.
 
     boxes: list of dicts with N, K, R, eps, box (packed back to back in pos_cat).
-    tune: (sinks_per_lane, stage, warps_per_block, blocks_per_sm) or None.
+    tune: (sinks_per_lane, stage, warps_per_block, blocks_per_sm), None for the
+    library default, or "auto": the autotuner (autotune.tune, cached in
+    tune_cache; None = always measure) picks the tuning on the first call's
+    positions, before any graph capture; the pick is in .tune and the
+    candidates' times in .tune_timings.
     """
 
-    def __init__(self, boxes: Sequence[dict], device=None, tune=None, net: bool = False):
+    def __init__(self, boxes: Sequence[dict], device=None, tune=None, net: bool = False,
+                 tune_cache: Optional[str] = "default"):
         self.device = torch.device(device if device is not None else "cuda")
         self.boxes = [dict(b) for b in boxes]
         self.arr = _lib.make_boxes(self.boxes)
         self.N = sum(int(b["N"]) for b in self.boxes)
-        self.tune = tune
+        self._auto = isinstance(tune, str) and tune == "auto"
+        if isinstance(tune, str) and not self._auto:
+            raise ValueError(f"tune must be a tuple, None or 'auto', not {tune!r}")
+        self.tune = None if self._auto else tune
+        self.tune_timings = None
+        self.tune_cache = tune_cache
         nbytes = _lib.nf_workspace_bytes_batched(self.boxes)
         if nbytes == 0:
             raise ValueError("invalid batch: " + _lib.nf_last_error())
@@ -218,17 +228,26 @@ class BatchedNearField:
     def _launch(self):
         _lib.nf_forces_batched(self.arr, self.pos, self.acc, self.net, self.tune, self.ws)
 
+    def _ensure_tuned(self):
+        if self._auto and self.tune is None:
+            from . import autotune
+            cache = autotune.DEFAULT_CACHE if self.tune_cache == "default" else self.tune_cache
+            self.tune, self.tune_timings = autotune.tune(self.boxes, self.pos, cache=cache)
+
     def __call__(self, pos_cat: Optional[torch.Tensor] = None) -> torch.Tensor:
         if pos_cat is not None:
             self.pos.copy_(pos_cat)
         if self.graph is not None:
             self.graph.replay()
         else:
+            self._ensure_tuned()
             self._launch()
         return self.acc
 
     def capture(self) -> "BatchedNearField":
-        """Record one batched call into a CUDA graph (replayed by __call__)."""
+        """Record one batched call into a CUDA graph (replayed by __call__).
+        With tune="auto" the search runs first, on the positions held now."""
+        self._ensure_tuned()
         s = torch.cuda.Stream(device=self.device)
         s.wait_stream(torch.cuda.current_stream(self.device))
         with torch.cuda.stream(s):
