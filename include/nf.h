@@ -112,8 +112,10 @@ int nf_bin(const float *pos, int64_t N, double box, int K,
  *        (2R+1)^3 cells around i's cell (j = i included; it adds 0).
  *   net  [3] FP64 (output) or NULL: sum_i (1/N) a_i of the FP32 results,
  *        accumulated in FP64 (zero up to roundoff by Newton's third law).
- * The pair arithmetic runs in FP32 on cell-relative coordinates; the partial
- * sums of the 2R+1 pencils that reach each particle are added in FP64. */
+ * The pair arithmetic runs in FP32 on cell-relative coordinates.  The 2R+1
+ * pencil partial sums that reach each particle are added without rounding
+ * error into an FP32 (hi, lo) pair (a TwoSum cascade), multiplied by the box
+ * scale m/w^2 held as a float pair, and rounded once to FP32. */
 int nf_forces(const float *pos, int64_t N, double box, int K, int R, double eps,
               float *acc, double *net, void *ws, size_t ws_bytes, void *stream);
 
@@ -456,7 +458,8 @@ int nf_stats_read(void *ws, int64_t *out, void *stream);
  *   bin_ms       cell ids, offsets, radix sort, cell-centred offsets;
  *   worklist_ms  pencil sizes, cost order, work items (and the gather of g);
  *   pair_ms      the persistent force or adjoint kernel alone;
- *   combine_ms   FP64 combine of the partial sums and scatter (and net force);
+ *   combine_ms   combine of the partial sums (error-free FP32 TwoSum), scatter
+ *                and the FP64 net force;
  *   total_ms     first event to last. */
 typedef struct {
     double bin_ms;
@@ -498,23 +501,6 @@ int nf_far_profile_read(int back, nf_far_profile *out);
 /* Number of kernels libnf has launched in this process (all entry points). */
 int64_t nf_kernel_launches(void);
 
-/* ---- Measurement aid (no counterpart in the paper) ----------------------
- * Multiply-add throughput probe, the measured denominator beside the derived
- * peaks of the rooflines: FP32 for the pair kernels (SMs x 128 lanes x 2 flop
- * x clock), FP64 for the far field.  Launches one kernel of 4 blocks of 256
- * threads per SM; every thread runs 8 independent multiply-add chains for
- * iters x 16 trips, as scalar fma.rn.f32 (mode 0), packed fma.rn.f32x2
- * (mode 1) or fma.rn.f64 (mode 2).
- *   sink   device float buffer of at least nf_fma_probe_sink_floats() values,
- *          caller-owned; receives one value per thread (keeps the work live)
- *   iters  1 .. 2^24
- *   flop   host double; receives the floating-point operations the launch
- *          performs (2 per multiply-add and lane)
- * The call is asynchronous on `stream`; time it with events on that stream.
- * Returns NF_ERR_ARG for NULL pointers, iters out of range or another mode,
- * NF_ERR_CUDA if the launch fails. */
-size_t nf_fma_probe_sink_floats(void);
-int nf_fma_probe(float *sink, int iters, int mode, double *flop, cudaStream_t stream);
 
 #ifdef __cplusplus
 }

@@ -16,7 +16,10 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libnf.so")
-SOURCES = ["nf_bin.cu", "nf_force.cu", "nf_step.cu", "nf_multipole.cu", "nf_far.cu", "nf_probe.cu", "nf_api.cu"]
+SOURCES = ["nf_bin.cu", "nf_force.cu", "nf_step.cu", "nf_multipole.cu", "nf_far.cu", "nf_api.cu"]
+# the benchmark's multiply-add probe: a library of its own, not part of libnf
+PROBE_SRC = os.path.join(CSRC, "probe", "fma_probe.cu")
+PROBE_LIB = os.path.join(PKG, "libnf_probe.so")
 HEADERS = ["nf_internal.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 LINK_LIBS = ["-lcufft"]  # the far field's 3-D FFTs
@@ -74,6 +77,17 @@ def build_library(force: bool = False, verbose: bool = False, extra_flags: List[
     subprocess.check_call([cc, "-shared", *ARCH, "-o", tmp, *objs, *LINK_LIBS, *rpath])
     os.replace(tmp, LIB)
     return LIB
+
+
+def build_probe(force: bool = False) -> str:
+    """Compile and link the multiply-add probe library (libnf_probe.so)."""
+    if not force and os.path.exists(PROBE_LIB) and os.path.getmtime(PROBE_LIB) >= os.path.getmtime(PROBE_SRC):
+        return PROBE_LIB
+    cc = nvcc()
+    tmp = PROBE_LIB + f".{os.getpid()}.tmp"
+    subprocess.check_call([cc, *NVCC_FLAGS, *ARCH, "-shared", "-o", tmp, PROBE_SRC])
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
 
 
 if __name__ == "__main__":

@@ -107,8 +107,6 @@ def load(build: bool = True) -> ctypes.CDLL:
         "nf_kdk_step_far": (i32, [P, P, P, i64, f64, i32, i32, f64, i32, P, sz, P, P, P, sz, P, sz, P]),
         "nf_set_debug": (i32, [i32]),
         "nf_debug_check": (i32, [P, P]),
-        "nf_fma_probe_sink_floats": (sz, []),
-        "nf_fma_probe": (i32, [P, i32, i32, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -127,8 +125,7 @@ def exported_symbols() -> Sequence[str]:
             "nf_kdk_step", "nf_multipoles", "nf_set_debug", "nf_debug_check",
             "nf_derivatives_bytes", "nf_far_workspace_bytes", "nf_derivatives", "nf_far_forces",
             "nf_far_profile_read", "nf_far_release", "nf_kdk_step_far", "nf_forces_total",
-            "nf_far_set_arith", "nf_far_get_arith",
-            "nf_fma_probe_sink_floats", "nf_fma_probe")
+            "nf_far_set_arith", "nf_far_get_arith")
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -279,21 +276,6 @@ def nf_far_profile_read(back: int = 0) -> dict:
 
 def nf_kernel_launches() -> int:
     return int(load().nf_kernel_launches())
-
-
-def nf_fma_probe_sink_floats() -> int:
-    return int(load().nf_fma_probe_sink_floats())
-
-
-def nf_fma_probe(sink: torch.Tensor, iters: int, mode, stream=None) -> float:
-    """Launches the multiply-add probe (mode 0 f32, 1 f32x2, 2 f64; a bool
-    selects 0 or 1); returns the flop count of the launch."""
-    if sink.dtype != torch.float32 or not sink.is_cuda or sink.numel() < nf_fma_probe_sink_floats():
-        raise ValueError("sink must be a CUDA float32 tensor of nf_fma_probe_sink_floats() values")
-    flop = ctypes.c_double(0.0)
-    _check(load().nf_fma_probe(_ptr(sink), int(iters), int(mode), ctypes.byref(flop), _stream(stream)),
-           "nf_fma_probe")
-    return flop.value
 
 
 def nf_forces_noalloc(pos: torch.Tensor, box: float, K: int, R: int, eps: float, acc: torch.Tensor,

@@ -1273,18 +1273,6 @@ int nf_profile_read(int back, nf_profile* out)
 
 int64_t nf_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
-size_t nf_fma_probe_sink_floats(void) { return nf::fma_probe_sink_floats(); }
-
-int nf_fma_probe(float* sink, int iters, int mode, double* flop, cudaStream_t stream)
-{
-    g_last_error.clear();
-    if (!sink || !flop) return fail(NF_ERR_ARG, "nf_fma_probe: sink and flop must be non-NULL");
-    if (iters < 1 || iters > (1 << 24)) return fail(NF_ERR_ARG, "nf_fma_probe: iters %d outside [1, 2^24]", iters);
-    if (mode < 0 || mode > 2) return fail(NF_ERR_ARG, "nf_fma_probe: mode %d is not 0, 1 or 2", mode);
-    const cudaError_t e = nf::launch_fma_probe(sink, iters, mode, flop, stream);
-    return e == cudaSuccess ? NF_OK : cuda_fail(e, "nf_fma_probe");
-}
-
 int nf_stats_read(void* ws, int64_t* out, void* stream)
 {
     g_last_error.clear();

@@ -11,7 +11,8 @@
 // A sink in cell (x, j, k) meets source cell (x+a, j+b, k+d) in the item
 // centred at x+a, with partial slot c = -a + R.  Every (sink, source-cell)
 // pair of the (2R+1)^3 stencil is therefore computed exactly once, and each
-// sink gets 2R+1 partial sums, one per slot, which k_combine adds in FP64.
+// sink gets 2R+1 partial sums, one per slot, which k_combine adds without
+// rounding error (an FP32 TwoSum cascade into a hi/lo pair).
 // Coordinates are cell-relative FP32 offsets shifted into the frame of the
 // item's centre cell (the paper's pencil-centred coordinates, Sec.
 // "Pencil-on-Pencil"), so the periodic wrap costs nothing in the pair loop.
@@ -806,7 +807,9 @@ k_force(const BoxDev* __restrict__ boxes, const int* __restrict__ off, const flo
 }
 
 // ---------------------------------------------------------------------------
-// Combine: sum the 2R+1 partials in FP64, scale, scatter to input order
+// Combine: sum the 2R+1 partials without rounding error (FP32 TwoSum into a
+// hi/lo pair), scale by a float-pair constant, round once, scatter to input
+// order; the optional net force is an FP64 sum
 // ---------------------------------------------------------------------------
 
 // Error-free sum of two floats: s + e == a + b exactly (Knuth's TwoSum).

@@ -178,9 +178,6 @@ cudaError_t launch_taylor_forces(int p, const int* off, const float4* rel, const
                                  double mass, double* acc_far, float* acc_add, cudaStream_t s);
 
 // Counts kernel launches (all translation units).
-// multiply-add throughput probe (measurement aid); mode 0 f32, 1 f32x2, 2 f64
-size_t fma_probe_sink_floats();
-cudaError_t launch_fma_probe(float* sink, int iters, int mode, double* flop, cudaStream_t s);
 void count_launches(int n);
 // Sets the dynamic shared-memory limit of a kernel once per (device, size).
 cudaError_t ensure_smem(const void* fn, int bytes);

@@ -1,4 +1,4 @@
-"""nf_fma_probe: the FP32 multiply-add probe behind the measured roofline denominator."""
+"""The benchmark's multiply-add probe (libnf_probe.so): flop count and values."""
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -7,13 +7,13 @@ pytestmark = pytest.mark.gpu
 @pytest.mark.parametrize("packed,chains", [(0, 8), (1, 16), (2, 8)])
 def test_probe_values_and_flop_count(packed, chains):
     import torch
-    from paper_2110_11392_gb300 import _lib
-    n = _lib.nf_fma_probe_sink_floats()
+    from paper_2110_11392_gb300 import probe
+    n = probe.sink_floats()
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     assert n == sms * 4 * 256
     sink = torch.full((n,), float("nan"), dtype=torch.float32, device="cuda")
     iters = 2048
-    flop = _lib.nf_fma_probe(sink, iters, packed)
+    flop = probe.fma_probe(sink, iters, packed)
     torch.cuda.synchronize()
     # n threads x iters x 16 trips x 8 chains x (2 lanes if packed) x 2 flop
     assert flop == n * iters * 16 * 8 * (2 if packed == 1 else 1) * 2
@@ -23,12 +23,12 @@ def test_probe_values_and_flop_count(packed, chains):
 
 def test_probe_rejects_bad_arguments():
     import torch
-    from paper_2110_11392_gb300 import _lib
+    from paper_2110_11392_gb300 import probe
     small = torch.empty(8, dtype=torch.float32, device="cuda")
     with pytest.raises(ValueError):
-        _lib.nf_fma_probe(small, 16, True)
-    sink = torch.empty(_lib.nf_fma_probe_sink_floats(), dtype=torch.float32, device="cuda")
-    with pytest.raises(_lib.NFError):
-        _lib.nf_fma_probe(sink, 0, True)
-    with pytest.raises(_lib.NFError):
-        _lib.nf_fma_probe(sink, 16, 3)
+        probe.fma_probe(small, 16, True)
+    sink = torch.empty(probe.sink_floats(), dtype=torch.float32, device="cuda")
+    with pytest.raises(ValueError):
+        probe.fma_probe(sink, 0, True)
+    with pytest.raises(ValueError):
+        probe.fma_probe(sink, 16, 3)
