@@ -185,14 +185,16 @@ class ClockSampler:
 
 def sample_cells(off: np.ndarray, perm: np.ndarray, frac: float, seed: int = 22):
     """A fixed random sample of sink cells (a fraction `frac` of all cells, seed
-    `seed`) and the particles in them, in increasing index order."""
+    `seed`) and the particles in them, listed cell by cell (the oracle then
+    visits the same neighbour cells for consecutive sinks, which keeps its
+    memory accesses local; the sums do not depend on the order)."""
     C = off.shape[0] - 1
     counts = np.diff(off)
     rng = np.random.default_rng(seed)
     cells = np.sort(rng.choice(C, max(1, int(round(frac * C))), replace=False))
     mask = np.zeros(C, bool)
     mask[cells] = True
-    sinks = np.sort(perm[np.repeat(mask, counts)]).astype(np.int64)
+    sinks = perm[np.repeat(mask, counts)].astype(np.int64)
     return cells, sinks
 
 
@@ -229,7 +231,7 @@ def oracle_sample(w, g, frac: float = 0.01, seed: int = 22, one_core_s: float = 
     nc = int(min(len(cells), max(1, np.searchsorted(csum, want) + 1)))
     m1 = np.zeros(w.K ** 3, bool)
     m1[cells[:nc]] = True
-    sk1 = np.sort(perm[np.repeat(m1, counts)]).astype(np.int64)
+    sk1 = perm[np.repeat(m1, counts)].astype(np.int64)
     t0 = time.perf_counter()
     grid.forces(sk1, threads=1)
     grid.adjoint(g64, sk1, threads=1)
@@ -237,7 +239,7 @@ def oracle_sample(w, g, frac: float = 0.01, seed: int = 22, one_core_s: float = 
     pairs1 = 2 * int(csum[nc - 1])
     grid.close()
     return ({"value": pairs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-             "sample": f"forces + adjoint of all {len(sinks)} particles in a fixed random 1 % of the sink cells "
+             "sample": f"forces + adjoint of all {len(sinks)} particles (listed cell by cell) in a fixed random 1 % of the sink cells "
                        f"({len(cells)} of {w.K ** 3}, seed {seed}); {pairs:.4e} pair interactions in {dt:.1f} s "
                        f"(forces {t_fwd:.1f} s, adjoint {t_adj:.1f} s), FP64, OpenMP; binning once before "
                        f"({setup_s:.1f} s, not in the rate)",
@@ -929,7 +931,7 @@ def run_reference(args, rank, world):
         cells = np.sort(rng.choice(C, n_cells, replace=False))
         mask = np.zeros(C, bool)
         mask[cells] = True
-        sk = np.sort(perm[np.repeat(mask, counts)]).astype(np.int64)
+        sk = perm[np.repeat(mask, counts)].astype(np.int64)  # cell by cell
         t0 = time.perf_counter()
         grid.forces(sk)
         grid.adjoint(g64, sk)
@@ -947,7 +949,7 @@ def run_reference(args, rank, world):
     grid.close()
     value = sum(pairs) / sum(times)
     sample = (f"forces + adjoint of every particle in {n_cells} random sink cells of {C} per step (fresh cells "
-              f"each step, about {int(np.mean(sizes))} particles), FP64; the particle set binned once before "
+              f"each step, about {int(np.mean(sizes))} particles, listed cell by cell), FP64; the particle set binned once before "
               f"the steps ({setup_s:.1f} s, not timed per step)")
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
