@@ -130,10 +130,10 @@ struct Plan {
     int max_R = 1;
     int max_nseg = 9;
     int nchunks = 0;     // combine chunks
-    RadixPlan rx{};
+    SortPlan sp{};
     std::vector<BoxDev> boxes;
     // region offsets (bytes from ws)
-    size_t o_boxes, o_keys_a, o_keys_b, o_vals_a, o_vals_b, o_off, o_hist, o_aux, o_rel, o_perm,
+    size_t o_boxes, o_keys_a, o_keys_b, o_rel_scratch, o_sort, o_off, o_rel, o_perm,
         o_chunks, o_bucket_of, o_bucket_count, o_items, o_gs, o_partial, o_chunk_sums, o_step, total;
     std::vector<size_t> guards;  // debug mode: guard block after each region
 };
@@ -228,7 +228,7 @@ int make_plan(const nf_box* boxes, int nboxes, bool need_force, int chunk_lanes,
     p->max_R = max_R;
     p->max_nseg = (2 * max_R + 1) * (2 * max_R + 1);
     p->nchunks = (int)nchunks;
-    p->rx = radix_plan(N, C);
+    p->sp = sort_plan(N, C);
 
     size_t o = 0;
     p->guards.clear();
@@ -245,13 +245,9 @@ int make_plan(const nf_box* boxes, int nboxes, bool need_force, int chunk_lanes,
     p->o_boxes = take(sizeof(BoxDev) * nboxes);
     p->o_keys_a = take(4 * (size_t)N);
     p->o_keys_b = take(4 * (size_t)N);
-    p->o_vals_a = take(4 * (size_t)N);
-    p->o_vals_b = take(4 * (size_t)N);
+    p->o_rel_scratch = take(p->sp.passes > 1 ? 16 * (size_t)N : 16);
+    p->o_sort = take(sort_ctl_bytes(p->sp));
     p->o_off = take(4 * (size_t)(C + 1));
-    p->o_hist = take(4 * radix_hist_words(p->rx));
-    size_t aux = scan_aux_words((size_t)C + 1);
-    size_t aux2 = scan_aux_words(radix_hist_words(p->rx));
-    p->o_aux = take(4 * (aux > aux2 ? aux : aux2));
     p->o_rel = take(16 * (size_t)N);
     p->o_perm = take(4 * (size_t)N);
     p->o_step = take(sizeof(StepScratch));
@@ -333,7 +329,6 @@ int run_binning(const Plan& p, const float* pos, void* ws, int32_t* cell_off, fl
     BoxDev* boxes = at<BoxDev>(ws, p.o_boxes);
     int rc = init_ws(p, ws, s);
     if (rc) return rc;
-    NF_CUDA(cudaMemsetAsync(cell_off, 0, 4 * (size_t)(p.C + 1), s), "clear counts");
     for (int first = 0; first < p.nboxes; first += kMaxBoxesPerFill) {
         BoxFill f;
         std::memset(&f, 0, sizeof f);
@@ -342,14 +337,10 @@ int run_binning(const Plan& p, const float* pos, void* ws, int32_t* cell_off, fl
         for (int q = 0; q < f.count; ++q) f.b[q] = p.boxes[first + q];
         NF_CUDA(launch_fill_boxes(f, boxes, s), "box table");
     }
-    int* keys_a = at<int>(ws, p.o_keys_a);
-    NF_CUDA(launch_shift(pos, (int)p.N, boxes, p.nboxes, keys_a, cell_off, hdr, s), "cell ids");
-    NF_CUDA(launch_scan(reinterpret_cast<unsigned*>(cell_off), (size_t)p.C + 1, at<unsigned>(ws, p.o_aux), s),
-            "cell offsets");
-    NF_CUDA(radix_sort(p.rx, (int)p.N, keys_a, at<int>(ws, p.o_keys_b), at<int>(ws, p.o_vals_a),
-                       at<int>(ws, p.o_vals_b), perm, at<unsigned>(ws, p.o_hist), at<unsigned>(ws, p.o_aux), s),
-            "radix sort");
-    NF_CUDA(launch_rel(pos, (int)p.N, boxes, p.nboxes, perm, rel, s), "offsets");
+    NF_CUDA(run_sort(p.sp, pos, (int)p.N, (int)p.C, boxes, p.nboxes, at<void>(ws, p.o_sort),
+                     at<float4>(ws, p.o_rel_scratch), at<int>(ws, p.o_keys_a), at<int>(ws, p.o_keys_b), rel, perm,
+                     cell_off, hdr, s),
+            "binning sort");
     return NF_OK;
 }
 

@@ -1,23 +1,32 @@
-// Binning: cell ids, cell offsets, stable LSD radix sort, cell-centred offsets.
+// Binning: cell ids, cell offsets and cell-centred offsets in grid order.
 //
 // The paper stores particles in grid order with FP32 positions relative to
 // the cell centre (Sec. "Force Accuracy", overview) on a K^3 grid of cells
-// (Sec. "Two-Stage Execution").  Here the grid order comes from a stable sort
-// by cell id done on the GPU:
-//   k_shift      FP64 shift of every coordinate into cell units, cell id, and
-//                an atomic histogram of cells (counts are order-independent);
-//   scan         exclusive prefix sum -> cell_offsets;
-//   radix passes stable LSD radix sort of (cell id, particle) with <= 2048
-//                bins per pass: per-tile histograms, a scan of the
-//                (bin, tile) matrix, then a stable scatter in which each warp
-//                ranks its own elements in order with __match_any_sync;
-//   k_rel        recomputes each sorted particle's offsets from its position.
+// (Sec. "Two-Stage Execution").  Here the grid order comes from a stable
+// least-significant-digit sort of (cell id, particle) done on the GPU, with
+// digits of at most 9 bits (one pass for K <= 8, two for K <= 32, three for
+// K <= 128):
+//   k_bin_hist   reads every position once, computes its cell id (FP64 rule
+//                below) and the global histogram of every pass's digit;
+//   k_sort_pass  one stable pass over tiles of 2048 particles: the first
+//                pass computes each particle's cell id and cell-centred
+//                offsets from its position, later passes read them back; a
+//                tile ranks its particles by digit in input order (each warp
+//                ranks its own consecutive elements with __match_any_sync),
+//                finds where its runs go by a decoupled look-back over the
+//                tiles before it (bounded waits), reorders the tile in shared
+//                memory and writes every run contiguously.  The offsets travel
+//                with the particle (float4, .w = original index), so no pass
+//                gathers positions at random;
+//   k_cell_off   cell_offsets from the sorted cell ids (the first slot of
+//                every cell; empty cells get the next cell's first slot).
 // The FP64 shift uses explicitly rounded intrinsics so that no FMA
 // contraction changes the rounding: the result is bit-identical to the plain
 // CPU definition (t = x * (K/box), c = floor(t), offset = fp32((t - c) - 1/2),
 // cell = c mod K).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 
 #include "nf_internal.cuh"
@@ -107,47 +116,41 @@ __global__ void k_fill_boxes(BoxFill f, BoxDev* boxes)
     if (i < f.count) boxes[f.first + i] = f.b[i];
 }
 
-__global__ void k_shift(const float* __restrict__ pos, int Ntot, const BoxDev* __restrict__ boxes,
-                        int nboxes, int* __restrict__ keys, int* __restrict__ counts,
-                        WsHeader* hdr)
+// Cell id (global: cell_base + local id) and cell-centred offsets of particle e.
+__device__ __forceinline__ int particle_key(const float* __restrict__ pos, int e, const BoxDev* __restrict__ boxes,
+                                           int nboxes, float4* rel, bool* bad)
 {
+    const BoxDev& B = boxes[nboxes > 1 ? find_box(boxes, nboxes, e) : 0];
+    float4 r;
+    const int cx = cell_coord(pos[3 * (size_t)e + 0], B, &r.x, bad);
+    const int cy = cell_coord(pos[3 * (size_t)e + 1], B, &r.y, bad);
+    const int cz = cell_coord(pos[3 * (size_t)e + 2], B, &r.z, bad);
+    r.w = __int_as_float(e);
+    *rel = r;
+    return B.cell_base + (cx * B.K + cy) * B.K + cz;
+}
+
+// Global histogram of every pass's digit (shared-memory partial histograms,
+// one atomic per bin and block at the end); flags non-finite input.
+__global__ void __launch_bounds__(256)
+k_bin_hist(const float* __restrict__ pos, int N, const BoxDev* __restrict__ boxes, int nboxes, SortPlan sp,
+           unsigned* __restrict__ ghist, WsHeader* hdr)
+{
+    __shared__ unsigned h[kSortMaxPasses][kSortMaxBins];
+    for (int i = threadIdx.x; i < kSortMaxPasses * kSortMaxBins; i += blockDim.x) (&h[0][0])[i] = 0u;
+    __syncthreads();
     bool bad = false;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Ntot; e += gridDim.x * blockDim.x) {
-        const BoxDev& B = boxes[find_box(boxes, nboxes, e)];
-        float o;
-        int cx = cell_coord(pos[3 * (size_t)e + 0], B, &o, &bad);
-        int cy = cell_coord(pos[3 * (size_t)e + 1], B, &o, &bad);
-        int cz = cell_coord(pos[3 * (size_t)e + 2], B, &o, &bad);
-        int key = B.cell_base + (cx * B.K + cy) * B.K + cz;
-        keys[e] = key;
-        atomicAdd(&counts[key], 1);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < N; e += gridDim.x * blockDim.x) {
+        float4 r;
+        const int key = particle_key(pos, e, boxes, nboxes, &r, &bad);
+        for (int k = 0; k < sp.passes; ++k) atomicAdd(&h[k][(key >> sp.shift[k]) & ((1 << sp.bits[k]) - 1)], 1u);
     }
+    __syncthreads();
+    for (int k = 0; k < sp.passes; ++k)
+        for (int d = threadIdx.x; d < (1 << sp.bits[k]); d += blockDim.x)
+            if (h[k][d]) atomicAdd(&ghist[k * kSortMaxBins + d], h[k][d]);
     if (bad) atomicOr(&hdr->status, 1 << NF_ERR_NONFINITE);
 }
-
-__global__ void k_rel(const float* __restrict__ pos, int Ntot, const BoxDev* __restrict__ boxes,
-                      int nboxes, const int* __restrict__ perm, float4* __restrict__ rel)
-{
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < Ntot; s += gridDim.x * blockDim.x) {
-        int e = perm[s];
-        const BoxDev& B = boxes[find_box(boxes, nboxes, e)];
-        bool bad = false;
-        float4 r;
-        cell_coord(pos[3 * (size_t)e + 0], B, &r.x, &bad);
-        cell_coord(pos[3 * (size_t)e + 1], B, &r.y, &bad);
-        cell_coord(pos[3 * (size_t)e + 2], B, &r.z, &bad);
-        r.w = __int_as_float(e);
-        rel[s] = r;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Exclusive scan of uint32 (reduce, scan of block sums, apply)
-// ---------------------------------------------------------------------------
-
-constexpr int kScanThreads = 1024;
-constexpr int kScanPer = 4;
-constexpr int kScanTile = kScanThreads * kScanPer;
 
 // Exclusive prefix of v over the block; *total gets the block sum.
 __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* total)
@@ -179,157 +182,187 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* total)
     return before;
 }
 
-__global__ void k_scan_reduce(const unsigned* __restrict__ d, size_t n, unsigned* __restrict__ aux)
+// In-place exclusive scan of a[0 .. n), n <= 2 * blockDim.x, by the whole block.
+__device__ __forceinline__ void block_scan_array(unsigned* a, int n)
 {
-    size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanPer;
-    unsigned s = 0;
-#pragma unroll
-    for (int i = 0; i < kScanPer; ++i)
-        if (base + i < n) s += d[base + i];
+    const int i0 = 2 * threadIdx.x;
+    const unsigned v0 = i0 < n ? a[i0] : 0u, v1 = i0 + 1 < n ? a[i0 + 1] : 0u;
     unsigned total;
-    block_excl_scan(s, &total);
-    if (threadIdx.x == 0) aux[blockIdx.x] = total;
+    const unsigned pre = block_excl_scan(v0 + v1, &total);
+    if (i0 < n) a[i0] = pre;
+    if (i0 + 1 < n) a[i0 + 1] = pre + v0;
+    __syncthreads();
 }
 
-__global__ void k_scan_aux(unsigned* aux, size_t nb)
+__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v)
 {
-    unsigned carry = 0;
-    for (size_t base = 0; base < nb; base += kScanTile) {
-        size_t i0 = base + (size_t)threadIdx.x * kScanPer;
-        unsigned v[kScanPer];
-        unsigned s = 0;
-#pragma unroll
-        for (int i = 0; i < kScanPer; ++i) {
-            v[i] = (i0 + i < nb) ? aux[i0 + i] : 0u;
-            s += v[i];
-        }
-        unsigned total;
-        unsigned pre = block_excl_scan(s, &total) + carry;
-#pragma unroll
-        for (int i = 0; i < kScanPer; ++i) {
-            if (i0 + i < nb) aux[i0 + i] = pre;
-            pre += v[i];
-        }
-        carry += total;
-    }
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 
-__global__ void k_scan_apply(unsigned* __restrict__ d, size_t n, const unsigned* __restrict__ aux)
+constexpr unsigned long long kAggregate = 1ull << 32;  // status word: the tile's own count is there
+constexpr unsigned long long kPrefix = 2ull << 32;     // status word: the count of every tile up to this one
+constexpr int kSpinLimit = 1 << 22;                    // look-back polls before giving up (with 64 ns sleeps)
+
+// Dynamic shared memory of k_sort_pass for B bins.
+__host__ __device__ constexpr size_t sort_smem_bytes(int B)
 {
-    size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanPer;
-    unsigned v[kScanPer];
-    unsigned s = 0;
-#pragma unroll
-    for (int i = 0; i < kScanPer; ++i) {
-        v[i] = (base + i < n) ? d[base + i] : 0u;
-        s += v[i];
-    }
-    unsigned total;
-    unsigned pre = block_excl_scan(s, &total) + aux[blockIdx.x];
-#pragma unroll
-    for (int i = 0; i < kScanPer; ++i) {
-        if (base + i < n) d[base + i] = pre;
-        pre += v[i];
-    }
+    return (size_t)kSortWarps * B * 4 + (size_t)kSortTile * 16 + (size_t)kSortTile * 4 + 3ull * B * 4;
 }
 
-// ---------------------------------------------------------------------------
-// Stable LSD radix sort
-// ---------------------------------------------------------------------------
-
-constexpr int kRxWarps = 8;
-constexpr int kRxMaxRounds = 64;            // rounds of 32 elements per warp (upper bound)
-constexpr int kRxMaxBits = 11;
-
-__global__ void __launch_bounds__(kRxWarps * 32)
-k_radix_up(const int* __restrict__ keys, int N, int shift, int mask, int bins, int tiles, int rounds,
-           unsigned* __restrict__ H)
+// One stable pass over the digit (key >> shift) & (2^bits - 1).  FIRST reads
+// positions and computes keys and offsets; later passes read (rel, key) from
+// the previous pass.  LAST also writes perm (the original index) and the keys
+// in their final order.
+template <bool FIRST, bool LAST>
+__global__ void __launch_bounds__(kSortWarps * 32, 2)
+k_sort_pass(const float* __restrict__ pos, const BoxDev* __restrict__ boxes, int nboxes,
+            const float4* __restrict__ rel_in, const int* __restrict__ key_in, float4* __restrict__ rel_out,
+            int* __restrict__ key_out, int* __restrict__ perm_out, int N, int shift, int bits,
+            const unsigned* __restrict__ ghist, unsigned long long* __restrict__ status, unsigned* ticket,
+            WsHeader* hdr)
 {
-    extern __shared__ unsigned hist[];
-    for (int b = threadIdx.x; b < bins; b += blockDim.x) hist[b] = 0;
-    __syncthreads();
-    const int tile = kRxWarps * 32 * rounds;
-    size_t base = (size_t)blockIdx.x * tile;
-#pragma unroll 4
-    for (int i = threadIdx.x; i < tile; i += blockDim.x) {
-        size_t e = base + i;
-        if (e < (size_t)N) atomicAdd(&hist[(keys[e] >> shift) & mask], 1u);
-    }
-    __syncthreads();
-    for (int b = threadIdx.x; b < bins; b += blockDim.x)
-        H[(size_t)b * tiles + blockIdx.x] = hist[b];
-}
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int B = 1 << bits, mask = B - 1;
+    unsigned* cnt = reinterpret_cast<unsigned*>(smem);                                // [warps][B]
+    float4* sbuf = reinterpret_cast<float4*>(smem + (size_t)kSortWarps * B * 4);      // [tile]
+    int* skey = reinterpret_cast<int*>(sbuf + kSortTile);                             // [tile]
+    unsigned* s_start = reinterpret_cast<unsigned*>(skey + kSortTile);                // [B] local run starts
+    unsigned* s_gbase = s_start + B;                                                  // [B] global run starts
+    unsigned* s_gex = s_gbase + B;                                                    // [B] digit starts
+    __shared__ int s_tile;
 
-// Stable scatter of one tile.  vals_in == nullptr means "value = index".
-// keys_out == nullptr skips the key write (last pass).
-__global__ void __launch_bounds__(kRxWarps * 32)
-k_radix_down(const int* __restrict__ keys_in, const int* __restrict__ vals_in, int N, int shift,
-             int mask, int bins, int tiles, int rounds, const unsigned* __restrict__ H,
-             int* __restrict__ keys_out, int* __restrict__ vals_out)
-{
-    extern __shared__ unsigned cnt[];  // [kRxWarps][bins]
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < kRxWarps * bins; i += blockDim.x) cnt[i] = 0;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0) s_tile = (int)atomicAdd(ticket, 1u);  // tiles in start order: the look-back always progresses
+    for (int i = tid; i < kSortWarps * B; i += blockDim.x) cnt[i] = 0u;
+    for (int d = tid; d < B; d += blockDim.x) s_gex[d] = ghist[d];
     __syncthreads();
-    const size_t sub = (size_t)blockIdx.x * (kRxWarps * 32 * rounds) + (size_t)w * (32 * rounds);
-    unsigned* my = cnt + w * bins;
-    const unsigned lt = (1u << lane) - 1u;
-    // counts of this warp's sub-tile; keys are loaded four rounds at a time so
-    // the loads overlap (rounds is a multiple of 4)
-    constexpr int G = 4;
-    for (int r0 = 0; r0 < rounds; r0 += G) {
-        if (sub + (size_t)r0 * 32 >= (size_t)N) break;
-        int kv[G];
+    const int tile = s_tile;
+    const size_t base = (size_t)tile * kSortTile;
+    const int n = (int)min((size_t)kSortTile, (size_t)N - base);
+    block_scan_array(s_gex, B);  // first slot of every digit in the output
+
+    // load: warp w owns the consecutive elements [w*32R, (w+1)*32R) of the tile
+    constexpr int R = kSortTile / (kSortWarps * 32);
+    float4 v[R];
+    int key[R];
+    bool bad = false;
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-            const size_t e = sub + (size_t)(r0 + g) * 32 + lane;
-            kv[g] = e < (size_t)N ? keys_in[e] : -1;
-        }
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            const bool valid = kv[g] >= 0;
-            const int d = valid ? ((kv[g] >> shift) & mask) : bins;
-            const unsigned peers = __match_any_sync(kFull, d);
-            if (valid && lane == __ffs(peers) - 1) my[d] += __popc(peers);
-            __syncwarp();
-        }
-    }
-    __syncthreads();
-    // global offsets: bins of earlier tiles and earlier warps of this tile
-    for (int b = threadIdx.x; b < bins; b += blockDim.x) {
-        unsigned run = H[(size_t)b * tiles + blockIdx.x];
-        for (int q = 0; q < kRxWarps; ++q) {
-            unsigned c = cnt[q * bins + b];
-            cnt[q * bins + b] = run;
-            run += c;
-        }
-    }
-    __syncthreads();
-    for (int r0 = 0; r0 < rounds; r0 += G) {
-        if (sub + (size_t)r0 * 32 >= (size_t)N) break;
-        int kv[G], vv[G];
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            const size_t e = sub + (size_t)(r0 + g) * 32 + lane;
-            const bool valid = e < (size_t)N;
-            kv[g] = valid ? keys_in[e] : -1;
-            vv[g] = valid ? (vals_in ? vals_in[e] : (int)e) : 0;
-        }
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            const bool valid = kv[g] >= 0;
-            const int d = valid ? ((kv[g] >> shift) & mask) : bins;
-            const unsigned peers = __match_any_sync(kFull, d);
-            const unsigned base = valid ? my[d] : 0u;
-            __syncwarp();
-            if (valid && lane == __ffs(peers) - 1) my[d] = base + __popc(peers);
-            __syncwarp();
-            if (valid) {
-                const unsigned p = base + __popc(peers & lt);
-                if (keys_out) keys_out[p] = kv[g];
-                vals_out[p] = vv[g];
+    for (int r = 0; r < R; ++r) {
+        const int l = w * 32 * R + r * 32 + lane;
+        key[r] = 0;
+        v[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (l < n) {
+            const int e = (int)(base + l);
+            if constexpr (FIRST) {
+                key[r] = particle_key(pos, e, boxes, nboxes, &v[r], &bad);
+            } else {
+                v[r] = rel_in[e];
+                key[r] = key_in[e];
             }
         }
+    }
+    (void)bad;  // non-finite input is flagged by k_bin_hist
+
+    // stable rank within the tile: by digit, then by position in the tile
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned* my = cnt + w * B;
+    unsigned rk[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const bool valid = w * 32 * R + r * 32 + lane < n;
+        const int d = valid ? ((key[r] >> shift) & mask) : B;
+        const unsigned peers = __match_any_sync(kFull, d);
+        const unsigned c = valid ? my[d] : 0u;
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) my[d] = c + __popc(peers);
+        __syncwarp();
+        rk[r] = c + __popc(peers & lt);
+    }
+    __syncthreads();
+    // per digit: the warps' counts -> exclusive over warps; the tile's total per digit
+    for (int d = tid; d < B; d += blockDim.x) {
+        unsigned run = 0;
+        for (int q = 0; q < kSortWarps; ++q) {
+            const unsigned c = cnt[q * B + d];
+            cnt[q * B + d] = run;
+            run += c;
+        }
+        s_start[d] = run;
+    }
+    __syncthreads();
+    // decoupled look-back: the count of every earlier tile, per digit
+    for (int d = tid; d < B; d += blockDim.x) {
+        const unsigned agg = s_start[d];
+        unsigned long long* st = status + (size_t)tile * B + d;
+        unsigned excl = 0;
+        if (tile == 0) {
+            st_relaxed(st, kPrefix | agg);
+        } else {
+            st_relaxed(st, kAggregate | agg);
+            int t = tile - 1, spins = 0;
+            while (t >= 0) {
+                const unsigned long long s = ld_relaxed(status + (size_t)t * B + d);
+                const unsigned long long flag = s & ~0xffffffffull;
+                if (flag == 0) {
+                    if (++spins > kSpinLimit) {
+                        atomicOr(&hdr->status, 1 << NF_ERR_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(64);
+                    continue;
+                }
+                excl += (unsigned)s;
+                if (flag == kPrefix) break;
+                --t;
+            }
+            st_relaxed(st, kPrefix | (excl + agg));
+        }
+        s_gbase[d] = s_gex[d] + excl;
+    }
+    __syncthreads();
+    block_scan_array(s_start, B);  // first slot of every digit's run in the tile
+    // reorder the tile in shared memory
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int l = w * 32 * R + r * 32 + lane;
+        if (l < n) {
+            const int d = (key[r] >> shift) & mask;
+            const unsigned lp = s_start[d] + cnt[w * B + d] + rk[r];
+            if (lp < (unsigned)kSortTile) {  // always true when the ranks are consistent
+                sbuf[lp] = v[r];
+                skey[lp] = key[r];
+            }
+        }
+    }
+    __syncthreads();
+    // every run goes out contiguously
+    for (int i = tid; i < n; i += blockDim.x) {
+        const int k = skey[i];
+        const int d = (k >> shift) & mask;
+        const size_t g = (size_t)s_gbase[d] + (size_t)(i - (int)s_start[d]);
+        if (g >= (size_t)N) continue;  // never, unless a look-back gave up (then the status says so)
+        const float4 x = sbuf[i];
+        rel_out[g] = x;
+        key_out[g] = k;
+        if constexpr (LAST) perm_out[g] = __float_as_int(x.w);
+    }
+}
+
+// cell_offsets[c] = first sorted slot whose key is >= c, for c in [0, C]
+__global__ void k_cell_off(const int* __restrict__ keys, int N, int C, int* __restrict__ off)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        const int k = keys[i];
+        const int prev = i > 0 ? keys[i - 1] : -1;
+        for (int c = prev + 1; c <= k; ++c) off[c] = i;
+        if (i == N - 1)
+            for (int c = k + 1; c <= C; ++c) off[c] = N;
     }
 }
 
@@ -350,88 +383,74 @@ cudaError_t launch_fill_boxes(const BoxFill& f, BoxDev* boxes, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_shift(const float* pos, int Ntot, const BoxDev* boxes, int nboxes, int* keys,
-                         int* counts, WsHeader* hdr, cudaStream_t s)
+SortPlan sort_plan(int64_t N, int64_t C)
 {
-    k_shift<<<grid_for(Ntot, 256), 256, 0, s>>>(pos, Ntot, boxes, nboxes, keys, counts, hdr);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-size_t scan_aux_words(size_t n)
-{
-    return (n + kScanTile - 1) / kScanTile + 1;
-}
-
-cudaError_t launch_scan(unsigned* data, size_t n, unsigned* aux, cudaStream_t s)
-{
-    if (n == 0) return cudaSuccess;
-    size_t nb = (n + kScanTile - 1) / kScanTile;
-    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(data, n, aux);
-    k_scan_aux<<<1, kScanThreads, 0, s>>>(aux, nb);
-    k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(data, n, aux);
-    count_launches(3);
-    return cudaGetLastError();
-}
-
-RadixPlan radix_plan(int64_t N, int64_t C)
-{
+    SortPlan p{};
     int bits = 1;
     while ((int64_t(1) << bits) < C) ++bits;
-    RadixPlan p;
-    p.passes = (bits + kRxMaxBits - 1) / kRxMaxBits;
-    p.digit_bits = (bits + p.passes - 1) / p.passes;
-    p.bins = 1 << p.digit_bits;
-    // Enough tiles to fill every SM several times over (the rounds of a warp
-    // run one after another), but no more than the (bin, tile) matrix needs.
-    p.rounds = kRxMaxRounds;
-    while (p.rounds > 4 && (N + kRxWarps * 32 * p.rounds - 1) / (kRxWarps * 32 * p.rounds) < 1024) p.rounds >>= 1;
-    const int64_t tile = (int64_t)kRxWarps * 32 * p.rounds;
-    p.tiles = (int)((N + tile - 1) / tile);
+    p.passes = (bits + kSortMaxBits - 1) / kSortMaxBits;
+    int left = bits, sh = 0;
+    for (int k = 0; k < p.passes; ++k) {
+        const int b = (left + (p.passes - k) - 1) / (p.passes - k);  // as even as possible
+        p.shift[k] = sh;
+        p.bits[k] = b;
+        sh += b;
+        left -= b;
+    }
+    p.tiles = (int)((N + kSortTile - 1) / kSortTile);
     if (p.tiles < 1) p.tiles = 1;
     return p;
 }
 
-size_t radix_hist_words(const RadixPlan& p)
+size_t sort_ctl_bytes(const SortPlan& p)
 {
-    return (size_t)p.bins * p.tiles;
+    size_t b = 256 + (size_t)kSortMaxPasses * kSortMaxBins * 4;  // tickets, then the digit histograms
+    for (int k = 0; k < p.passes; ++k) b += (size_t)p.tiles * ((size_t)1 << p.bits[k]) * 8;
+    return b;
 }
 
-cudaError_t radix_sort(const RadixPlan& p, int N, int* keys_a, int* keys_b, int* vals_a,
-                       int* vals_b, int* perm, unsigned* hist, unsigned* aux, cudaStream_t s)
+cudaError_t run_sort(const SortPlan& p, const float* pos, int N, int C, const BoxDev* boxes, int nboxes,
+                     void* ctl, float4* rel_scratch, int* key_a, int* key_b, float4* rel, int* perm, int* cell_off,
+                     WsHeader* hdr, cudaStream_t s)
 {
-    const size_t smem_up = (size_t)p.bins * sizeof(unsigned);
-    const size_t smem_down = (size_t)kRxWarps * p.bins * sizeof(unsigned);
-    cudaError_t err = ensure_smem((const void*)k_radix_down, (int)smem_down);
+    cudaError_t err = cudaMemsetAsync(ctl, 0, sort_ctl_bytes(p), s);
     if (err != cudaSuccess) return err;
-    const int* kin = keys_a;
-    const int* vin = nullptr;
-    int* kbuf[2] = {keys_b, keys_a};
-    int* vbuf[2] = {vals_b, vals_a};
-    for (int pass = 0; pass < p.passes; ++pass) {
-        const int shift = pass * p.digit_bits;
-        const int mask = p.bins - 1;
-        const bool last = pass == p.passes - 1;
-        int* kout = last ? nullptr : kbuf[pass & 1];
-        int* vout = last ? perm : vbuf[pass & 1];
-        k_radix_up<<<p.tiles, kRxWarps * 32, smem_up, s>>>(kin, N, shift, mask, p.bins, p.tiles, p.rounds, hist);
+    unsigned* tickets = static_cast<unsigned*>(ctl);
+    unsigned* ghist = reinterpret_cast<unsigned*>(static_cast<char*>(ctl) + 256);
+    unsigned long long* status = reinterpret_cast<unsigned long long*>(
+        static_cast<char*>(ctl) + 256 + (size_t)kSortMaxPasses * kSortMaxBins * 4);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int hist_blocks = (int)std::min<int64_t>((int64_t)sms * 4, ((int64_t)N + 255) / 256);
+    k_bin_hist<<<hist_blocks, 256, 0, s>>>(pos, N, boxes, nboxes, p, ghist, hdr);
+    count_launches(1);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    // buffers: the last pass writes rel and the keys in key_a; the others alternate so
+    // that no pass reads the buffer it writes
+    const float4* rin = nullptr;
+    const int* kin = nullptr;
+    for (int k = 0; k < p.passes; ++k) {
+        const bool first = k == 0, last = k == p.passes - 1;
+        const int from_end = p.passes - 1 - k;  // 0 for the last pass
+        float4* rout = (from_end % 2 == 0) ? rel : rel_scratch;
+        int* kout = (from_end % 2 == 0) ? key_a : key_b;
+        const int B = 1 << p.bits[k];
+        const size_t smem = sort_smem_bytes(B);
+        typedef void (*PassFn)(const float*, const BoxDev*, int, const float4*, const int*, float4*, int*, int*,
+                               int, int, int, const unsigned*, unsigned long long*, unsigned*, WsHeader*);
+        PassFn fn = first ? (last ? k_sort_pass<true, true> : k_sort_pass<true, false>)
+                          : (last ? k_sort_pass<false, true> : k_sort_pass<false, false>);
+        if ((err = ensure_smem((const void*)fn, (int)smem)) != cudaSuccess) return err;
+        fn<<<p.tiles, kSortWarps * 32, smem, s>>>(pos, boxes, nboxes, rin, kin, rout, kout, perm, N, p.shift[k],
+                                                  p.bits[k], ghist + k * kSortMaxBins, status, tickets + k, hdr);
         count_launches(1);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
-        if ((err = launch_scan(hist, radix_hist_words(p), aux, s)) != cudaSuccess) return err;
-        k_radix_down<<<p.tiles, kRxWarps * 32, smem_down, s>>>(kin, vin, N, shift, mask, p.bins,
-                                                               p.tiles, p.rounds, hist, kout, vout);
-        count_launches(1);
-        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        status += (size_t)p.tiles * B;
+        rin = rout;
         kin = kout;
-        vin = vout;
     }
-    return cudaSuccess;
-}
-
-cudaError_t launch_rel(const float* pos, int Ntot, const BoxDev* boxes, int nboxes,
-                       const int* perm, float4* rel, cudaStream_t s)
-{
-    k_rel<<<grid_for(Ntot, 256), 256, 0, s>>>(pos, Ntot, boxes, nboxes, perm, rel);
+    k_cell_off<<<grid_for(N, 256), 256, 0, s>>>(key_a, N, C, cell_off);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -2,7 +2,9 @@
 //
 // Data layout in device memory (all regions caller-owned, carved out of the
 // workspace by nf_api.cu):
-//   keys/vals   int32 [N]       radix-sort double buffers (cell id, particle)
+//   keys a/b    int32 [N]       cell ids between the sort's passes (a: sorted at the end)
+//   rel scratch float4 [N]      offsets between the sort's passes
+//   sort ctl    tickets, digit histograms, look-back status words of the sort
 //   cell_off    int32 [C+1]     first sorted slot of every global cell
 //   rel         float4 [N]      sorted cell-centred offsets, .w = index bits
 //   perm        int32 [N]       sorted slot -> particle (global index)
@@ -184,28 +186,28 @@ cudaError_t ensure_smem(const void* fn, int bytes);
 
 // ---- launch wrappers (nf_bin.cu) ----
 cudaError_t launch_fill_boxes(const BoxFill& f, BoxDev* boxes, cudaStream_t s);
-cudaError_t launch_shift(const float* pos, int Ntot, const BoxDev* boxes, int nboxes,
-                         int* keys, int* counts, WsHeader* hdr, cudaStream_t s);
-// Exclusive scan of n uint32 values in place; aux must hold scan_aux_words(n) words.
-size_t scan_aux_words(size_t n);
-cudaError_t launch_scan(unsigned* data, size_t n, unsigned* aux, cudaStream_t s);
-
-struct RadixPlan {
+// Stable LSD sort of (cell id, particle): digits of at most kSortMaxBits bits,
+// one k_sort_pass launch per digit over tiles of kSortTile particles.
+constexpr int kSortMaxBits = 9;
+constexpr int kSortMaxBins = 1 << kSortMaxBits;
+constexpr int kSortMaxPasses = 4;  // cell ids below 2^31 need at most 4 passes of <= 9 bits
+constexpr int kSortTile = 2048;
+constexpr int kSortWarps = 8;
+struct SortPlan {
     int passes;
-    int digit_bits;
-    int bins;
+    int shift[kSortMaxPasses];
+    int bits[kSortMaxPasses];
     int tiles;
-    int rounds;  // rounds of 32 elements per warp in one tile (8 warps per tile)
 };
-RadixPlan radix_plan(int64_t N, int64_t C);
-size_t radix_hist_words(const RadixPlan& p);
-// Stable LSD radix sort of keys (0 .. C-1), values start as the index.
-// keys_a holds the input keys; the sorted particle order lands in perm.
-cudaError_t radix_sort(const RadixPlan& p, int N, int* keys_a, int* keys_b, int* vals_a,
-                       int* vals_b, int* perm, unsigned* hist, unsigned* aux,
-                       cudaStream_t s);
-cudaError_t launch_rel(const float* pos, int Ntot, const BoxDev* boxes, int nboxes,
-                       const int* perm, float4* rel, cudaStream_t s);
+SortPlan sort_plan(int64_t N, int64_t C);
+// bytes of the sort's control region (tickets, digit histograms, look-back status words)
+size_t sort_ctl_bytes(const SortPlan& p);
+// Bins N particles of the boxes: rel [N] (sorted cell-centred offsets, .w =
+// index bits), perm [N], cell_off [C+1].  rel_scratch [N], key_a [N], key_b [N]
+// and ctl (sort_ctl_bytes) are workspace; key_a ends with the sorted cell ids.
+cudaError_t run_sort(const SortPlan& p, const float* pos, int N, int C, const BoxDev* boxes, int nboxes,
+                     void* ctl, float4* rel_scratch, int* key_a, int* key_b, float4* rel, int* perm, int* cell_off,
+                     WsHeader* hdr, cudaStream_t s);
 
 // ---- work list, force, adjoint, combine (nf_force.cu) ----
 struct ForceTuning {

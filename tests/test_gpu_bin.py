@@ -33,10 +33,11 @@ def test_bin_configs_bit_exact(name):
 @pytest.mark.parametrize("N,K,box,seed", [
     (1, 5, 1.0, 0),
     (7, 5, 1.0, 1),
-    (1000, 7, 3.7, 2),        # one radix pass, box != 1, K not a power of two
-    (70001, 11, 1.0, 3),      # ragged tiles
-    (300000, 24, 2.5, 4),     # two passes
-    (1 << 20, 128, 1.0, 5),   # 21-bit keys: two 11-bit passes, many tiles
+    (1000, 7, 3.7, 2),        # 9-bit keys: one sort pass, box != 1, K not a power of two
+    (70001, 11, 1.0, 3),      # 11-bit keys: two passes; ragged last tile
+    (300000, 24, 2.5, 4),     # 14-bit keys: two passes
+    (1 << 20, 128, 1.0, 5),   # 21-bit keys: three 7-bit passes, 512 tiles
+    (20000, 520, 1.0, 10),    # 28-bit keys: four passes, nearly every cell empty
     (200000, 24, 2.0, 6),     # K / box = 12: dyadic, integer shift path
     (200000, 10, 0.625, 7),   # K / box = 16
     (200000, 13, 1.3, 8),     # K / box = 10 (box not dyadic): FP64 shift path
