@@ -6,18 +6,20 @@
 // least-significant-digit sort of (cell id, particle) done on the GPU, with
 // digits of at most 9 bits (one pass for K <= 8, two for K <= 32, three for
 // K <= 128):
-//   k_bin_hist   reads every position once, computes its cell id (FP64 rule
-//                below) and the global histogram of every pass's digit;
-//   k_sort_pass  one stable pass over tiles of 2048 particles: the first
-//                pass computes each particle's cell id and cell-centred
-//                offsets from its position, later passes read them back; a
-//                tile ranks its particles by digit in input order (each warp
-//                ranks its own consecutive elements with __match_any_sync),
-//                finds where its runs go by a decoupled look-back over the
-//                tiles before it (bounded waits), reorders the tile in shared
-//                memory and writes every run contiguously.  The offsets travel
-//                with the particle (float4, .w = original index), so no pass
-//                gathers positions at random;
+//   k_tile_hist  per tile of 2048 particles, the count of every digit value
+//                of this pass (the first pass computes the cell ids from the
+//                positions, FP64 rule below; later ones read them), written
+//                digit-major so that one exclusive scan of the whole matrix
+//                gives every (digit, tile) run its first output slot;
+//   scan         that exclusive scan (reduce, scan of block sums, apply);
+//   k_sort_pass  one stable pass over the same tiles: the first pass computes
+//                each particle's cell id and cell-centred offsets from its
+//                position, later passes read them back; a tile ranks its
+//                particles by digit in input order (each warp ranks its own
+//                consecutive elements with __match_any_sync), reorders the
+//                tile in shared memory and writes every run contiguously.  The
+//                offsets travel with the particle (float4, .w = original
+//                index), so no pass gathers positions at random;
 //   k_cell_off   cell_offsets from the sorted cell ids (the first slot of
 //                every cell; empty cells get the next cell's first slot).
 // The FP64 shift uses explicitly rounded intrinsics so that no FMA
@@ -66,6 +68,7 @@ __device__ __forceinline__ int cell_coord_fp64(float x, double kl, int K, float*
     *off = __double2float_rn(o);
     // c mod K into [0, K): c is an exact integer, so integer arithmetic gives
     // the same value as an FP64 remainder (and avoids the slow FP64 one)
+    if (c >= 0.0 && c < (double)K) return (int)c;  // inside the box: no wrap
     if (fabs(c) < 2147483647.0) {
         int cm = (int)c % K;
         return cm < 0 ? cm + K : cm;
@@ -103,6 +106,7 @@ __device__ __forceinline__ int cell_coord(float x, const BoxDev& B, float* off, 
             const long long o = frac - (one >> 1);
             // exact scaling of the rounded integer by 2^-s
             *off = __ll2float_rn(o) * __int_as_float((127 - s) << 23);
+            if (c >= 0 && c < B.K) return (int)c;  // inside the box: no wrap (64-bit % is slow)
             long long cm = c % B.K;
             return (int)(cm < 0 ? cm + B.K : cm);
         }
@@ -116,40 +120,68 @@ __global__ void k_fill_boxes(BoxFill f, BoxDev* boxes)
     if (i < f.count) boxes[f.first + i] = f.b[i];
 }
 
-// Cell id (global: cell_base + local id) and cell-centred offsets of particle e.
-__device__ __forceinline__ int particle_key(const float* __restrict__ pos, int e, const BoxDev* __restrict__ boxes,
-                                           int nboxes, float4* rel, bool* bad)
+// Cell id (global: cell_base + local id) and cell-centred offsets of particle
+// e, whose coordinates are x[0..2].
+__device__ __forceinline__ int particle_key(const float* x, int e, const BoxDev* __restrict__ boxes, int nboxes,
+                                           float4* rel, bool* bad)
 {
     const BoxDev& B = boxes[nboxes > 1 ? find_box(boxes, nboxes, e) : 0];
     float4 r;
-    const int cx = cell_coord(pos[3 * (size_t)e + 0], B, &r.x, bad);
-    const int cy = cell_coord(pos[3 * (size_t)e + 1], B, &r.y, bad);
-    const int cz = cell_coord(pos[3 * (size_t)e + 2], B, &r.z, bad);
+    const int cx = cell_coord(x[0], B, &r.x, bad);
+    const int cy = cell_coord(x[1], B, &r.y, bad);
+    const int cz = cell_coord(x[2], B, &r.z, bad);
     r.w = __int_as_float(e);
     *rel = r;
     return B.cell_base + (cx * B.K + cy) * B.K + cz;
 }
 
-// Global histogram of every pass's digit (shared-memory partial histograms,
-// one atomic per bin and block at the end); flags non-finite input.
-__global__ void __launch_bounds__(256)
-k_bin_hist(const float* __restrict__ pos, int N, const BoxDev* __restrict__ boxes, int nboxes, SortPlan sp,
-           unsigned* __restrict__ ghist, WsHeader* hdr)
+// Copies the coordinates of particles [base, base + n) into shared memory
+// (3n floats) with coalesced loads, 16 bytes at a time when aligned.
+__device__ __forceinline__ void stage_positions(const float* __restrict__ pos, size_t base, int n, float* spos)
 {
-    __shared__ unsigned h[kSortMaxPasses][kSortMaxBins];
-    for (int i = threadIdx.x; i < kSortMaxPasses * kSortMaxBins; i += blockDim.x) (&h[0][0])[i] = 0u;
+    const float* src = pos + 3 * base;
+    const int nf = 3 * n;
+    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        const int n4 = nf >> 2;
+        const float4* s4 = reinterpret_cast<const float4*>(src);
+        float4* d4 = reinterpret_cast<float4*>(spos);
+        for (int i = threadIdx.x; i < n4; i += blockDim.x) d4[i] = s4[i];
+        for (int i = 4 * n4 + threadIdx.x; i < nf; i += blockDim.x) spos[i] = src[i];
+    } else {
+        for (int i = threadIdx.x; i < nf; i += blockDim.x) spos[i] = src[i];
+    }
+}
+
+// Counts of every digit value in each tile, written to M[digit * tiles + tile].
+// FIRST computes the cell ids from the positions (and flags non-finite input).
+template <bool FIRST>
+__global__ void __launch_bounds__(kSortWarps * 32)
+k_tile_hist(const float* __restrict__ pos, const BoxDev* __restrict__ boxes, int nboxes,
+            const int* __restrict__ key_in, int N, int shift, int bits, int tiles, unsigned* __restrict__ M,
+            WsHeader* hdr)
+{
+    __shared__ unsigned h[kSortMaxBins];
+    __shared__ __align__(16) float spos[FIRST ? 3 * kSortTile : 4];
+    const int B = 1 << bits, mask = B - 1;
+    for (int d = threadIdx.x; d < B; d += blockDim.x) h[d] = 0u;
+    const size_t base = (size_t)blockIdx.x * kSortTile;
+    const int n = (int)min((size_t)kSortTile, (size_t)N - base);
+    if constexpr (FIRST) stage_positions(pos, base, n, spos);
     __syncthreads();
     bool bad = false;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < N; e += gridDim.x * blockDim.x) {
-        float4 r;
-        const int key = particle_key(pos, e, boxes, nboxes, &r, &bad);
-        for (int k = 0; k < sp.passes; ++k) atomicAdd(&h[k][(key >> sp.shift[k]) & ((1 << sp.bits[k]) - 1)], 1u);
+    for (int l = threadIdx.x; l < n; l += blockDim.x) {
+        int key;
+        if constexpr (FIRST) {
+            float4 r;
+            key = particle_key(spos + 3 * l, (int)(base + l), boxes, nboxes, &r, &bad);
+        } else {
+            key = key_in[base + l];
+        }
+        atomicAdd(&h[(key >> shift) & mask], 1u);
     }
     __syncthreads();
-    for (int k = 0; k < sp.passes; ++k)
-        for (int d = threadIdx.x; d < (1 << sp.bits[k]); d += blockDim.x)
-            if (h[k][d]) atomicAdd(&ghist[k * kSortMaxBins + d], h[k][d]);
-    if (bad) atomicOr(&hdr->status, 1 << NF_ERR_NONFINITE);
+    for (int d = threadIdx.x; d < B; d += blockDim.x) M[(size_t)d * tiles + blockIdx.x] = h[d];
+    if (FIRST && bad) atomicOr(&hdr->status, 1 << NF_ERR_NONFINITE);
 }
 
 // Exclusive prefix of v over the block; *total gets the block sum.
@@ -194,25 +226,69 @@ __device__ __forceinline__ void block_scan_array(unsigned* a, int n)
     __syncthreads();
 }
 
-__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v)
+// Exclusive scan of uint32 (reduce, scan of block sums, apply)
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 4;
+constexpr int kScanTile = kScanThreads * kScanPer;
+
+__global__ void k_scan_reduce(const unsigned* __restrict__ d, size_t n, unsigned* __restrict__ aux)
 {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p)
-{
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
+    size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanPer;
+    unsigned s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i)
+        if (base + i < n) s += d[base + i];
+    unsigned total;
+    block_excl_scan(s, &total);
+    if (threadIdx.x == 0) aux[blockIdx.x] = total;
 }
 
-constexpr unsigned long long kAggregate = 1ull << 32;  // status word: the tile's own count is there
-constexpr unsigned long long kPrefix = 2ull << 32;     // status word: the count of every tile up to this one
-constexpr int kSpinLimit = 1 << 22;                    // look-back polls before giving up (with 64 ns sleeps)
+__global__ void k_scan_aux(unsigned* aux, size_t nb)
+{
+    unsigned carry = 0;
+    for (size_t base = 0; base < nb; base += kScanTile) {
+        size_t i0 = base + (size_t)threadIdx.x * kScanPer;
+        unsigned v[kScanPer];
+        unsigned s = 0;
+#pragma unroll
+        for (int i = 0; i < kScanPer; ++i) {
+            v[i] = (i0 + i < nb) ? aux[i0 + i] : 0u;
+            s += v[i];
+        }
+        unsigned total;
+        unsigned pre = block_excl_scan(s, &total) + carry;
+#pragma unroll
+        for (int i = 0; i < kScanPer; ++i) {
+            if (i0 + i < nb) aux[i0 + i] = pre;
+            pre += v[i];
+        }
+        carry += total;
+    }
+}
+
+__global__ void k_scan_apply(unsigned* __restrict__ d, size_t n, const unsigned* __restrict__ aux)
+{
+    size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanPer;
+    unsigned v[kScanPer];
+    unsigned s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+        v[i] = (base + i < n) ? d[base + i] : 0u;
+        s += v[i];
+    }
+    unsigned total;
+    unsigned pre = block_excl_scan(s, &total) + aux[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+        if (base + i < n) d[base + i] = pre;
+        pre += v[i];
+    }
+}
 
 // Dynamic shared memory of k_sort_pass for B bins.
 __host__ __device__ constexpr size_t sort_smem_bytes(int B)
 {
-    return (size_t)kSortWarps * B * 4 + (size_t)kSortTile * 16 + (size_t)kSortTile * 4 + 3ull * B * 4;
+    return (size_t)kSortWarps * B * 4 + (size_t)kSortTile * 16 + (size_t)kSortTile * 4 + 2ull * B * 4;
 }
 
 // One stable pass over the digit (key >> shift) & (2^bits - 1).  FIRST reads
@@ -223,9 +299,8 @@ template <bool FIRST, bool LAST>
 __global__ void __launch_bounds__(kSortWarps * 32, 2)
 k_sort_pass(const float* __restrict__ pos, const BoxDev* __restrict__ boxes, int nboxes,
             const float4* __restrict__ rel_in, const int* __restrict__ key_in, float4* __restrict__ rel_out,
-            int* __restrict__ key_out, int* __restrict__ perm_out, int N, int shift, int bits,
-            const unsigned* __restrict__ ghist, unsigned long long* __restrict__ status, unsigned* ticket,
-            WsHeader* hdr)
+            int* __restrict__ key_out, int* __restrict__ perm_out, int N, int shift, int bits, int tiles,
+            const unsigned* __restrict__ M)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int B = 1 << bits, mask = B - 1;
@@ -234,18 +309,19 @@ k_sort_pass(const float* __restrict__ pos, const BoxDev* __restrict__ boxes, int
     int* skey = reinterpret_cast<int*>(sbuf + kSortTile);                             // [tile]
     unsigned* s_start = reinterpret_cast<unsigned*>(skey + kSortTile);                // [B] local run starts
     unsigned* s_gbase = s_start + B;                                                  // [B] global run starts
-    unsigned* s_gex = s_gbase + B;                                                    // [B] digit starts
-    __shared__ int s_tile;
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    if (tid == 0) s_tile = (int)atomicAdd(ticket, 1u);  // tiles in start order: the look-back always progresses
+    const int tile = blockIdx.x;
     for (int i = tid; i < kSortWarps * B; i += blockDim.x) cnt[i] = 0u;
-    for (int d = tid; d < B; d += blockDim.x) s_gex[d] = ghist[d];
-    __syncthreads();
-    const int tile = s_tile;
+    for (int d = tid; d < B; d += blockDim.x) s_gbase[d] = M[(size_t)d * tiles + tile];  // scanned: first output slot
     const size_t base = (size_t)tile * kSortTile;
     const int n = (int)min((size_t)kSortTile, (size_t)N - base);
-    block_scan_array(s_gex, B);  // first slot of every digit in the output
+    // the first pass reads the tile's positions into the (still unused) reorder buffer
+    float* spos = reinterpret_cast<float*>(sbuf);
+    if constexpr (FIRST) {
+        stage_positions(pos, base, n, spos);
+        __syncthreads();
+    }
 
     // load: warp w owns the consecutive elements [w*32R, (w+1)*32R) of the tile
     constexpr int R = kSortTile / (kSortWarps * 32);
@@ -260,14 +336,14 @@ k_sort_pass(const float* __restrict__ pos, const BoxDev* __restrict__ boxes, int
         if (l < n) {
             const int e = (int)(base + l);
             if constexpr (FIRST) {
-                key[r] = particle_key(pos, e, boxes, nboxes, &v[r], &bad);
+                key[r] = particle_key(spos + 3 * l, e, boxes, nboxes, &v[r], &bad);
             } else {
                 v[r] = rel_in[e];
                 key[r] = key_in[e];
             }
         }
     }
-    (void)bad;  // non-finite input is flagged by k_bin_hist
+    (void)bad;  // non-finite input is flagged by k_tile_hist
 
     // stable rank within the tile: by digit, then by position in the tile
     const unsigned lt = (1u << lane) - 1u;
@@ -296,36 +372,6 @@ k_sort_pass(const float* __restrict__ pos, const BoxDev* __restrict__ boxes, int
         s_start[d] = run;
     }
     __syncthreads();
-    // decoupled look-back: the count of every earlier tile, per digit
-    for (int d = tid; d < B; d += blockDim.x) {
-        const unsigned agg = s_start[d];
-        unsigned long long* st = status + (size_t)tile * B + d;
-        unsigned excl = 0;
-        if (tile == 0) {
-            st_relaxed(st, kPrefix | agg);
-        } else {
-            st_relaxed(st, kAggregate | agg);
-            int t = tile - 1, spins = 0;
-            while (t >= 0) {
-                const unsigned long long s = ld_relaxed(status + (size_t)t * B + d);
-                const unsigned long long flag = s & ~0xffffffffull;
-                if (flag == 0) {
-                    if (++spins > kSpinLimit) {
-                        atomicOr(&hdr->status, 1 << NF_ERR_TIMEOUT);
-                        break;
-                    }
-                    __nanosleep(64);
-                    continue;
-                }
-                excl += (unsigned)s;
-                if (flag == kPrefix) break;
-                --t;
-            }
-            st_relaxed(st, kPrefix | (excl + agg));
-        }
-        s_gbase[d] = s_gex[d] + excl;
-    }
-    __syncthreads();
     block_scan_array(s_start, B);  // first slot of every digit's run in the tile
     // reorder the tile in shared memory
 #pragma unroll
@@ -346,7 +392,7 @@ k_sort_pass(const float* __restrict__ pos, const BoxDev* __restrict__ boxes, int
         const int k = skey[i];
         const int d = (k >> shift) & mask;
         const size_t g = (size_t)s_gbase[d] + (size_t)(i - (int)s_start[d]);
-        if (g >= (size_t)N) continue;  // never, unless a look-back gave up (then the status says so)
+        if (g >= (size_t)N) continue;  // never: the scanned counts keep every run inside the output
         const float4 x = sbuf[i];
         rel_out[g] = x;
         key_out[g] = k;
@@ -354,15 +400,31 @@ k_sort_pass(const float* __restrict__ pos, const BoxDev* __restrict__ boxes, int
     }
 }
 
-// cell_offsets[c] = first sorted slot whose key is >= c, for c in [0, C]
+// cell_offsets[c] = first sorted slot whose key is >= c, for c in [0, C];
+// each thread takes four consecutive sorted keys
 __global__ void k_cell_off(const int* __restrict__ keys, int N, int C, int* __restrict__ off)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-        const int k = keys[i];
-        const int prev = i > 0 ? keys[i - 1] : -1;
-        for (int c = prev + 1; c <= k; ++c) off[c] = i;
-        if (i == N - 1)
-            for (int c = k + 1; c <= C; ++c) off[c] = N;
+    const int nq = (N + 3) >> 2;
+    const bool vec = (reinterpret_cast<uintptr_t>(keys) & 15) == 0;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+        const int i0 = 4 * q;
+        int k[4];
+        if (vec && i0 + 3 < N) {
+            const int4 v = reinterpret_cast<const int4*>(keys)[q];
+            k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
+        } else {
+            for (int j = 0; j < 4; ++j) k[j] = i0 + j < N ? keys[i0 + j] : C;
+        }
+        int prev = i0 > 0 ? keys[i0 - 1] : -1;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int i = i0 + j;
+            if (i >= N) break;
+            for (int c = prev + 1; c <= k[j]; ++c) off[c] = i;
+            prev = k[j];
+            if (i == N - 1)
+                for (int c = k[j] + 1; c <= C; ++c) off[c] = N;
+        }
     }
 }
 
@@ -402,30 +464,26 @@ SortPlan sort_plan(int64_t N, int64_t C)
     return p;
 }
 
+size_t sort_matrix_words(const SortPlan& p)
+{
+    size_t m = 0;
+    for (int k = 0; k < p.passes; ++k) m = std::max(m, (size_t)p.tiles << p.bits[k]);
+    return m;
+}
+
 size_t sort_ctl_bytes(const SortPlan& p)
 {
-    size_t b = 256 + (size_t)kSortMaxPasses * kSortMaxBins * 4;  // tickets, then the digit histograms
-    for (int k = 0; k < p.passes; ++k) b += (size_t)p.tiles * ((size_t)1 << p.bits[k]) * 8;
-    return b;
+    const size_t m = sort_matrix_words(p);
+    return (m + (m + kScanTile - 1) / kScanTile + 64) * 4;  // the count matrix and the scan's block sums
 }
 
 cudaError_t run_sort(const SortPlan& p, const float* pos, int N, int C, const BoxDev* boxes, int nboxes,
                      void* ctl, float4* rel_scratch, int* key_a, int* key_b, float4* rel, int* perm, int* cell_off,
                      WsHeader* hdr, cudaStream_t s)
 {
-    cudaError_t err = cudaMemsetAsync(ctl, 0, sort_ctl_bytes(p), s);
-    if (err != cudaSuccess) return err;
-    unsigned* tickets = static_cast<unsigned*>(ctl);
-    unsigned* ghist = reinterpret_cast<unsigned*>(static_cast<char*>(ctl) + 256);
-    unsigned long long* status = reinterpret_cast<unsigned long long*>(
-        static_cast<char*>(ctl) + 256 + (size_t)kSortMaxPasses * kSortMaxBins * 4);
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int hist_blocks = (int)std::min<int64_t>((int64_t)sms * 4, ((int64_t)N + 255) / 256);
-    k_bin_hist<<<hist_blocks, 256, 0, s>>>(pos, N, boxes, nboxes, p, ghist, hdr);
-    count_launches(1);
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    cudaError_t err;
+    unsigned* M = static_cast<unsigned*>(ctl);
+    unsigned* aux = M + sort_matrix_words(p);
     // buffers: the last pass writes rel and the keys in key_a; the others alternate so
     // that no pass reads the buffer it writes
     const float4* rin = nullptr;
@@ -436,21 +494,35 @@ cudaError_t run_sort(const SortPlan& p, const float* pos, int N, int C, const Bo
         float4* rout = (from_end % 2 == 0) ? rel : rel_scratch;
         int* kout = (from_end % 2 == 0) ? key_a : key_b;
         const int B = 1 << p.bits[k];
+        const size_t mn = (size_t)p.tiles * B;
+        if (first)
+            k_tile_hist<true><<<p.tiles, kSortWarps * 32, 0, s>>>(pos, boxes, nboxes, nullptr, N, p.shift[k],
+                                                                 p.bits[k], p.tiles, M, hdr);
+        else
+            k_tile_hist<false><<<p.tiles, kSortWarps * 32, 0, s>>>(pos, boxes, nboxes, kin, N, p.shift[k],
+                                                                  p.bits[k], p.tiles, M, hdr);
+        count_launches(1);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        const size_t nb = (mn + kScanTile - 1) / kScanTile;
+        k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(M, mn, aux);
+        k_scan_aux<<<1, kScanThreads, 0, s>>>(aux, nb);
+        k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(M, mn, aux);
+        count_launches(3);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
         const size_t smem = sort_smem_bytes(B);
         typedef void (*PassFn)(const float*, const BoxDev*, int, const float4*, const int*, float4*, int*, int*,
-                               int, int, int, const unsigned*, unsigned long long*, unsigned*, WsHeader*);
+                               int, int, int, int, const unsigned*);
         PassFn fn = first ? (last ? k_sort_pass<true, true> : k_sort_pass<true, false>)
                           : (last ? k_sort_pass<false, true> : k_sort_pass<false, false>);
         if ((err = ensure_smem((const void*)fn, (int)smem)) != cudaSuccess) return err;
         fn<<<p.tiles, kSortWarps * 32, smem, s>>>(pos, boxes, nboxes, rin, kin, rout, kout, perm, N, p.shift[k],
-                                                  p.bits[k], ghist + k * kSortMaxBins, status, tickets + k, hdr);
+                                                  p.bits[k], p.tiles, M);
         count_launches(1);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
-        status += (size_t)p.tiles * B;
         rin = rout;
         kin = kout;
     }
-    k_cell_off<<<grid_for(N, 256), 256, 0, s>>>(key_a, N, C, cell_off);
+    k_cell_off<<<grid_for(((size_t)N + 3) / 4, 256), 256, 0, s>>>(key_a, N, C, cell_off);
     count_launches(1);
     return cudaGetLastError();
 }
