@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-side", action="store_true",
+                    help="skip the secondary measurements (other workloads, density, steps, far field)")
     ap.add_argument("--tune", default=None, help="sinks_per_lane,stage,warps,blocks_per_sm")
     return ap.parse_args()
 
@@ -365,7 +367,9 @@ def run_native(args, rank, world, local):
         "config": {"workload": describe(w), "pairs_per_pass": P, "pairs_per_step": 2 * P,
                    "step": "nf_forces + nf_forces_adjoint", "l2": "flushed (512 MB write) before each step",
                    "parallelism": f"replicas: one box per GPU x {world}",
-                   "tuning": list(_lib.nf_get_default_tuning())},
+                   "tuning": {"forward": list(_lib.nf_get_default_tuning()),
+                              "adjoint": list(_lib.nf_get_default_tuning_adjoint()),
+                              "fields": "sinks per lane, sources per stage, warps per block, blocks per SM (0: as many as fit)"}},
         "fwd": {"pairs_per_s": P / (fwd_ms / 1e3), "particle_updates_per_s": N / (fwd_ms / 1e3),
                 "ms": fwd_ms, "pair_kernel_ms": fwd_pair_ms, "bin_ms": bin_ms},
         "fwd_adjoint": {"pairs_per_s": P / ((fwd_ms + adj_ms) / 1e3), "ms": fwd_ms + adj_ms,
@@ -376,13 +380,14 @@ def run_native(args, rank, world, local):
                   "lane_utilisation": st["pairs"] / max(st["lane_pairs"], 1)},
     }
 
-    if args.workload != "clustered":
-        out["clustered128"] = measure_step_side("clustered", dev, flush, fp32_peak, rank)
-    out["uniform"] = measure_uniform(w, dev, flush, fp32_peak)
-    out["density"] = measure_density(w, pos, ws, acc, fwd_pair_ms, flush)
-    out["kdk"] = measure_kdk(w, dev, flush)
-    out["multipoles"] = measure_multipoles(w, pos, dev, flush)
-    out["far"] = measure_far(w, pos, dev, flush, fma, fwd_ms_for_far(out))
+    if not args.no_side:
+        if args.workload != "clustered":
+            out["clustered128"] = measure_step_side("clustered", dev, flush, fp32_peak, rank)
+        out["uniform"] = measure_uniform(w, dev, flush, fp32_peak)
+        out["density"] = measure_density(w, pos, ws, acc, fwd_pair_ms, flush)
+        out["kdk"] = measure_kdk(w, dev, flush)
+        out["multipoles"] = measure_multipoles(w, pos, dev, flush)
+        out["far"] = measure_far(w, pos, dev, flush, fma, fwd_ms_for_far(out))
     if not args.no_e2e:
         out["e2e"] = measure_e2e(args, w, g_np, dev, P, flush)
     if not args.no_batched:
@@ -517,23 +522,29 @@ def measure_uniform(w, dev, flush, fp32_peak, reps=5):
 
 
 def measure_density(w, pos, ws, acc, fwd_pair_ms, flush):
-    """The forward with the fused top-hat density estimate (b = half a cell):
-    its pair kernel time against the plain forward pair kernel."""
+    """The forward with the fused top-hat density estimate: its pair kernel
+    time against the plain forward pair kernel, at the FoF scale the paper
+    uses it for (b = 0.2 mean interparticle spacings, Sec. "Group Finding")
+    and at b = half a cell."""
     import torch
     from paper_2110_11392_gb300 import _lib
-    b = 0.5 * w.box / w.K
     rho = torch.empty(w.N, dtype=torch.float32, device=pos.device)
-    _lib.nf_forces_density(pos, w.box, w.K, w.R, w.eps, b, acc, rho, ws)
-    _lib.nf_profile_enable(True)
-    ms = []
-    for _ in range(3):
-        flush.zero_()
+    spacing = w.box / w.N ** (1.0 / 3.0)
+    out = {}
+    for name, b in (("fof", 0.2 * spacing), ("half_cell", 0.5 * w.box / w.K)):
         _lib.nf_forces_density(pos, w.box, w.K, w.R, w.eps, b, acc, rho, ws)
-        ms.append(_lib.nf_profile_read(0)["pair_ms"])
-    _lib.nf_profile_enable(False)
-    t = float(np.mean(ms))
-    return {"b_cells": 0.5, "pair_kernel_ms": t, "over_fwd_pair_kernel": t / fwd_pair_ms,
-            "mean_rho": float(rho.mean().item())}
+        _lib.nf_profile_enable(True)
+        ms = []
+        for _ in range(3):
+            flush.zero_()
+            _lib.nf_forces_density(pos, w.box, w.K, w.R, w.eps, b, acc, rho, ws)
+            ms.append(_lib.nf_profile_read(0)["pair_ms"])
+        _lib.nf_profile_enable(False)
+        t = float(np.mean(ms))
+        out[name] = {"b_cells": b * w.K / w.box, "pair_kernel_ms": t, "over_fwd_pair_kernel": t / fwd_pair_ms,
+                     "mean_rho": float(rho.mean().item())}
+    out["note"] = "b = 0.2 mean spacings (FoF scale) and b = half a cell; plain forward pair kernel as the base"
+    return out
 
 
 def measure_kdk(w, dev, flush, steps=5):
@@ -600,7 +611,7 @@ def measure_far(w, pos, dev, flush, fma, fwd_ms, p=8, reps=5):
     ev = lambda: torch.cuda.Event(enable_timing=True)
     a, b = ev(), ev()
     torch.cuda.synchronize(dev)
-    ff = nf.FarField(w.K, w.R, p, w.box, device=dev)   # first call: allocations and cuFFT plans
+    ff = nf.FarField(w.K, w.R, p, w.box, device=dev)   # first call: allocations
     ws = ff.workspace(w.N)
     torch.cuda.synchronize(dev)
     a.record(stream)
@@ -701,7 +712,8 @@ def measure_far(w, pos, dev, flush, fma, fwd_ms, p=8, reps=5):
             "taylor_roofline": taylor_roof,
             "note": "derivatives in FP64, once per (K, R, p, box); in double-float mode (K a power of two) the "
                     "multipoles, transforms, k-space product, rebuild and Taylors are double-float on the FP32 "
-                    "pipe; in FP64 mode cuFFT and FP64 kernels; Ewald-summed periodic force = near + far"}
+                    "pipe; in FP64 mode FP64 kernels (this library's mixed-radix transforms); Ewald-summed periodic "
+                    "force = near + far"}
 
 
 def measure_multipoles(w, pos, dev, flush, p=8, reps=3):

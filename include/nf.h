@@ -180,11 +180,19 @@ typedef struct {
     int blocks_per_sm;
 } nf_tuning;
 
-/* The tuning nf_forces and nf_forces_adjoint use when no tuning is given.
- * nf_set_default_tuning copies *t (validated; NULL restores the built-in
- * default); both are process-wide and not thread-safe against running calls. */
+/* The tunings used when no tuning is given: one for the forward calls
+ * (nf_forces, nf_forces_density, nf_forces_batched, the time steps and
+ * nf_forces_total) and one for the adjoint calls (nf_forces_adjoint,
+ * nf_forces_adjoint_batched).  The built-in defaults, measured best on GB300,
+ * are {4, 128, 8, 0} forward and {2, 128, 8, 0} adjoint.
+ * nf_set_default_tuning copies *t (validated) into both; NULL restores both
+ * built-ins.  nf_set_default_tuning_adjoint sets the adjoint's alone (NULL:
+ * its built-in).  All are process-wide and not thread-safe against running
+ * calls. */
 int nf_set_default_tuning(const nf_tuning *t);
 void nf_get_default_tuning(nf_tuning *t);
+int nf_set_default_tuning_adjoint(const nf_tuning *t);
+void nf_get_default_tuning_adjoint(nf_tuning *t);
 
 /* Workspace for a batch (host array boxes[nboxes]); 0 if the batch is invalid. */
 size_t nf_workspace_bytes_batched(const nf_box *boxes, int nboxes);
@@ -278,37 +286,37 @@ int nf_multipoles(const float *pos, int64_t N, double box, int K, int p, double 
  * complete basis of (p+3)(p+2)(p+1)/6 terms (ordered as in nf_multipoles).
  * The uniform background of Ewald summation is included (the mean density
  * exerts no force).  Arithmetic: FP64 for the derivatives; double-float or
- * FP64 for the rest (see nf_far_set_arith).  The transforms are this
- * library's double-float kernels for a power-of-two K in double-float mode,
- * cuFFT's FP64 transforms otherwise. */
+ * FP64 for the rest (see nf_far_set_arith).  The 3-D transforms are this
+ * library's own kernels: radix-4/2 in double-float for a power-of-two K, and
+ * mixed-radix (factors 4, 2, 3, 5, 7 and any larger prime) for any K, in
+ * double-float or IEEE FP64. */
 #define NF_MAX_FAR_ORDER 12
 
 /* Bytes of a derivatives buffer for grid K and order p (0 if out of range):
  * a 256-byte header, the convolution's tables and the transformed
- * derivatives, (p+3)(p+2)(p+1)/6 FP64 fields of K*K*(K/2+1) values (for a
- * power-of-two K a second copy as double-float pairs, with the pairs'
- * coefficients and the transforms' twiddles in that form).  The transform
+ * derivatives, (p+3)(p+2)(p+1)/6 FP64 fields of K*K*(K/2+1) values, a
+ * second copy as double-float pairs with the pairs' coefficients in that
+ * form, and the transforms' twiddles (FP64 and double-float).  The transform
  * of a term of even order is real and of odd order imaginary (the
  * derivatives have definite parity, Sec. "Far-field Computation"), so one
  * real number per term and frequency is kept. */
 size_t nf_derivatives_bytes(int K, int p);
 
 /* Workspace bytes of nf_far_forces (N particles) and of nf_derivatives (any
- * N >= 1 will do): the binning, the multipoles, two complex spectra and the
- * cuFFT work area.  0 if the arguments are out of range. */
+ * N >= 1 will do): the binning, the multipoles and two complex spectra.
+ * 0 if the arguments are out of range. */
 size_t nf_far_workspace_bytes(int64_t N, int K, int p);
 
 /* Precomputes the derivatives tensor of grid K, near-field radius R, order p
  * and box side box into `derivs` (device memory, caller-owned, 256-byte
  * aligned, at least nf_derivatives_bytes(K, p) bytes); ws is a device
  * workspace of nf_far_workspace_bytes(1, K, p) bytes.  Asynchronous on
- * `stream`.  The first call for a (K, p) on a device creates its cuFFT plans
- * (cuFFT keeps its own small tables); make it before any graph capture.
+ * `stream` (its host-built tables are copied from pageable memory, so the
+ * call returns once they are staged).
  * Errors: NF_ERR_ARG for K < 2R+1, R outside 1..NF_MAX_R, p outside
- * 0..NF_MAX_FAR_ORDER, (p+3)(p+2)(p+1)/6 K^3 >= 2^31 (the FFT plans' 32-bit
- * element offsets; K <= 235 at p = 8), box <= 0 or NULL pointers;
- * NF_ERR_WORKSPACE for a short or misaligned buffer; NF_ERR_CUDA if a
- * launch or transform fails. */
+ * 0..NF_MAX_FAR_ORDER, (p+3)(p+2)(p+1)/6 K^3 >= 2^31 (32-bit field offsets;
+ * K <= 235 at p = 8), box <= 0 or NULL pointers; NF_ERR_WORKSPACE for a
+ * short or misaligned buffer; NF_ERR_CUDA if a launch fails. */
 int nf_derivatives(int K, int R, int p, double box, void *derivs, size_t derivs_bytes,
                    void *ws, size_t ws_bytes, void *stream);
 
@@ -322,11 +330,9 @@ int nf_derivatives(int K, int R, int p, double box, void *derivs, size_t derivs_
  *            the potential in cell c is -m sum_t taylors[c][t] x^a y^b z^c,
  *            x the displacement from the cell centre in box units.
  * All device memory, caller-owned; ws holds nf_far_workspace_bytes(N, K, p)
- * bytes.  Asynchronous on `stream` and graph-capturable once the cuFFT plans
- * exist (after the first call for this (K, p)).  Errors: as nf_derivatives;
- * NF_ERR_ARG also when `derivs` was made for another (K, R, p, box) by this
- * process; NF_ERR_CUDA with cuFFT's status in nf_last_error() if a
- * transform fails. */
+ * bytes.  Asynchronous on `stream` and graph-capturable.  Errors: as
+ * nf_derivatives; NF_ERR_ARG also when `derivs` was made for another
+ * (K, R, p, box) by this process. */
 int nf_far_forces(const float *pos, int64_t N, double box, int K, int R, int p,
                   const void *derivs, size_t derivs_bytes, double *acc_far, float *acc_add,
                   double *taylors, void *ws, size_t ws_bytes, void *stream);
@@ -348,10 +354,9 @@ int nf_forces_total(const float *pos, int64_t N, double box, int K, int R, doubl
  * as an unevaluated sum of two FP32 numbers, held exact by error-free
  * transformations, on the FP32 pipe: about 48 significant bits.  Both modes
  * give the same far field to 1e-12 of its largest value (tested).  In
- * double-float mode with K a power of two the transforms and the k-space
- * product are double-float too; otherwise (and in FP64 mode) they are
- * cuFFT's FP64 transforms and an FP64 product.  The derivatives are FP64
- * in both.  nf_far_set_arith returns
+ * double-float mode the transforms and the k-space product are double-float
+ * too; in FP64 mode they are FP64.  The derivatives are FP64 in both.
+ * nf_far_set_arith returns
  * NF_ERR_ARG for another mode; calls already enqueued keep the mode they
  * were enqueued with. */
 #define NF_FAR_FP64 0
@@ -359,10 +364,10 @@ int nf_forces_total(const float *pos, int64_t N, double box, int K, int R, doubl
 int nf_far_set_arith(int mode);
 int nf_far_get_arith(void);
 
-/* Destroys the cuFFT plans the far-field calls keep per (device, K, p), e.g.
- * before cudaDeviceReset or to return cuFFT's tables; later calls create them
- * again (so the next call must not be captured into a graph).  Call only
- * when no far-field work is being enqueued.  Always NF_OK. */
+/* Releases what the far-field calls keep between calls.  The transforms are
+ * the library's own kernels and keep no plans or tables of their own, so
+ * there is nothing to release; kept so that callers written for earlier
+ * versions still link.  Always NF_OK. */
 int nf_far_release(void);
 
 /* ------------------------------------------------------------------------ */
@@ -409,8 +414,8 @@ int nf_kdk_step(float *pos, float *vel, float *acc, int64_t N, double box, int K
  * input positions.  derivs comes from nf_derivatives for (K, R, p, box) (the
  * far field, Sec. "Far-field Computation"); ws is
  * a near-field workspace (nf_workspace_bytes(N, K, R)) and ws_far a far-field
- * one (nf_far_workspace_bytes(N, K, p)).  Graph-capturable once the cuFFT
- * plans for (K, p) exist.  Errors as nf_kdk_step and nf_far_forces. */
+ * one (nf_far_workspace_bytes(N, K, p)).  Graph-capturable.  Errors as
+ * nf_kdk_step and nf_far_forces. */
 int nf_kdk_step_far(float *pos, float *vel, float *acc, int64_t N, double box, int K, int R, double eps,
                     int p, const void *derivs, size_t derivs_bytes, double *dt, const nf_step_params *prm,
                     void *ws, size_t ws_bytes, void *ws_far, size_t ws_far_bytes, void *stream);
@@ -447,6 +452,18 @@ int nf_status_read(void *ws, void *stream);
  *   out[3] = sink lanes issued (32 * sinks_per_lane rounded up per chunk),
  *            so out[0] / (out[3] * sources) measures lane utilisation. */
 int nf_stats_read(void *ws, int64_t *out, void *stream);
+
+/* Stages of the pair kernel in the last force, adjoint or density call that
+ * used `ws` (a measurement aid; no counterpart in the paper), host array
+ * out[3], after a stream synchronisation:
+ *   out[0] = stages (a warp's pass over one batch of staged sources);
+ *   out[1] = stages computed on the exact path from the start (the sources of
+ *            the work item's own cell: self pairs and the closest neighbours);
+ *   out[2] = stages computed on the fast path (f = r^-3) and computed again on
+ *            the exact path because a pair closer than eps_s met there
+ *            (Eq. (spline)).
+ * Returns NF_ERR_ARG for NULL pointers, NF_ERR_CUDA if a CUDA call fails. */
+int nf_stage_stats_read(void *ws, int64_t *out, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* Measurement                                                               */

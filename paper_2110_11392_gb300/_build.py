@@ -22,7 +22,7 @@ PROBE_SRC = os.path.join(CSRC, "probe", "fma_probe.cu")
 PROBE_LIB = os.path.join(PKG, "libnf_probe.so")
 HEADERS = ["nf_internal.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-LINK_LIBS = ["-lcufft"]  # the far field's 3-D FFTs
+LINK_LIBS: List[str] = []
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
 

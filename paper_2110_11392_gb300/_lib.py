@@ -85,8 +85,11 @@ def load(build: bool = True) -> ctypes.CDLL:
         "nf_forces_adjoint_batched": (i32, [P, i32, P, P, P, P, P, sz, P]),
         "nf_set_default_tuning": (i32, [P]),
         "nf_get_default_tuning": (None, [P]),
+        "nf_set_default_tuning_adjoint": (i32, [P]),
+        "nf_get_default_tuning_adjoint": (None, [P]),
         "nf_status_read": (i32, [P, P]),
         "nf_stats_read": (i32, [P, P, P]),
+        "nf_stage_stats_read": (i32, [P, P, P]),
         "nf_profile_enable": (i32, [i32]),
         "nf_profile_read": (i32, [i32, P]),
         "nf_kernel_launches": (i64, []),
@@ -120,7 +123,8 @@ def exported_symbols() -> Sequence[str]:
     return ("nf_last_error", "nf_version", "nf_workspace_bytes", "nf_workspace_bytes_batched",
             "nf_bin", "nf_forces", "nf_forces_adjoint", "nf_forces_batched",
             "nf_forces_adjoint_batched", "nf_set_default_tuning", "nf_get_default_tuning",
-            "nf_status_read", "nf_stats_read", "nf_profile_enable", "nf_profile_read",
+            "nf_set_default_tuning_adjoint", "nf_get_default_tuning_adjoint",
+            "nf_status_read", "nf_stats_read", "nf_stage_stats_read", "nf_profile_enable", "nf_profile_read",
             "nf_kernel_launches", "nf_forces_noalloc", "nf_forces_density", "nf_timestep",
             "nf_kdk_step", "nf_multipoles", "nf_set_debug", "nf_debug_check",
             "nf_derivatives_bytes", "nf_far_workspace_bytes", "nf_derivatives", "nf_far_forces",
@@ -245,6 +249,18 @@ def nf_get_default_tuning() -> tuple:
     return t.as_tuple()
 
 
+def nf_set_default_tuning_adjoint(tune) -> None:
+    t = make_tuning(tune)
+    _check(load().nf_set_default_tuning_adjoint(ctypes.byref(t) if t is not None else None),
+           "nf_set_default_tuning_adjoint")
+
+
+def nf_get_default_tuning_adjoint() -> tuple:
+    t = nf_tuning()
+    load().nf_get_default_tuning_adjoint(ctypes.byref(t))
+    return t.as_tuple()
+
+
 def nf_status_read(ws: torch.Tensor, stream=None) -> int:
     return int(load().nf_status_read(_ptr(ws), _stream(stream)))
 
@@ -254,6 +270,12 @@ def nf_stats_read(ws: torch.Tensor, stream=None) -> dict:
     _check(load().nf_stats_read(_ptr(ws), out, _stream(stream)), "nf_stats_read")
     return {"pairs": int(out[0]), "items": int(out[1]), "max_occupancy": int(out[2]),
             "lane_pairs": int(out[3])}
+
+
+def nf_stage_stats_read(ws: torch.Tensor, stream=None) -> dict:
+    out = (ctypes.c_int64 * 3)()
+    _check(load().nf_stage_stats_read(_ptr(ws), out, _stream(stream)), "nf_stage_stats_read")
+    return {"stages": int(out[0]), "exact": int(out[1]), "rerun": int(out[2])}
 
 
 def nf_profile_enable(on: bool) -> None:

@@ -99,7 +99,13 @@ cudaError_t prof_mark(int i, cudaStream_t s)
     }
     return cudaEventRecord(ev, s);
 }
-ForceTuning g_default_tuning = {2, 128, 8, 0};
+// Built-in tunings, measured best on GB300 (clustered 128^3 and 512^3 boxes):
+// the forward prefers four sinks per lane, the adjoint (more registers per
+// sink) two.
+constexpr ForceTuning kBuiltinTuning = {4, 128, 8, 0};
+constexpr ForceTuning kBuiltinTuningAdj = {2, 128, 8, 0};
+ForceTuning g_default_tuning = kBuiltinTuning;
+ForceTuning g_default_tuning_adj = kBuiltinTuningAdj;
 
 int fail(int code, const char* fmt, ...)
 {
@@ -273,10 +279,10 @@ T* at(void* ws, size_t off)
     return reinterpret_cast<T*>(static_cast<char*>(ws) + off);
 }
 
-int check_tuning(const nf_tuning* t, ForceTuning* out)
+int check_tuning(const nf_tuning* t, ForceTuning* out, bool adjoint = false)
 {
     if (!t) {
-        *out = g_default_tuning;
+        *out = adjoint ? g_default_tuning_adj : g_default_tuning;
         return NF_OK;
     }
     ForceTuning f = {t->sinks_per_lane, t->stage, t->warps_per_block, t->blocks_per_sm};
@@ -410,7 +416,7 @@ int forces_entry(const nf_box* boxes, int nboxes, bool adjoint, const float* pos
 {
     g_last_error.clear();
     ForceTuning t;
-    int rc = check_tuning(tune, &t);
+    int rc = check_tuning(tune, &t, adjoint);
     if (rc) return rc;
     Plan p;
     rc = make_plan(boxes, nboxes, true, 32 * t.sinks_per_lane, &p);
@@ -550,23 +556,48 @@ int nf_set_default_tuning(const nf_tuning* t)
 {
     g_last_error.clear();
     if (!t) {
-        g_default_tuning = ForceTuning{2, 128, 8, 0};
+        g_default_tuning = kBuiltinTuning;
+        g_default_tuning_adj = kBuiltinTuningAdj;
         return NF_OK;
     }
     ForceTuning f;
     int rc = check_tuning(t, &f);
     if (rc) return rc;
     g_default_tuning = f;
+    g_default_tuning_adj = f;
     return NF_OK;
+}
+
+int nf_set_default_tuning_adjoint(const nf_tuning* t)
+{
+    g_last_error.clear();
+    if (!t) {
+        g_default_tuning_adj = kBuiltinTuningAdj;
+        return NF_OK;
+    }
+    ForceTuning f;
+    int rc = check_tuning(t, &f);
+    if (rc) return rc;
+    g_default_tuning_adj = f;
+    return NF_OK;
+}
+
+static void copy_tuning(const ForceTuning& f, nf_tuning* t)
+{
+    t->sinks_per_lane = f.sinks_per_lane;
+    t->stage = f.stage;
+    t->warps_per_block = f.warps_per_block;
+    t->blocks_per_sm = f.blocks_per_sm;
 }
 
 void nf_get_default_tuning(nf_tuning* t)
 {
-    if (!t) return;
-    t->sinks_per_lane = g_default_tuning.sinks_per_lane;
-    t->stage = g_default_tuning.stage;
-    t->warps_per_block = g_default_tuning.warps_per_block;
-    t->blocks_per_sm = g_default_tuning.blocks_per_sm;
+    if (t) copy_tuning(g_default_tuning, t);
+}
+
+void nf_get_default_tuning_adjoint(nf_tuning* t)
+{
+    if (t) copy_tuning(g_default_tuning_adj, t);
 }
 
 int nf_forces_noalloc(const float* pos, int64_t N, double box, int K, int R, double eps, float* acc, double* net,
@@ -683,10 +714,11 @@ struct DerivLayout {
     int nt = 0, nr = 0;
     long long npairs = 0, nnz = 0;
     size_t o_seg = 0, o_pairs = 0, o_dh = 0, o_rseg = 0, o_rk = 0, o_rcoef = 0, o_ops = 0, o_opf = 0, total = 0;
-    size_t o_drdf = 0, o_pcdf = 0, o_tw = 0;  // double-float transform path (power-of-two K) only
+    size_t o_drdf = 0, o_pcdf = 0, o_tw = 0;  // double-float path: derivatives, pair coefficients, twiddles
+    size_t o_tw64 = 0;                        // FP64 twiddles
 };
 
-// K^3 and, for the cuFFT plans' 32-bit element offsets, n_t K^3 below 2^31
+// K^3 and n_t K^3 below 2^31 (32-bit field offsets)
 bool far_args_ok(int K, int p)
 {
     if (K < 1 || p < 0 || p > NF_MAX_FAR_ORDER) return false;
@@ -734,17 +766,16 @@ DerivLayout deriv_layout(int K, int p)
     L.o_ops = take(sizeof(int4) * (size_t)L.nt);
     L.o_opf = take(sizeof(double2) * (size_t)L.nt);
     L.o_dh = take(8 * (size_t)L.nt * K * K * (K / 2 + 1));  // one real per (term, frequency)
-    if (far_df_fft(K)) {
-        L.o_drdf = take(8 * (size_t)L.nt * K * K * (K / 2 + 1));  // the same as double-float pairs
-        L.o_pcdf = take(8 * (size_t)L.npairs);
-        L.o_tw = take(16 * (size_t)(K / 2));
-    }
+    L.o_drdf = take(8 * (size_t)L.nt * K * K * (K / 2 + 1));  // the same as double-float pairs
+    L.o_pcdf = take(8 * (size_t)L.npairs);
+    L.o_tw = take(16 * (size_t)K);
+    L.o_tw64 = take(16 * (size_t)K);
     L.total = o;
     return L;
 }
 
 struct FarLayout {
-    size_t o_M = 0, o_Mr = 0, o_Mh = 0, o_Th = 0, o_Tdf = 0, o_m002 = 0, o_s002 = 0, o_work = 0, work = 0, total = 0;
+    size_t o_M = 0, o_Mr = 0, o_Mh = 0, o_Th = 0, o_Tdf = 0, o_m002 = 0, o_s002 = 0, total = 0;
 };
 
 // The far-field regions follow the binning plan's; in debug mode each is
@@ -754,8 +785,7 @@ struct FarLayout {
 // (FP64, or a double-float pair on the double-float transform path); Mh, Th:
 // spectra [nr][nq], 16 bytes each (FP64 complex or double-float complex);
 // Tdf: double-float Taylor pairs [C][nt]; m002: each cell's (0,0,2)
-// multipole [C]; s002: partial sums of the (0,0,2) multipoles; then the
-// cuFFT work area (unused on the double-float transform path).
+// multipole [C]; s002: partial sums of the (0,0,2) multipoles.
 FarLayout far_layout(const Plan& pl, int K, int p, std::vector<size_t>* guards = nullptr)
 {
     FarLayout F;
@@ -779,10 +809,6 @@ FarLayout far_layout(const Plan& pl, int K, int p, std::vector<size_t>* guards =
     F.o_Tdf = take(8 * (size_t)nt * cells);
     F.o_m002 = take(8 * cells);
     F.o_s002 = take(8 * (size_t)far_sum_partials());
-    // the derivatives' transform (nt fields) and the far call's (nr fields) share the area
-    const size_t w1 = far_fft_work_bytes(K, nt), w2 = far_fft_work_bytes(K, nr);
-    F.work = w1 > w2 ? w1 : w2;
-    F.o_work = take(F.work);
     F.total = o;
     return F;
 }
@@ -812,12 +838,6 @@ int far_validate(int K, int R, int p, double box)
 
 namespace {
 
-int fft_fail(cudaError_t e, const char* where)
-{
-    if (e == cudaErrorMemoryAllocation) return fail(NF_ERR_WORKSPACE, "%s: cuFFT work area larger than reserved", where);
-    if (e == cudaErrorUnknown) return fail(NF_ERR_CUDA, "%s: cuFFT status %d", where, far_fft_last_status());
-    return cuda_fail(e, where);
-}
 
 }  // namespace
 
@@ -835,8 +855,7 @@ int nf_far_get_arith(void) { return g_far_arith.load(); }
 int nf_far_release(void)
 {
     g_last_error.clear();
-    far_release_plans();
-    return NF_OK;
+    return NF_OK;  // the library keeps no transform plans (its transforms are its own kernels)
 }
 
 size_t nf_derivatives_bytes(int K, int p)
@@ -883,11 +902,18 @@ int nf_derivatives(int K, int R, int p, double box, void* derivs, size_t derivs_
     // the first one are contiguous and large enough (checked below)
     double* D = at<double>(ws, F.o_M);
     double2* Dh = at<double2>(ws, F.o_Mr);
-    if (F.o_Mr + 16 * (size_t)L.nt * K * K * (K / 2 + 1) > F.o_work)
+    if (F.o_Mr + 16 * (size_t)L.nt * K * K * (K / 2 + 1) > F.total)
         return fail(NF_ERR_WORKSPACE, "internal: derivative spectrum does not fit the far workspace");
+    {
+        // the FP64 twiddles first: the derivatives' transform below reads them
+        const std::vector<double2> tw64 = far_twiddles64(K);
+        NF_CUDA(cudaMemcpyAsync(at<char>(derivs, L.o_tw64), tw64.data(), sizeof(double2) * tw64.size(),
+                                cudaMemcpyHostToDevice, s),
+                "far tables");
+    }
     NF_CUDA(launch_deriv_real(K, R, p, box, alpha, kFarNimg, D, s), "derivatives (real space)");
-    cudaError_t e = launch_far_fft(K, L.nt, true, D, Dh, at<void>(ws, F.o_work), F.work, s);
-    if (e != cudaSuccess) return fft_fail(e, "derivatives (forward FFT)");
+    NF_CUDA(launch_far_fft64(K, L.nt, true, D, Dh, nullptr, at<double2>(derivs, L.o_tw64), s),
+            "derivatives (forward transform)");
     NF_CUDA(launch_deriv_recip(K, p, box, alpha, kFarHmax, Dh, at<double>(derivs, L.o_dh), s),
             "derivatives (reciprocal space)");
     {
@@ -907,7 +933,7 @@ int nf_derivatives(int K, int R, int p, double box, void* derivs, size_t derivs_
         NF_CUDA(up(L.o_rcoef, tb.red_coef.data(), 8 * tb.red_coef.size()), "far tables");
         NF_CUDA(up(L.o_ops, tb.ops.data(), sizeof(int4) * tb.ops.size()), "far tables");
         NF_CUDA(up(L.o_opf, tb.opf.data(), sizeof(double2) * tb.opf.size()), "far tables");
-        if (L.o_drdf) {
+        {
             const std::vector<float4> tw = far_twiddles(K);
             NF_CUDA(up(L.o_pcdf, tb.pair_cdf.data(), sizeof(float2) * tb.pair_cdf.size()), "far tables");
             NF_CUDA(up(L.o_tw, tw.data(), sizeof(float4) * tw.size()), "far tables");
@@ -941,6 +967,7 @@ int nf_derivatives(int K, int R, int p, double box, void* derivs, size_t derivs_
     h.o_drdf = L.o_drdf;
     h.o_pcdf = L.o_pcdf;
     h.o_tw = L.o_tw;
+    h.o_tw64 = L.o_tw64;
     h.total = L.total;
     NF_CUDA(launch_deriv_header(h, derivs, s), "derivatives header");
     {
@@ -1037,8 +1064,8 @@ int run_far(const FarCall& fc, const float* pos, int64_t N, double box, int K, i
     const int* rk = static_cast<const int*>(dat(L.o_rk));
     const double* rcoef = static_cast<const double*>(dat(L.o_rcoef));
     const int i002 = p >= 2 ? 2 : -1;  // (0,0,2): the third term of the complete basis (a, then b, then c)
-    // double-float mode, power-of-two K: the transforms and the k-space product in double-float too
-    const bool dft = dfl && L.o_drdf != 0;
+    // double-float mode: the transforms and the k-space product in double-float too
+    const bool dft = dfl;
     if (dfl) {
         // the fold runs inside the multipole kernel; each cell's (0,0,2) term is kept for its sum
         double* m002 = at<double>(ws, F.o_m002);
@@ -1062,14 +1089,13 @@ int run_far(const FarCall& fc, const float* pos, int64_t N, double box, int K, i
                 "convolution");
         NF_CUDA(launch_far_fft_df(K, L.nr, false, nullptr, Th, Mr, tw, s), "Taylors (inverse transform)");
     } else {
-        cudaError_t e = launch_far_fft(K, L.nr, true, Mr, Mh, at<void>(ws, F.o_work), F.work, s);
-        if (e != cudaSuccess) return fft_fail(e, "multipoles (forward FFT)");
+        const double2* tw64 = static_cast<const double2*>(dat(L.o_tw64));
+        NF_CUDA(launch_far_fft64(K, L.nr, true, Mr, Mh, nullptr, tw64, s), "multipoles (forward transform)");
         NF_CUDA(launch_far_contract(K, L.nr, static_cast<const int*>(dat(L.o_seg)),
                                     static_cast<const FarPair*>(dat(L.o_pairs)),
                                     static_cast<const double*>(dat(L.o_dh)), Mh, Th, s),
                 "convolution");
-        e = launch_far_fft(K, L.nr, false, Th, Mr, at<void>(ws, F.o_work), F.work, s);
-        if (e != cudaSuccess) return fft_fail(e, "Taylors (inverse FFT)");
+        NF_CUDA(launch_far_fft64(K, L.nr, false, nullptr, Th, Mr, tw64, s), "Taylors (inverse transform)");
     }
     double* T = M;  // the complete multipoles are no longer needed: the rebuilt Taylors go there
     const bool pairs_needed = dfl && (acc_far || acc_add);
@@ -1263,6 +1289,21 @@ int nf_profile_read(int back, nf_profile* out)
 }
 
 int64_t nf_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+int nf_stage_stats_read(void* ws, int64_t* out, void* stream)
+{
+    g_last_error.clear();
+    if (!ws || !out) return fail(NF_ERR_ARG, "null pointer argument");
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "stage stats sync");
+    WsHeader h;
+    e = cudaMemcpy(&h, ws, sizeof h, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "stage stats read");
+    out[0] = (int64_t)h.stages;
+    out[1] = (int64_t)h.stages_exact;
+    out[2] = (int64_t)h.stages_rerun;
+    return NF_OK;
+}
 
 int nf_stats_read(void* ws, int64_t* out, void* stream)
 {

@@ -35,10 +35,9 @@
 // forward transforms of D and of the multipoles; the inverse transform gives
 // T in every cell.  The convolution runs on the (p+1)^2 reduced terms (see
 // far_tables) and the complete Taylors are rebuilt per cell
-// (k_far_rebuild).  The transforms are this file's double-float kernels
-// (k_fft_*) for a power-of-two K in double-float mode, cuFFT's FP64
-// transforms (a plain library transform) otherwise; every other step is a
-// kernel of this file.  The per-particle work runs in cell units
+// (k_far_rebuild).  The transforms are this file's kernels: radix-4/2 ones
+// in double-float for a power-of-two K (k_fft_*), mixed-radix ones for any K
+// in double-float or FP64 (k_gfft_*); every step is a kernel of this file.  The per-particle work runs in cell units
 // (multipoles of the stored offsets x / w, Taylors T'^n = T^n w^{|n|}); the
 // factors w^{|n|+|k|} live in the convolution's coefficients.
 //
@@ -46,12 +45,11 @@
 // a = m sum_n T^n grad(x^n) = (m / w) sum_n T'^n grad'(x'^n), x' the
 // particle's FP32 cell-centred offset, evaluated by nested Horner schemes in
 // z, y and x (k_taylor_forces).  The derivatives are FP64.  The rest is
-// FP64 (k_multipoles in nf_multipole.cu, k_far_reduce, cuFFT,
+// FP64 (k_multipoles in nf_multipole.cu, k_far_reduce, k_gfft_*,
 // k_far_contract, k_taylor_forces) or double-float on the FP32 pipe
-// (k_multipoles_red_df, k_fft_*, k_far_contract_df, k_taylor_forces_df), as
-// the caller selects.
+// (k_multipoles_red_df, k_fft_* or k_gfft_*, k_far_contract_df,
+// k_taylor_forces_df), as the caller selects.
 #include <cuda_runtime.h>
-#include <cufft.h>
 
 #include <cmath>
 #include <map>
@@ -500,14 +498,15 @@ __device__ __forceinline__ dfl df_from(double v)
 }
 
 // ---- double-float transforms and k-space product ---------------------------
-// GB300's FP64 pipe makes cuFFT's double-precision transforms and the FP64
-// k-space product the slow part of the convolution.  For power-of-two K they
-// run here in double-float on the FP32 pipe instead: a complex value is a
+// GB300's FP64 pipe makes double-precision transforms and the FP64 k-space
+// product the slow part of the convolution.  In double-float mode they run on
+// the FP32 pipe instead (for a power-of-two K with these kernels, otherwise
+// with the mixed-radix ones below): a complex value is a
 // float4 {re.h, re.l, im.h, im.l}.  The 3-D real transform is three passes of
 // 1-D transforms over lines held in shared memory (bit-reversed on load,
 // pairs of radix-2 stages done as one radix-4 step with one __syncthreads,
 // twiddles e^{-2 pi i j/K} as double-float pairs built on the host from FP64
-// cos/sin).  Layouts are cuFFT's: the real
+// cos/sin).  Layouts: the real
 // side is cell-major [x][y][z][field], the spectrum term-major
 // [field][x][y][kz] with kz in 0..K/2; forward is e^{-i...}, the inverse is
 // unnormalised (the 1/K^3 sits in the k-space product).
@@ -729,12 +728,13 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_z_inv(const float4* __restr
 
 // The k-space product of k_far_contract in double-float: derivatives and
 // pair coefficients as double-float pairs, spectra as double-float complex;
-// scale (1/K^3, a power of two) is exact on both halves.
+// the scale 1/K^3 is a double-float pair (for K a power of two one float,
+// exact on both halves).
 __global__ void __launch_bounds__(256) k_far_contract_df(long long nq, int nout, const int* __restrict__ seg,
                                                          const FarPair* __restrict__ pairs,
                                                          const float2* __restrict__ pcoef,
                                                          const dfl* __restrict__ Dr, const float4* __restrict__ Mh,
-                                                         float4* __restrict__ Th, float scale)
+                                                         float4* __restrict__ Th, float2 scale, bool pow2)
 {
     const long long total = nq * nout;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
@@ -754,7 +754,13 @@ __global__ void __launch_bounds__(256) k_far_contract_df(long long nq, int nout,
             re = df_fma(odd ? df_neg(cd) : cd, mr, re);
             im = df_fma(cd, mi, im);
         }
-        Th[e] = make_float4(re.h * scale, re.l * scale, im.h * scale, im.l * scale);
+        if (pow2) {  // 1/K^3 is a power of two: exact on each half
+            Th[e] = make_float4(re.h * scale.x, re.l * scale.x, im.h * scale.x, im.l * scale.x);
+        } else {
+            const dfl sc = {scale.x, scale.y};
+            const dfl r = df_mul(re, sc), i = df_mul(im, sc);
+            Th[e] = make_float4(r.h, r.l, i.h, i.l);
+        }
     }
 }
 
@@ -1143,57 +1149,6 @@ int device_sms()
     return sms > 0 ? sms : 1;
 }
 
-// ---- cuFFT plans: one per (device, K, nt, direction), cell-major real side
-struct PlanEntry {
-    cufftHandle h = 0;
-    size_t work = 0;
-};
-std::mutex g_fft_mu;
-std::map<std::tuple<int, int, int, int>, PlanEntry> g_plans;
-thread_local int g_cufft_status = 0;  // cuFFT's status of the last failed transform
-
-cufftResult plan_layout(int K, int nt, bool forward, cufftHandle h, size_t* work, bool estimate_only)
-{
-    int n[3] = {K, K, K};
-    int real_emb[3] = {K, K, K};
-    int cplx_emb[3] = {K, K, K / 2 + 1};
-    const int cdist = K * K * (K / 2 + 1);
-    if (forward) {
-        if (estimate_only)
-            return cufftEstimateMany(3, n, real_emb, nt, 1, cplx_emb, 1, cdist, CUFFT_D2Z, nt, work);
-        return cufftMakePlanMany(h, 3, n, real_emb, nt, 1, cplx_emb, 1, cdist, CUFFT_D2Z, nt, work);
-    }
-    if (estimate_only) return cufftEstimateMany(3, n, cplx_emb, 1, cdist, real_emb, nt, 1, CUFFT_Z2D, nt, work);
-    return cufftMakePlanMany(h, 3, n, cplx_emb, 1, cdist, real_emb, nt, 1, CUFFT_Z2D, nt, work);
-}
-
-cudaError_t get_plan(int K, int nt, bool forward, PlanEntry* out)
-{
-    int dev = 0;
-    cudaGetDevice(&dev);
-    const auto key = std::make_tuple(dev, K, nt, forward ? 1 : 0);
-    auto it = g_plans.find(key);
-    if (it != g_plans.end()) {
-        *out = it->second;
-        return cudaSuccess;
-    }
-    PlanEntry pe;
-    cufftResult r = cufftCreate(&pe.h);
-    if (r != CUFFT_SUCCESS) {
-        g_cufft_status = (int)r;
-        return cudaErrorUnknown;
-    }
-    r = cufftSetAutoAllocation(pe.h, 0);
-    if (r == CUFFT_SUCCESS) r = plan_layout(K, nt, forward, pe.h, &pe.work, false);
-    if (r != CUFFT_SUCCESS) {
-        g_cufft_status = (int)r;
-        cufftDestroy(pe.h);
-        return cudaErrorUnknown;
-    }
-    g_plans[key] = pe;
-    *out = pe;
-    return cudaSuccess;
-}
 
 }  // namespace
 
@@ -1300,62 +1255,328 @@ FarTables far_tables(int p, double w)
     return tb;
 }
 
-size_t far_fft_work_bytes(int K, int nt)
+// ---- mixed-radix transforms for any K ---------------------------------------
+// The same 3-D real transforms as above (layouts of the power-of-two kernels:
+// real side cell-major [x][y][z][field], spectrum [field][x][y][kz], kz <=
+// K/2; forward e^{-i...}, the inverse unnormalised) for any K, in IEEE FP64
+// (the derivatives tensor, and the FP64 mode) or in double-float (K not a
+// power of two).  Each 1-D transform runs on lines held in shared memory as a
+// self-sorting Stockham sequence of radix-R steps over the factors of K
+// (fours first, then 2, 3, 5, 7, then any larger prime): with Ns the product
+// of the radices already done, step j (j < K/R) reads a[j + r K/R] times
+// W_K^{r k K/(Ns R)} (k = j mod Ns) for r < R, forms their R-point DFT by
+// definition (roots W_K^{(q m mod R) K/R}), and writes it to
+// y[(j - k) R + k + m Ns]; natural order in and out, two buffers in turn.
+// The real z lines are transformed as complex lines with zero imaginary
+// parts; the inverse z pass rebuilds the whole Hermitian line from kz <= K/2
+// (dropping the imaginary parts at kz = 0 and K/2, as a complex-to-real
+// transform does) and keeps the real parts.
+namespace {
+
+struct ArF64 {
+    typedef double real_t;
+    typedef double2 spec_t;
+    struct cx {
+        double re, im;
+    };
+    static __device__ __forceinline__ cx ld(spec_t v) { return {v.x, v.y}; }
+    static __device__ __forceinline__ spec_t st(cx v) { return make_double2(v.re, v.im); }
+    static __device__ __forceinline__ cx from_real(real_t v) { return {v, 0.0}; }
+    static __device__ __forceinline__ real_t real(cx v) { return v.re; }
+    static __device__ __forceinline__ cx conj(cx v) { return {v.re, -v.im}; }
+    static __device__ __forceinline__ cx no_im(cx v) { return {v.re, 0.0}; }
+    static __device__ __forceinline__ cx add(cx a, cx b) { return {a.re + b.re, a.im + b.im}; }
+    static __device__ __forceinline__ cx mul(cx w, cx x)
+    {
+        return {fma(w.re, x.re, -w.im * x.im), fma(w.re, x.im, w.im * x.re)};
+    }
+};
+
+struct ArDF {
+    typedef dfl real_t;
+    typedef float4 spec_t;
+    typedef cdf cx;
+    static __device__ __forceinline__ cx ld(spec_t v) { return cdf_ld(v); }
+    static __device__ __forceinline__ spec_t st(cx v) { return cdf_st(v); }
+    static __device__ __forceinline__ cx from_real(real_t v) { return {v, dfl{0.0f, 0.0f}}; }
+    static __device__ __forceinline__ real_t real(cx v) { return v.re; }
+    static __device__ __forceinline__ cx conj(cx v) { return {v.re, df_neg(v.im)}; }
+    static __device__ __forceinline__ cx no_im(cx v) { return {v.re, dfl{0.0f, 0.0f}}; }
+    static __device__ __forceinline__ cx add(cx a, cx b) { return cdf_add(a, b); }
+    static __device__ __forceinline__ cx mul(cx w, cx x) { return cdf_mul(w, x); }
+};
+
+constexpr int kGPoints = 1024;  // complex points per buffer of one block
+
+__host__ __device__ inline int gfft_lines_per_block(int K) { return K >= kGPoints ? 1 : kGPoints / K; }
+
+template <class A, bool INV>
+__device__ __forceinline__ typename A::cx gtw(const typename A::cx* tw, int j)
 {
-    // Cached per (K, nt): the size query that sizes a workspace always comes
-    // first, so a call being captured into a CUDA graph never asks cuFFT (its
-    // estimate is not a capture-safe call).
-    static std::mutex mu;
-    static std::map<std::pair<int, int>, size_t> cache;
-    std::lock_guard<std::mutex> lk(mu);
-    const auto key = std::make_pair(K, nt);
-    auto it = cache.find(key);
-    if (it != cache.end()) return it->second;
-    size_t w1 = 0, w2 = 0;
-    const bool ok = plan_layout(K, nt, true, 0, &w1, true) == CUFFT_SUCCESS &&
-                    plan_layout(K, nt, false, 0, &w2, true) == CUFFT_SUCCESS;
-    const size_t data = (size_t)nt * K * K * (K / 2 + 1) * 16;
-    size_t w = ok ? (w1 > w2 ? w1 : w2) : data;
-    // keep a margin: cuFFT's estimate is an upper bound, a made plan may choose differently
-    w += (w >> 2) + (1u << 20);
-    cache[key] = w;
-    return w;
+    return INV ? A::conj(tw[j]) : tw[j];
 }
 
-cudaError_t launch_far_fft(int K, int nt, bool forward, void* in, void* out, void* work, size_t work_bytes,
-                           cudaStream_t s)
+// One radix-R step for the point j of a line (R known at compile time).
+template <class A, bool INV, int R>
+__device__ __forceinline__ void gfft_step(const typename A::cx* a, typename A::cx* y, const typename A::cx* tw, int K,
+                                          int KR, int Ns, int j)
 {
-    std::lock_guard<std::mutex> lk(g_fft_mu);
-    PlanEntry pe;
-    cudaError_t e = get_plan(K, nt, forward, &pe);
-    if (e != cudaSuccess) return e;
-    if (pe.work > work_bytes) return cudaErrorMemoryAllocation;
-    cufftResult r = cufftSetStream(pe.h, s);
-    if (r == CUFFT_SUCCESS) r = cufftSetWorkArea(pe.h, work);
-    if (r == CUFFT_SUCCESS)
-        r = forward ? cufftExecD2Z(pe.h, (cufftDoubleReal*)in, (cufftDoubleComplex*)out)
-                    : cufftExecZ2D(pe.h, (cufftDoubleComplex*)in, (cufftDoubleReal*)out);
-    if (r != CUFFT_SUCCESS) {
-        g_cufft_status = (int)r;
-        return cudaErrorUnknown;
+    typedef typename A::cx cx;
+    const int k = j % Ns, step = KR / Ns;  // K / (Ns R)
+    cx v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const cx x = a[j + r * KR];
+        v[r] = r ? A::mul(gtw<A, INV>(tw, r * k * step), x) : x;
     }
+    const int o = (j - k) * R + k;
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+        cx acc = v[0];
+#pragma unroll
+        for (int q = 1; q < R; ++q) acc = A::add(acc, A::mul(gtw<A, INV>(tw, ((q * m) % R) * KR), v[q]));
+        y[o + m * Ns] = acc;
+    }
+}
+
+// The same for a radix known only at run time (a prime factor above 7).
+template <class A, bool INV>
+__device__ void gfft_step_any(const typename A::cx* a, typename A::cx* y, const typename A::cx* tw, int K, int R,
+                              int KR, int Ns, int j)
+{
+    typedef typename A::cx cx;
+    const int k = j % Ns, step = KR / Ns;
+    const int o = (j - k) * R + k;
+    for (int m = 0; m < R; ++m) {
+        cx acc = a[j];
+        for (int q = 1; q < R; ++q) {
+            const cx x = A::mul(gtw<A, INV>(tw, q * k * step), a[j + q * KR]);
+            acc = A::add(acc, A::mul(gtw<A, INV>(tw, ((q * m) % R) * KR), x));
+        }
+        y[o + m * Ns] = acc;
+    }
+}
+
+// Transforms nl lines of K points in b0 (natural order); returns the buffer
+// that holds the result (b0 or b1).
+template <class A, bool INV>
+__device__ typename A::cx* gfft_stages(typename A::cx* b0, typename A::cx* b1, int nl, int K, const Radices& rd,
+                                       const typename A::cx* tw)
+{
+    typedef typename A::cx cx;
+    cx* src = b0;
+    cx* dst = b1;
+    int Ns = 1;
+    for (int st = 0; st < rd.n; ++st) {
+        const int R = rd.r[st], KR = K / R;
+        for (int idx = threadIdx.x; idx < nl * KR; idx += blockDim.x) {
+            const int l = idx / KR, j = idx - l * KR;
+            const cx* a = src + (size_t)l * K;
+            cx* y = dst + (size_t)l * K;
+            switch (R) {
+                case 2: gfft_step<A, INV, 2>(a, y, tw, K, KR, Ns, j); break;
+                case 3: gfft_step<A, INV, 3>(a, y, tw, K, KR, Ns, j); break;
+                case 4: gfft_step<A, INV, 4>(a, y, tw, K, KR, Ns, j); break;
+                case 5: gfft_step<A, INV, 5>(a, y, tw, K, KR, Ns, j); break;
+                case 7: gfft_step<A, INV, 7>(a, y, tw, K, KR, Ns, j); break;
+                default: gfft_step_any<A, INV>(a, y, tw, K, R, KR, Ns, j); break;
+            }
+        }
+        __syncthreads();
+        cx* t = src;
+        src = dst;
+        dst = t;
+        Ns *= R;
+    }
+    return src;
+}
+
+// Shared memory of the generic kernels: the K twiddles, then two buffers of
+// (lines per block) x K points.
+template <class A>
+__host__ __device__ size_t gfft_smem(int K)
+{
+    return sizeof(typename A::cx) * ((size_t)K + 2ull * gfft_lines_per_block(K) * K);
+}
+
+// Forward z pass: real fields R [x][y][z][nf] -> spectrum S [nf][x][y][kz].
+template <class A>
+__global__ void __launch_bounds__(kFftThreads) k_gfft_z_fwd(const typename A::real_t* __restrict__ Rf, int K, int nf,
+                                                            int nchunk, Radices rd,
+                                                            const typename A::spec_t* __restrict__ twg,
+                                                            typename A::spec_t* __restrict__ S)
+{
+    typedef typename A::cx cx;
+    extern __shared__ __align__(16) unsigned char gsm[];
+    cx* tw = reinterpret_cast<cx*>(gsm);
+    const int FB = gfft_lines_per_block(K), H = K / 2 + 1;
+    cx* b0 = tw + K;
+    cx* b1 = b0 + (size_t)FB * K;
+    const int chunk = blockIdx.x % nchunk;
+    const long long xy = blockIdx.x / nchunk;
+    const int f0 = chunk * FB, nfc = min(FB, nf - f0);
+    for (int j = threadIdx.x; j < K; j += blockDim.x) tw[j] = A::ld(twg[j]);
+    const typename A::real_t* src = Rf + (size_t)xy * K * nf + f0;
+    for (int idx = threadIdx.x; idx < K * nfc; idx += blockDim.x) {
+        const int z = idx / nfc, fl = idx - z * nfc;
+        b0[(size_t)fl * K + z] = A::from_real(src[(size_t)z * nf + fl]);
+    }
+    __syncthreads();
+    const cx* out = gfft_stages<A, false>(b0, b1, nfc, K, rd, tw);
+    const size_t fstride = (size_t)K * K * H;
+    for (int idx = threadIdx.x; idx < nfc * H; idx += blockDim.x) {
+        const int fl = idx / H, k = idx - fl * H;
+        S[(size_t)(f0 + fl) * fstride + (size_t)xy * H + k] = A::st(out[(size_t)fl * K + k]);
+    }
+}
+
+// Complex passes along y or x, in place on S (as k_fft_lines).
+template <class A, bool INV>
+__global__ void __launch_bounds__(kFftThreads) k_gfft_lines(typename A::spec_t* __restrict__ S, int K, int nA,
+                                                            long long astride, long long pstride, int nchunk,
+                                                            Radices rd, const typename A::spec_t* __restrict__ twg)
+{
+    typedef typename A::cx cx;
+    extern __shared__ __align__(16) unsigned char gsm[];
+    cx* tw = reinterpret_cast<cx*>(gsm);
+    const int W = gfft_lines_per_block(K), H = K / 2 + 1;
+    cx* b0 = tw + K;
+    cx* b1 = b0 + (size_t)W * K;
+    const int chunk = blockIdx.x % nchunk;
+    const long long fa = blockIdx.x / nchunk;
+    const long long f = fa / nA, a = fa - f * nA;
+    const int k0 = chunk * W, wc = min(W, H - k0);
+    for (int j = threadIdx.x; j < K; j += blockDim.x) tw[j] = A::ld(twg[j]);
+    typename A::spec_t* base = S + f * (long long)K * K * H + a * astride + k0;
+    for (int idx = threadIdx.x; idx < K * wc; idx += blockDim.x) {
+        const int pt = idx / wc, w = idx - pt * wc;
+        b0[(size_t)w * K + pt] = A::ld(base[pt * pstride + w]);
+    }
+    __syncthreads();
+    const cx* out = gfft_stages<A, INV>(b0, b1, wc, K, rd, tw);
+    for (int idx = threadIdx.x; idx < K * wc; idx += blockDim.x) {
+        const int pt = idx / wc, w = idx - pt * wc;
+        base[pt * pstride + w] = A::st(out[(size_t)w * K + pt]);
+    }
+}
+
+// Inverse z pass: spectrum S (kz <= K/2) -> real fields R [x][y][z][nf].
+template <class A>
+__global__ void __launch_bounds__(kFftThreads) k_gfft_z_inv(const typename A::spec_t* __restrict__ S, int K, int nf,
+                                                            int nchunk, Radices rd,
+                                                            const typename A::spec_t* __restrict__ twg,
+                                                            typename A::real_t* __restrict__ Rf)
+{
+    typedef typename A::cx cx;
+    extern __shared__ __align__(16) unsigned char gsm[];
+    cx* tw = reinterpret_cast<cx*>(gsm);
+    const int FB = gfft_lines_per_block(K), H = K / 2 + 1;
+    cx* b0 = tw + K;
+    cx* b1 = b0 + (size_t)FB * K;
+    const int chunk = blockIdx.x % nchunk;
+    const long long xy = blockIdx.x / nchunk;
+    const int f0 = chunk * FB, nfc = min(FB, nf - f0);
+    for (int j = threadIdx.x; j < K; j += blockDim.x) tw[j] = A::ld(twg[j]);
+    const size_t fstride = (size_t)K * K * H;
+    for (int idx = threadIdx.x; idx < nfc * K; idx += blockDim.x) {
+        const int fl = idx / K, k = idx - fl * K;
+        const typename A::spec_t* row = S + (size_t)(f0 + fl) * fstride + (size_t)xy * H;
+        cx v;
+        if (k < H) {
+            v = A::ld(row[k]);
+            if (k == 0 || 2 * k == K) v = A::no_im(v);
+        } else {
+            v = A::conj(A::ld(row[K - k]));  // Hermitian symmetry of a real field
+        }
+        b0[(size_t)fl * K + k] = v;
+    }
+    __syncthreads();
+    const cx* out = gfft_stages<A, true>(b0, b1, nfc, K, rd, tw);
+    typename A::real_t* dst = Rf + (size_t)xy * K * nf + f0;
+    for (int idx = threadIdx.x; idx < K * nfc; idx += blockDim.x) {
+        const int z = idx / nfc, fl = idx - z * nfc;
+        dst[(size_t)z * nf + fl] = A::real(out[(size_t)fl * K + z]);
+    }
+}
+
+template <class A>
+cudaError_t launch_gfft(int K, int nf, bool forward, const void* real_in, void* spec, void* real_out, const void* tw,
+                        cudaStream_t s)
+{
+    typedef typename A::spec_t spec_t;
+    typedef typename A::real_t real_t;
+    const Radices rd = far_radices(K);
+    const int H = K / 2 + 1, FB = gfft_lines_per_block(K);
+    const size_t smem = gfft_smem<A>(K);
+    const spec_t* twg = static_cast<const spec_t*>(tw);
+    spec_t* S = static_cast<spec_t*>(spec);
+    const int zchunks = (nf + FB - 1) / FB, lchunks = (H + FB - 1) / FB;
+    const long long zblocks = (long long)K * K * zchunks, lblocks = (long long)nf * K * lchunks;
+    const long long KH = (long long)K * H;
+    cudaError_t e;
+    if (forward) {
+        e = ensure_smem((const void*)k_gfft_z_fwd<A>, (int)smem);
+        if (e == cudaSuccess) e = ensure_smem((const void*)k_gfft_lines<A, false>, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_gfft_z_fwd<A><<<(unsigned)zblocks, kFftThreads, smem, s>>>(static_cast<const real_t*>(real_in), K, nf,
+                                                                      zchunks, rd, twg, S);
+        k_gfft_lines<A, false><<<(unsigned)lblocks, kFftThreads, smem, s>>>(S, K, K, KH, H, lchunks, rd, twg);
+        k_gfft_lines<A, false><<<(unsigned)lblocks, kFftThreads, smem, s>>>(S, K, K, H, KH, lchunks, rd, twg);
+    } else {
+        e = ensure_smem((const void*)k_gfft_z_inv<A>, (int)smem);
+        if (e == cudaSuccess) e = ensure_smem((const void*)k_gfft_lines<A, true>, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_gfft_lines<A, true><<<(unsigned)lblocks, kFftThreads, smem, s>>>(S, K, K, H, KH, lchunks, rd, twg);
+        k_gfft_lines<A, true><<<(unsigned)lblocks, kFftThreads, smem, s>>>(S, K, K, KH, H, lchunks, rd, twg);
+        k_gfft_z_inv<A><<<(unsigned)zblocks, kFftThreads, smem, s>>>(S, K, nf, zchunks, rd, twg,
+                                                                      static_cast<real_t*>(real_out));
+    }
+    count_launches(3);
     return cudaGetLastError();
 }
 
-int far_fft_last_status() { return g_cufft_status; }
+}  // namespace
 
-void far_release_plans()
+Radices far_radices(int K)
 {
-    std::lock_guard<std::mutex> lk(g_fft_mu);
-    int cur = 0;
-    cudaGetDevice(&cur);
-    for (auto& kv : g_plans) {
-        cudaSetDevice(std::get<0>(kv.first));
-        cufftDestroy(kv.second.h);
+    Radices rd{};
+    int n = K;
+    auto push = [&](int r) { rd.r[rd.n++] = r; };
+    while (n % 4 == 0) {
+        push(4);
+        n /= 4;
     }
-    g_plans.clear();
-    cudaSetDevice(cur);
+    for (int r : {2, 3, 5, 7}) {
+        while (n % r == 0) {
+            push(r);
+            n /= r;
+        }
+    }
+    for (int r = 11; n > 1; r += 2) {
+        while (n % r == 0) {
+            push(r);
+            n /= r;
+        }
+    }
+    return rd;
 }
+
+std::vector<double2> far_twiddles64(int K)
+{
+    std::vector<double2> tw(K);
+    for (int j = 0; j < K; ++j) {
+        const double th = 2.0 * 3.14159265358979323846 * j / K;
+        tw[j] = make_double2(std::cos(th), -std::sin(th));
+    }
+    return tw;
+}
+
+cudaError_t launch_far_fft64(int K, int nf, bool forward, const double* real_in, double2* spec, double* real_out,
+                             const double2* tw, cudaStream_t s)
+{
+    return launch_gfft<ArF64>(K, nf, forward, real_in, spec, real_out, tw, s);
+}
+
 
 cudaError_t launch_deriv_real(int K, int R, int p, double box, double alpha, int nimg, double* D, cudaStream_t s)
 {
@@ -1387,8 +1608,8 @@ bool far_df_fft(int K) { return K >= 4 && K <= 256 && (K & (K - 1)) == 0; }
 
 std::vector<float4> far_twiddles(int K)
 {
-    std::vector<float4> tw(K / 2);
-    for (int j = 0; j < K / 2; ++j) {
+    std::vector<float4> tw(K);
+    for (int j = 0; j < K; ++j) {
         const double th = 2.0 * 3.14159265358979323846 * j / K;
         const double c = std::cos(th), sn = -std::sin(th);
         const float ch = (float)c, sh = (float)sn;
@@ -1400,7 +1621,7 @@ std::vector<float4> far_twiddles(int K)
 cudaError_t launch_far_fft_df(int K, int nf, bool forward, const void* real_in, void* spec, void* real_out,
                               const void* tw, cudaStream_t s)
 {
-    if (!far_df_fft(K)) return cudaErrorInvalidValue;
+    if (!far_df_fft(K)) return launch_gfft<ArDF>(K, nf, forward, real_in, spec, real_out, tw, s);
     int logK = 0;
     while ((1 << logK) < K) ++logK;
     const int H = K / 2 + 1, FB = fft_lines_per_block(K);
@@ -1440,10 +1661,14 @@ cudaError_t launch_far_contract_df(int K, int nout, const int* seg, const FarPai
     long long blocks = (nq * nout + 255) / 256;
     const long long cap = (long long)device_sms() * 64;
     if (blocks > cap) blocks = cap;
-    const float scale = 1.0f / ((float)K * K * K);  // the unnormalised inverse transform; exact for K = 2^n
+    // the unnormalised inverse transform's 1/K^3, as a double-float pair (one float when K = 2^n)
+    const double sd = 1.0 / ((double)K * K * K);
+    const float sh = (float)sd;
+    const float2 scale = make_float2(sh, (float)(sd - (double)sh));
+    const bool pow2 = (K & (K - 1)) == 0;
     k_far_contract_df<<<(int)blocks, 256, 0, s>>>(nq, nout, seg, pairs, static_cast<const float2*>(pcoef),
                                                   static_cast<const dfl*>(Dr), static_cast<const float4*>(Mh),
-                                                  static_cast<float4*>(Th), scale);
+                                                  static_cast<float4*>(Th), scale, pow2);
     count_launches(1);
     return cudaGetLastError();
 }

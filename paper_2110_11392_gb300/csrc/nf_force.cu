@@ -43,7 +43,7 @@
 // it met; if any lane saw r < eps_s, the warp recomputes the stage with the
 // exact path.  Stages with the item's own centre cell (self pairs) always
 // take the exact path: the source list puts that cell first, in stages of
-// its own.
+// its own; the other source cells follow in rings around it (c_ring).
 #include <cuda_runtime.h>
 
 #include "nf_internal.cuh"
@@ -92,6 +92,21 @@ __device__ __forceinline__ int find_box_by_part(const BoxDev* boxes, int nboxes,
     }
     return lo;
 }
+
+// Source cells of an item, (b, d) offsets in the plane, in rings around the
+// centre: the centre, its 8 neighbours, then rings 2, 3, 4 (the first
+// (2R+1)^2 entries are exactly the cells of the stencil for any R <= 4).
+// A ball of radius at most one cell around a sink of the pencil reaches only
+// the centre and its first ring, so the density estimate needs only those.
+__constant__ signed char c_ring[81][2] = {
+    {0, 0}, {-1, -1}, {-1, 0}, {-1, 1}, {0, -1}, {0, 1}, {1, -1}, {1, 0}, {1, 1}, {-2, -2}, {-2, -1}, {-2, 0},
+    {-2, 1}, {-2, 2}, {-1, -2}, {-1, 2}, {0, -2}, {0, 2}, {1, -2}, {1, 2}, {2, -2}, {2, -1}, {2, 0}, {2, 1},
+    {2, 2}, {-3, -3}, {-3, -2}, {-3, -1}, {-3, 0}, {-3, 1}, {-3, 2}, {-3, 3}, {-2, -3}, {-2, 3}, {-1, -3}, {-1, 3},
+    {0, -3}, {0, 3}, {1, -3}, {1, 3}, {2, -3}, {2, 3}, {3, -3}, {3, -2}, {3, -1}, {3, 0}, {3, 1}, {3, 2},
+    {3, 3}, {-4, -4}, {-4, -3}, {-4, -2}, {-4, -1}, {-4, 0}, {-4, 1}, {-4, 2}, {-4, 3}, {-4, 4}, {-3, -4}, {-3, 4},
+    {-2, -4}, {-2, 4}, {-1, -4}, {-1, 4}, {0, -4}, {0, 4}, {1, -4}, {1, 4}, {2, -4}, {2, 4}, {3, -4}, {3, 4},
+    {4, -4}, {4, -3}, {4, -2}, {4, -1}, {4, 0}, {4, 1}, {4, 2}, {4, 3}, {4, 4}};
+static_assert(NF_MAX_R <= 4, "the ring table covers R <= 4");
 
 __device__ __forceinline__ int cell_count(const int* off, int cid, int* start)
 {
@@ -218,12 +233,14 @@ struct Coef {
 typedef unsigned long long f2;
 
 // Where r^-2 comes from in the fast paths: 1 = MUFU reciprocal, 0 = r^-1 * r^-1
-// on the FMA pipe (measured per direction on GB300).
+// on the FMA pipe.  Measured on GB300: the MUFU unit (16 lanes per clock per
+// SM) is already the second bottleneck beside the FMA pipe with one rsqrt per
+// pair, so both directions take r^-2 from the FMA pipe.
 #ifndef NF_FWD_RCP
 #define NF_FWD_RCP 0
 #endif
 #ifndef NF_ADJ_RCP
-#define NF_ADJ_RCP 1
+#define NF_ADJ_RCP 0
 #endif
 // Unroll depth of the fast pair loops over groups of four sources.
 #ifndef NF_FWD_UNROLL
@@ -311,9 +328,9 @@ __device__ __forceinline__ f2 tophat2(f2 r2, f2 b2)
     return pk(fmaxf(lo(t), 0.0f), fmaxf(hi(t), 0.0f));
 }
 
-// Forward, fast path: f = r^-3 for every pair; tracks the smallest r^2.
+// Forward, fast path: f = r^-3 for every pair; TRK tracks the smallest r^2.
 // DENS adds the top-hat density estimate as a 4th sum.
-template <int S, bool DENS>
+template <int S, bool DENS, bool TRK = true>
 __device__ __forceinline__ void stage_fwd_fast(const StageView& v, int cnt, SinkSet<S>& k, float& trk, f2 b2)
 {
     const f2 tiny = pk(kTiny, kTiny);
@@ -331,7 +348,7 @@ __device__ __forceinline__ void stage_fwd_fast(const StageView& v, int cnt, Sink
                 f2 r2 = fma2(dx, dx, tiny);
                 r2 = fma2(dy, dy, r2);
                 r2 = fma2(dz, dz, r2);
-                trk = fminf(trk, fminf(lo(r2), hi(r2)));
+                if constexpr (TRK) trk = fminf(trk, fminf(lo(r2), hi(r2)));
                 if constexpr (DENS) k.sw[s] = add2(k.sw[s], tophat2(r2, b2));
 #if NF_FWD_RCP
                 const f2 f = mul2(rcp2(r2), rsqrt2(r2));
@@ -380,8 +397,9 @@ __device__ __forceinline__ void stage_fwd_exact(const StageView& v, int cnt, Sin
     }
 }
 
-// Adjoint, fast path: J v = r^-3 (v - 3 r^-2 (d.v) d), v = g_j - g_i.
-template <int S>
+// Adjoint, fast path: J v = r^-3 (v - 3 r^-2 (d.v) d), v = g_j - g_i; TRK
+// tracks the smallest r^2.
+template <int S, bool TRK = true>
 __device__ __forceinline__ void stage_adj_fast(const StageView& v, int cnt, SinkSet<S>& k, float& trk)
 {
     const f2 tiny = pk(kTiny, kTiny);
@@ -404,7 +422,7 @@ __device__ __forceinline__ void stage_adj_fast(const StageView& v, int cnt, Sink
                 f2 r2 = fma2(dx, dx, tiny);
                 r2 = fma2(dy, dy, r2);
                 r2 = fma2(dz, dz, r2);
-                trk = fminf(trk, fminf(lo(r2), hi(r2)));
+                if constexpr (TRK) trk = fminf(trk, fminf(lo(r2), hi(r2)));
 #if NF_ADJ_RCP
                 const f2 ri2 = rcp2(r2);
                 const f2 ri3 = mul2(ri2, rsqrt2(r2));
@@ -519,6 +537,7 @@ struct ItemCtx {
     int chunk_begin;
     int n_src;
     int n_c0;         // sources of the centre cell (processed first, exact path)
+    int n_near;       // sources of the centre cell and its first ring
 };
 
 // Sorted slot and partial slot of the sink at pencil position p.
@@ -550,7 +569,7 @@ __device__ __forceinline__ void run_item(const ItemCtx& it, const Coef& cf, f2 b
                                          const float4* __restrict__ rel, const float4* __restrict__ gs,
                                          const WarpBufs& wb, const int* seg_pre,
                                          const int* seg_start, const float* seg_dy, const float* seg_dz,
-                                         float* __restrict__ partial, int Ntot)
+                                         float* __restrict__ partial, int Ntot, unsigned (&ctr)[3])
 {
     constexpr int NC = WarpSmem<B, ADJ>::NC;
     const int lane = threadIdx.x & 31;
@@ -577,6 +596,8 @@ __device__ __forceinline__ void run_item(const ItemCtx& it, const Coef& cf, f2 b
     }
 
     constexpr int PER = B / 32;
+    const bool dens_near_only = lo(b2) <= 1.0f;    // b <= one cell width
+    const bool soft_near_only = cf.eps2 <= 1.0f;   // eps_s <= one cell width
     const int nst0 = (it.n_c0 + B - 1) / B;
     const int nst = nst0 + (it.n_src - it.n_c0 + B - 1) / B;
     int cur = 0;
@@ -657,19 +678,36 @@ __device__ __forceinline__ void run_item(const ItemCtx& it, const Coef& cf, f2 b
         v.GY = reinterpret_cast<const float4*>(soa + (ADJ ? 4 : 0) * B);
         v.GZ = reinterpret_cast<const float4*>(soa + (ADJ ? 5 : 0) * B);
         bool exact = st < nst0;
+        // Sources of ring 2 and beyond are at least one cell away from every
+        // sink of the pencil: the top-hat (b <= one cell) and the softened
+        // branch (eps_s <= one cell) cannot occur there.
+        const bool far = beg >= it.n_near;
+        const bool dens = DENS && (!dens_near_only || !far);
         if (!exact) {
 #pragma unroll
             for (int s = 0; s < S; ++s) k.sx[s] = k.sy[s] = k.sz[s] = k.sw[s] = 0ull;
             float trk = kBig;
-            if constexpr (ADJ) stage_adj_fast<S>(v, cnt, k, trk);
-            else stage_fwd_fast<S, DENS>(v, cnt, k, trk, b2);
-            exact = __any_sync(kFull, trk < cf.eps2);
+            if (far && soft_near_only) {
+                if constexpr (ADJ) stage_adj_fast<S, false>(v, cnt, k, trk);
+                else if (dens) stage_fwd_fast<S, DENS, false>(v, cnt, k, trk, b2);
+                else stage_fwd_fast<S, false, false>(v, cnt, k, trk, b2);
+            } else {
+                if constexpr (ADJ) stage_adj_fast<S>(v, cnt, k, trk);
+                else if (dens) stage_fwd_fast<S, DENS>(v, cnt, k, trk, b2);
+                else stage_fwd_fast<S, false>(v, cnt, k, trk, b2);
+                exact = __any_sync(kFull, trk < cf.eps2);
+                ctr[2] += exact ? 1u : 0u;
+            }
+        } else {
+            ctr[1] += 1u;
         }
+        ctr[0] += 1u;
         if (exact) {
 #pragma unroll
             for (int s = 0; s < S; ++s) k.sx[s] = k.sy[s] = k.sz[s] = k.sw[s] = 0ull;
             if constexpr (ADJ) stage_adj_exact<S>(v, cnt, k, cf);
-            else stage_fwd_exact<S, DENS>(v, cnt, k, cf, b2);
+            else if (dens) stage_fwd_exact<S, DENS>(v, cnt, k, cf, b2);
+            else stage_fwd_exact<S, false>(v, cnt, k, cf, b2);
         }
 #pragma unroll
         for (int s = 0; s < S; ++s) {
@@ -719,11 +757,19 @@ k_force(const BoxDev* __restrict__ boxes, const int* __restrict__ off, const flo
 
     const int n_items = *((volatile int*)&hdr->n_items);
     constexpr int CH = 32 * SMAX;
+    unsigned ctr[3] = {0u, 0u, 0u};  // stages, exact from the start, re-run exactly (warp-uniform)
     for (;;) {
         int itn = 0;
         if (lane == 0) itn = atomicAdd(&hdr->queue, 1);
         itn = __shfl_sync(kFull, itn, 0);
-        if (itn >= n_items) break;
+        if (itn >= n_items) {
+            if (lane == 0) {
+                atomicAdd(&hdr->stages, (unsigned long long)ctr[0]);
+                atomicAdd(&hdr->stages_exact, (unsigned long long)ctr[1]);
+                atomicAdd(&hdr->stages_rerun, (unsigned long long)ctr[2]);
+            }
+            break;
+        }
         const int4 item = items[itn];
         const BoxDev& Bx = boxes[item.z];
         ItemCtx it;
@@ -759,16 +805,15 @@ k_force(const BoxDev* __restrict__ boxes, const int* __restrict__ off, const flo
         it.sc_incl = incl;
         it.n_sink = __shfl_sync(kFull, incl, it.ns - 1);
         it.chunk_begin = item.y * CH;
-        // source segments: centre cell first, then (b, d) in row order without it
+        // source segments: the plane's cells in rings around the centre (c_ring)
         const int nseg = it.ns * it.ns;
         int carry = 0;
         for (int base = 0; base < nseg; base += 32) {
             const int q = base + lane;
             int cnt = 0, st = 0, b = 0, d = 0;
             if (q < nseg) {
-                int r = q == 0 ? (nseg >> 1) : (q <= (nseg >> 1) ? q - 1 : q);
-                b = r / it.ns - R;
-                d = r % it.ns - R;
+                b = c_ring[q][0];
+                d = c_ring[q][1];
                 cnt = cell_count(off, it.cb + (it.i * K + wrap(it.j + b, K)) * K + wrap(it.k + d, K), &st);
             }
             int inc = cnt;
@@ -789,19 +834,20 @@ k_force(const BoxDev* __restrict__ boxes, const int* __restrict__ off, const flo
         it.n_src = carry;
         __syncwarp();
         it.n_c0 = seg_pre[1];
+        it.n_near = seg_pre[nseg < 9 ? nseg : 9];
         const int n_chunk = min(CH, it.n_sink - it.chunk_begin);
         const int S = (n_chunk + 31) >> 5;
         if (SMAX >= 4 && S >= 4)
             run_item<(SMAX >= 4 ? 4 : 1), B, ADJ, DENS>(it, cf, b2, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz,
-                                                  partial, Ntot);
+                                                  partial, Ntot, ctr);
         else if (SMAX >= 3 && S == 3)
             run_item<(SMAX >= 3 ? 3 : 1), B, ADJ, DENS>(it, cf, b2, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz,
-                                                  partial, Ntot);
+                                                  partial, Ntot, ctr);
         else if (SMAX >= 2 && S == 2)
             run_item<(SMAX >= 2 ? 2 : 1), B, ADJ, DENS>(it, cf, b2, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz,
-                                                  partial, Ntot);
+                                                  partial, Ntot, ctr);
         else
-            run_item<1, B, ADJ, DENS>(it, cf, b2, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz, partial, Ntot);
+            run_item<1, B, ADJ, DENS>(it, cf, b2, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz, partial, Ntot, ctr);
         __syncwarp();
     }
 }
@@ -841,6 +887,7 @@ k_combine(const BoxDev* __restrict__ boxes, int nboxes, const float* __restrict_
     const float s_hi = (float)scale;
     const float s_lo = (float)(scale - (double)s_hi);
     const double m = 1.0 / (double)B.N;
+    const bool out_aligned8 = (reinterpret_cast<uintptr_t>(out) & 7) == 0;
     const int s0 = B.part_base + (chunk - B.chunk_base) * kCombineChunk;
     const int s1 = min(s0 + kCombineChunk, B.part_base + B.N);
     double net[3] = {0.0, 0.0, 0.0};
@@ -854,6 +901,7 @@ k_combine(const BoxDev* __restrict__ boxes, int nboxes, const float* __restrict_
 #pragma unroll
             for (int q = 0; q < kMaxSlots; ++q)
                 v[c][q] = q < nslot ? partial[((size_t)q * 4 + c) * (size_t)Ntot + s] : 0.0f;
+        float a3[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             // the 2R+1 pencil partials, summed without rounding error into (sh, sl)
@@ -871,8 +919,22 @@ k_combine(const BoxDev* __restrict__ boxes, int nboxes, const float* __restrict_
             const float p = __fmul_rn(sh, s_hi);
             const float perr = __fmaf_rn(sh, s_hi, -p);
             const float a = __fadd_rn(p, __fmaf_rn(sh, s_lo, __fmaf_rn(sl, s_hi, perr)));
-            out[3 * (size_t)e + c] = a;
+            a3[c] = a;
             if (chunk_sums) net[c] += m * (double)a;
+        }
+        // the particle's row goes out in two stores (its 12 bytes start 8-byte
+        // aligned for even e, 4 bytes past it for odd e)
+        float* row = out + 3 * (size_t)e;
+        if (out_aligned8 && (e & 1) == 0) {
+            *reinterpret_cast<float2*>(row) = make_float2(a3[0], a3[1]);
+            row[2] = a3[2];
+        } else if (out_aligned8) {
+            row[0] = a3[0];
+            *reinterpret_cast<float2*>(row + 1) = make_float2(a3[1], a3[2]);
+        } else {
+            row[0] = a3[0];
+            row[1] = a3[1];
+            row[2] = a3[2];
         }
         if (rho) {
             // density partials (b^2 - r^2 sums), compensated, times 1/b^2

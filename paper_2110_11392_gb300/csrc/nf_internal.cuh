@@ -62,7 +62,9 @@ struct WsHeader {
     int guard_count;
     int pad0;
     long long guard_off[24];
-    int pad1[6];
+    // pair-kernel stages: all, on the exact path from the start (the item's own
+    // cell), and re-run on the exact path after the fast path met r < eps_s
+    unsigned long long stages, stages_exact, stages_rerun;
 };
 static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
 
@@ -108,8 +110,9 @@ struct DerivHeader {
     unsigned long long o_seg, o_pairs, o_dh, total;  // reduced pair segments and pairs, transformed derivatives
     unsigned long long o_rseg, o_rk, o_rcoef, o_ops, o_opf;  // fold and rebuild tables
     long long nnz;
-    unsigned long long o_drdf, o_pcdf, o_tw;  // double-float derivatives, pair coefficients, twiddles (K = 2^n)
-    unsigned long long pad[12];
+    unsigned long long o_drdf, o_pcdf, o_tw;  // double-float derivatives, pair coefficients, twiddles
+    unsigned long long o_tw64;                 // FP64 twiddles
+    unsigned long long pad[11];
 };
 static_assert(sizeof(DerivHeader) == 256, "derivatives header is 256 bytes");
 constexpr unsigned kDerivMagic = 0x4E464452u;
@@ -142,13 +145,20 @@ int far_sum_partials();
 cudaError_t launch_far_rebuild(const void* Tr, bool df_in, int C, int p, int nt, int nr, const int4* ops,
                                const double2* opf, int t002, double lap, double t0_per_s002, const double* partial,
                                double* T, void* Tdf, cudaStream_t s);
-// cuFFT work-area bytes to reserve for the forward and inverse transforms of nt fields on K^3
-size_t far_fft_work_bytes(int K, int nt);
-// forward: real cell-major [K^3][nt] -> complex term-major [nt][K][K][K/2+1]; inverse the reverse
-cudaError_t launch_far_fft(int K, int nt, bool forward, void* in, void* out, void* work, size_t work_bytes,
-                           cudaStream_t s);
-int far_fft_last_status();   // cuFFT status behind the last cudaErrorUnknown of launch_far_fft
-void far_release_plans();    // destroys every cached cuFFT plan
+// Factors of K in the order the mixed-radix transforms take them (fours, then
+// 2, 3, 5, 7, then any larger prime).
+struct Radices {
+    int n;
+    int r[24];
+};
+Radices far_radices(int K);
+// e^{-2 pi i j / K}, j < K, in FP64
+std::vector<double2> far_twiddles64(int K);
+// FP64 3-D transforms for any K: forward, real cell-major [K^3][nf] -> complex
+// term-major [nf][K][K][K/2+1]; inverse (unnormalised) the reverse (spec is
+// overwritten); tw = far_twiddles64(K) in device memory
+cudaError_t launch_far_fft64(int K, int nf, bool forward, const double* real_in, double2* spec, double* real_out,
+                             const double2* tw, cudaStream_t s);
 cudaError_t launch_deriv_real(int K, int R, int p, double box, double alpha, int nimg, double* D, cudaStream_t s);
 cudaError_t launch_deriv_recip(int K, int p, double box, double alpha, int hmax, const double2* Dh, double* Dr,
                                cudaStream_t s);
@@ -160,11 +170,12 @@ cudaError_t launch_unscale_taylors(const double* Tc, int C, int p, double w, dou
 cudaError_t launch_multipoles_red_df(const int* off, const float4* rel, int C, int p, const int* rseg,
                                      const int* rk, const double* rcoef, long long nnz, double* Mr, void* Mrd,
                                      double* m002, cudaStream_t s);
-// Double-float transforms for power-of-two K (4..256): forward, real cell-major
-// pairs [C][nf] -> spectrum [nf][K][K][K/2+1] of float4 {re.h, re.l, im.h, im.l};
-// inverse (unnormalised), spectrum (overwritten) -> real pairs [C][nf].
+// Double-float transforms: forward, real cell-major pairs [C][nf] -> spectrum
+// [nf][K][K][K/2+1] of float4 {re.h, re.l, im.h, im.l}; inverse (unnormalised),
+// spectrum (overwritten) -> real pairs [C][nf].  Radix-4/2 kernels for a
+// power-of-two K (4..256, far_df_fft), the mixed-radix ones otherwise.
 bool far_df_fft(int K);
-std::vector<float4> far_twiddles(int K);  // e^{-2 pi i j/K}, j < K/2, as double-float pairs
+std::vector<float4> far_twiddles(int K);  // e^{-2 pi i j/K}, j < K, as double-float pairs
 cudaError_t launch_far_fft_df(int K, int nf, bool forward, const void* real_in, void* spec, void* real_out,
                               const void* tw, cudaStream_t s);
 // the k-space product on double-float spectra (pcoef: the pairs' coefficients as float2 pairs)

@@ -53,7 +53,7 @@ def test_tuner_pick_cache_and_parity(tmp_path):
     assert run.tune is not None and run.tune_timings is not None
     assert run.tune_timings[_key(run.tune)] == min(run.tune_timings.values())
     acc = acc.cpu().numpy()
-    old = _lib.nf_get_default_tuning()
+    old, old_adj = _lib.nf_get_default_tuning(), _lib.nf_get_default_tuning_adjoint()
     _lib.nf_set_default_tuning(run.tune)
     try:
         off = 0
@@ -68,6 +68,7 @@ def test_tuner_pick_cache_and_parity(tmp_path):
             off += bw.N
     finally:
         _lib.nf_set_default_tuning(old)
+        _lib.nf_set_default_tuning_adjoint(old_adj)
 
 
 def test_auto_tuning_then_graph_capture(tmp_path):

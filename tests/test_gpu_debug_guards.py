@@ -89,7 +89,7 @@ def test_far_field_entries_keep_their_guards():
         _lib.nf_kdk_step_far(pos.clone(), vel, acc, w.box, w.K, w.R, w.eps, 6, ff.derivs, dt, None, ws, wsf)
         assert _lib.nf_status_read(wsf) == _lib.NF_OK and _lib.nf_status_read(ws) == _lib.NF_OK
         assert torch.equal(far, ref_far) and torch.equal(tot, ref_tot)
-        # an overwrite in the last guard (after the cuFFT work area) is caught
+        # an overwrite in the last guard (after the last far-field region) is caught
         wsf[wsf.numel() - 100] = 0
         _lib.nf_debug_check(wsf)
         assert _lib.nf_status_read(wsf) == _lib.NF_ERR_CORRUPT
