@@ -170,6 +170,7 @@ int make_box(const nf_box& in, bool need_force, BoxDev* out)
         if (m > 0 && m < (1LL << 29)) {
             b.kl_mant = (int)m;
             b.kl_exp = ex;
+            if (m == 1 && ex >= -100 && ex <= 100) b.kl_pow2 = (float)b.kl;
         }
     }
     const double w = in.box / in.K;

@@ -86,6 +86,20 @@ __device__ __forceinline__ int cell_coord_fp64(float x, double kl, int K, float*
 // take the FP64 path; both give identical results.
 __device__ __forceinline__ int cell_coord(float x, const BoxDev& B, float* off, bool* bad)
 {
+    // K / box a power of two and x >= 0: t = x * K/box is exact in FP32 as in
+    // FP64, so are c = floor(t) and t - c (for t >= 0), and one FP32
+    // subtraction rounds (t - c) - 1/2 exactly as the FP64 rule's final
+    // rounding does.  (For t < 0, t - floor(t) can round in FP32.)
+    if (B.kl_pow2 != 0.0f) {
+        const float t = __fmul_rn(x, B.kl_pow2);
+        if (t >= 0.0f && t < 1073741824.0f) {  // false for NaN
+            const float c = floorf(t);
+            *off = __fsub_rn(__fsub_rn(t, c), 0.5f);
+            const int ci = (int)c;
+            if (ci < B.K) return ci;
+            return ci % B.K;
+        }
+    }
     const unsigned bits = __float_as_uint(x);
     const int E = (int)((bits >> 23) & 0xFF);
     if (B.kl_mant > 0 && E >= 127 - 29 && E < 127 + 30) {

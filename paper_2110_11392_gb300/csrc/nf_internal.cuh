@@ -46,7 +46,9 @@ struct BoxDev {
     int kl_mant, kl_exp;
     // top-hat density estimate (Sec. "Force Kernel"): b^2 and 1/b^2 in cell units
     float dens_b2, dens_inv_b2;
-    float pad0, pad1;
+    // K / box when it is a power of two (then x * K / box is exact in FP32), else 0
+    float kl_pow2;
+    float pad1;
 };
 static_assert(sizeof(BoxDev) % 16 == 0, "BoxDev must stay 16-byte aligned");
 
