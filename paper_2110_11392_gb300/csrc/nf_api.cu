@@ -366,7 +366,7 @@ int run_forces(const Plan& p, bool adjoint, const ForceTuning& t, const float* p
     unsigned* bucket_count = at<unsigned>(ws, p.o_bucket_count);
     NF_CUDA(cudaMemsetAsync(bucket_count, 0, 4 * kBuckets, s), "clear buckets");
     const int CH = 32 * t.sinks_per_lane;
-    NF_CUDA(launch_pencils(boxes, p.nboxes, (int)p.C, off, CH, at<int>(ws, p.o_chunks), bucket_count,
+    NF_CUDA(launch_pencils(boxes, p.nboxes, (int)p.C, off, CH, t.stage, at<int>(ws, p.o_chunks), bucket_count,
                            at<unsigned char>(ws, p.o_bucket_of), hdr, s),
             "pencils");
     NF_CUDA(launch_items(boxes, p.nboxes, (int)p.C, at<int>(ws, p.o_chunks), at<unsigned char>(ws, p.o_bucket_of),

@@ -82,16 +82,6 @@ __device__ __forceinline__ int find_box_by_cell(const BoxDev* boxes, int nboxes,
     return lo;
 }
 
-__device__ __forceinline__ int find_box_by_part(const BoxDev* boxes, int nboxes, int e)
-{
-    int lo = 0, hi = nboxes - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (boxes[mid].part_base <= e) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
 
 // Source cells of an item, (b, d) offsets in the plane, in rings around the
 // centre: the centre, its 8 neighbours, then rings 2, 3, 4 (the first
@@ -128,11 +118,11 @@ __device__ __forceinline__ int cost_bucket(unsigned long long cost)
 // ---------------------------------------------------------------------------
 
 __global__ void k_pencils(const BoxDev* __restrict__ boxes, int nboxes, int Ctot,
-                          const int* __restrict__ off, int CH, int* __restrict__ chunks,
+                          const int* __restrict__ off, int CH, int SB, int* __restrict__ chunks,
                           unsigned* __restrict__ bucket_count, unsigned char* __restrict__ bucket_of,
                           WsHeader* hdr)
 {
-    unsigned long long pairs = 0, lane_pairs = 0;
+    unsigned long long pairs = 0, lane_pairs = 0, stages = 0, stages_exact = 0;
     int max_occ = 0;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < Ctot; g += gridDim.x * blockDim.x) {
         const BoxDev& B = boxes[find_box_by_cell(boxes, nboxes, g)];
@@ -155,6 +145,11 @@ __global__ void k_pencils(const BoxDev* __restrict__ boxes, int nboxes, int Ctot
         bucket_of[g] = (unsigned char)bk;
         if (nch) atomicAdd(&bucket_count[bk], (unsigned)nch);
         pairs += (unsigned long long)n_sink * (unsigned long long)n_src;
+        // every chunk of this pencil runs the centre cell's sources in stages of their
+        // own (exact path) and the rest in stages of SB (the pair kernel's stage_range)
+        const int st0 = (occ + SB - 1) / SB;
+        stages += (unsigned long long)nch * (unsigned long long)(st0 + (n_src - occ + SB - 1) / SB);
+        stages_exact += (unsigned long long)nch * (unsigned long long)st0;
         if (nch) {
             int rem = n_sink - (nch - 1) * CH;
             unsigned long long lanes = (unsigned long long)(nch - 1) * CH + 32ull * ((rem + 31) / 32);
@@ -164,11 +159,15 @@ __global__ void k_pencils(const BoxDev* __restrict__ boxes, int nboxes, int Ctot
     for (int o = 16; o; o >>= 1) {
         pairs += __shfl_xor_sync(kFull, pairs, o);
         lane_pairs += __shfl_xor_sync(kFull, lane_pairs, o);
+        stages += __shfl_xor_sync(kFull, stages, o);
+        stages_exact += __shfl_xor_sync(kFull, stages_exact, o);
         max_occ = max(max_occ, __shfl_xor_sync(kFull, max_occ, o));
     }
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(&hdr->pairs, pairs);
         atomicAdd(&hdr->lane_pairs, lane_pairs);
+        atomicAdd(&hdr->stages, stages);
+        atomicAdd(&hdr->stages_exact, stages_exact);
         atomicMax(&hdr->max_occ, max_occ);
     }
 }
@@ -258,6 +257,8 @@ __device__ __forceinline__ f2 pk(float lo, float hi)
     asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
     return r;
 }
+// one half of a packed pair (the unpack names both halves; one is unused)
+#pragma nv_diag_suppress 550
 __device__ __forceinline__ float lo(f2 v)
 {
     float a, b;
@@ -270,6 +271,7 @@ __device__ __forceinline__ float hi(f2 v)
     asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
     return b;
 }
+#pragma nv_diag_default 550
 __device__ __forceinline__ f2 add2(f2 a, f2 b)
 {
     f2 d;
@@ -295,6 +297,21 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 __device__ __forceinline__ f2 rsqrt2(f2 v) { return pk(rsqrt_approx(lo(v)), rsqrt_approx(hi(v))); }
+// Smallest r^2 met so far, updated with both halves of a packed r^2: one
+// three-input min (sm_100 and later) instead of two.
+#ifndef NF_MIN3
+#define NF_MIN3 1
+#endif
+__device__ __forceinline__ float track_min(float t, f2 r2)
+{
+#if NF_MIN3
+    float m;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(m) : "f"(t), "f"(lo(r2)), "f"(hi(r2)));
+    return m;
+#else
+    return fminf(t, fminf(lo(r2), hi(r2)));
+#endif
+}
 // r^-2 from the MUFU reciprocal: keeps the FMA pipe (the bottleneck) for the sums
 __device__ __forceinline__ f2 rcp2(f2 v) { return pk(rcp_approx(lo(v)), rcp_approx(hi(v))); }
 
@@ -348,7 +365,7 @@ __device__ __forceinline__ void stage_fwd_fast(const StageView& v, int cnt, Sink
                 f2 r2 = fma2(dx, dx, tiny);
                 r2 = fma2(dy, dy, r2);
                 r2 = fma2(dz, dz, r2);
-                if constexpr (TRK) trk = fminf(trk, fminf(lo(r2), hi(r2)));
+                if constexpr (TRK) trk = track_min(trk, r2);
                 if constexpr (DENS) k.sw[s] = add2(k.sw[s], tophat2(r2, b2));
 #if NF_FWD_RCP
                 const f2 f = mul2(rcp2(r2), rsqrt2(r2));
@@ -422,7 +439,7 @@ __device__ __forceinline__ void stage_adj_fast(const StageView& v, int cnt, Sink
                 f2 r2 = fma2(dx, dx, tiny);
                 r2 = fma2(dy, dy, r2);
                 r2 = fma2(dz, dz, r2);
-                if constexpr (TRK) trk = fminf(trk, fminf(lo(r2), hi(r2)));
+                if constexpr (TRK) trk = track_min(trk, r2);
 #if NF_ADJ_RCP
                 const f2 ri2 = rcp2(r2);
                 const f2 ri3 = mul2(ri2, rsqrt2(r2));
@@ -569,9 +586,8 @@ __device__ __forceinline__ void run_item(const ItemCtx& it, const Coef& cf, f2 b
                                          const float4* __restrict__ rel, const float4* __restrict__ gs,
                                          const WarpBufs& wb, const int* seg_pre,
                                          const int* seg_start, const float* seg_dy, const float* seg_dz,
-                                         float* __restrict__ partial, int Ntot, unsigned (&ctr)[3])
+                                         float* __restrict__ partial, int Ntot, WsHeader* hdr)
 {
-    constexpr int NC = WarpSmem<B, ADJ>::NC;
     const int lane = threadIdx.x & 31;
     SinkSet<S> k;
 #pragma unroll
@@ -696,12 +712,9 @@ __device__ __forceinline__ void run_item(const ItemCtx& it, const Coef& cf, f2 b
                 else if (dens) stage_fwd_fast<S, DENS>(v, cnt, k, trk, b2);
                 else stage_fwd_fast<S, false>(v, cnt, k, trk, b2);
                 exact = __any_sync(kFull, trk < cf.eps2);
-                ctr[2] += exact ? 1u : 0u;
+                if (exact && lane == 0) atomicAdd(&hdr->stages_rerun, 1ull);  // rare
             }
-        } else {
-            ctr[1] += 1u;
         }
-        ctr[0] += 1u;
         if (exact) {
 #pragma unroll
             for (int s = 0; s < S; ++s) k.sx[s] = k.sy[s] = k.sz[s] = k.sw[s] = 0ull;
@@ -757,19 +770,12 @@ k_force(const BoxDev* __restrict__ boxes, const int* __restrict__ off, const flo
 
     const int n_items = *((volatile int*)&hdr->n_items);
     constexpr int CH = 32 * SMAX;
-    unsigned ctr[3] = {0u, 0u, 0u};  // stages, exact from the start, re-run exactly (warp-uniform)
+
     for (;;) {
         int itn = 0;
         if (lane == 0) itn = atomicAdd(&hdr->queue, 1);
         itn = __shfl_sync(kFull, itn, 0);
-        if (itn >= n_items) {
-            if (lane == 0) {
-                atomicAdd(&hdr->stages, (unsigned long long)ctr[0]);
-                atomicAdd(&hdr->stages_exact, (unsigned long long)ctr[1]);
-                atomicAdd(&hdr->stages_rerun, (unsigned long long)ctr[2]);
-            }
-            break;
-        }
+        if (itn >= n_items) break;
         const int4 item = items[itn];
         const BoxDev& Bx = boxes[item.z];
         ItemCtx it;
@@ -839,15 +845,15 @@ k_force(const BoxDev* __restrict__ boxes, const int* __restrict__ off, const flo
         const int S = (n_chunk + 31) >> 5;
         if (SMAX >= 4 && S >= 4)
             run_item<(SMAX >= 4 ? 4 : 1), B, ADJ, DENS>(it, cf, b2, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz,
-                                                  partial, Ntot, ctr);
+                                                  partial, Ntot, hdr);
         else if (SMAX >= 3 && S == 3)
             run_item<(SMAX >= 3 ? 3 : 1), B, ADJ, DENS>(it, cf, b2, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz,
-                                                  partial, Ntot, ctr);
+                                                  partial, Ntot, hdr);
         else if (SMAX >= 2 && S == 2)
             run_item<(SMAX >= 2 ? 2 : 1), B, ADJ, DENS>(it, cf, b2, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz,
-                                                  partial, Ntot, ctr);
+                                                  partial, Ntot, hdr);
         else
-            run_item<1, B, ADJ, DENS>(it, cf, b2, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz, partial, Ntot, ctr);
+            run_item<1, B, ADJ, DENS>(it, cf, b2, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz, partial, Ntot, hdr);
         __syncwarp();
     }
 }
@@ -1058,11 +1064,11 @@ int force_blocks_per_sm(bool adjoint, bool density, const ForceTuning& t, int ma
     return nb;
 }
 
-cudaError_t launch_pencils(const BoxDev* boxes, int nboxes, int Ctot, const int* cell_off, int chunk,
+cudaError_t launch_pencils(const BoxDev* boxes, int nboxes, int Ctot, const int* cell_off, int chunk, int stage,
                            int* chunks, unsigned* bucket_count, unsigned char* bucket_of, WsHeader* hdr,
                            cudaStream_t s)
 {
-    k_pencils<<<grid_for(Ctot, 256), 256, 0, s>>>(boxes, nboxes, Ctot, cell_off, chunk, chunks,
+    k_pencils<<<grid_for(Ctot, 256), 256, 0, s>>>(boxes, nboxes, Ctot, cell_off, chunk, stage, chunks,
                                                   bucket_count, bucket_of, hdr);
     count_launches(1);
     cudaError_t e = cudaGetLastError();

@@ -231,7 +231,7 @@ struct ForceTuning {
 };
 
 cudaError_t launch_pencils(const BoxDev* boxes, int nboxes, int Ctot, const int* cell_off,
-                           int chunk, int* chunks, unsigned* bucket_count,
+                           int chunk, int stage, int* chunks, unsigned* bucket_count,
                            unsigned char* bucket_of, WsHeader* hdr, cudaStream_t s);
 cudaError_t launch_items(const BoxDev* boxes, int nboxes, int Ctot, const int* chunks,
                          const unsigned char* bucket_of, unsigned* bucket_count,

@@ -162,3 +162,36 @@ def test_stats_pair_count():
     assert st["pairs"] == int((n * S).sum())
     assert st["max_occupancy"] == int(n.max())
     assert st["lane_pairs"] >= st["pairs"]
+
+
+def test_stage_counters_match_the_work_list():
+    """nf_stage_stats_read: the pair kernel's stages and exact-from-start stages equal the count
+    implied by the cell occupancies (each pencil chunk runs its centre cell's sources in
+    stages of their own, the rest of the plane in stages of the tuning's size); re-runs are
+    rare and never more than the fast stages."""
+    import torch
+    from paper_2110_11392_gb300 import _lib
+    from workloads import config_adjoint
+    w = config_adjoint()
+    off, _, _ = oracle.bin_particles(w.pos, w.box, w.K)
+    n = np.diff(off).reshape(w.K, w.K, w.K).astype(np.int64)
+    R = w.R
+    sink = sum(np.roll(n, -c, axis=0) for c in range(-R, R + 1))
+    src = sum(np.roll(n, (-b, -d), axis=(1, 2)) for b in range(-R, R + 1) for d in range(-R, R + 1))
+    pos = torch.from_numpy(w.pos).cuda()
+    g = torch.from_numpy(np.ones_like(w.pos)).cuda()
+    ws = torch.empty(_lib.nf_workspace_bytes(w.N, w.K, R), dtype=torch.uint8, device="cuda")
+    out = torch.empty_like(pos)
+    for adjoint, tune in ((False, _lib.nf_get_default_tuning()), (True, _lib.nf_get_default_tuning_adjoint())):
+        S, B = tune[0], tune[1]
+        CH = 32 * S
+        nch = (sink + CH - 1) // CH
+        exact = int((nch * ((n + B - 1) // B)).sum())
+        total = int((nch * ((n + B - 1) // B + (src - n + B - 1) // B)).sum())
+        if adjoint:
+            _lib.nf_forces_adjoint(pos, g, w.box, w.K, R, w.eps, out, ws)
+        else:
+            _lib.nf_forces(pos, w.box, w.K, R, w.eps, out, None, ws)
+        st = _lib.nf_stage_stats_read(ws)
+        assert st["stages"] == total and st["exact"] == exact, (adjoint, st, total, exact)
+        assert 0 <= st["rerun"] <= total - exact
