@@ -131,6 +131,20 @@ int nf_forces(const float *pos, int64_t N, double box, int K, int R, double eps,
 int nf_forces_density(const float *pos, int64_t N, double box, int K, int R, double eps,
                       double b, float *acc, float *rho, void *ws, size_t ws_bytes, void *stream);
 
+/* Where nf_forces_density's top-hat term runs (process-wide; not thread-safe
+ * against running calls).  Both modes give bit-identical acc and rho; the
+ * choice only moves work:
+ *   1 fused     the term is added in every pair-kernel stage whose sources
+ *               can lie within b of a sink;
+ *   2 deferred  those stages track their smallest r^2 (which the softening
+ *               test needs anyway) and add the term in a second sweep over
+ *               the stage only when some pair is closer than b; cheap for a
+ *               small b (the friends-of-friends scale of the paper);
+ *   0 auto      (default) deferred for b <= w / 4, fused above.
+ * nf_set_density_mode returns NF_ERR_ARG for any other value. */
+int nf_set_density_mode(int mode);
+int nf_get_density_mode(void);
+
 /* Adjoint of nf_forces: for a loss L with g = dL/da,
  *   g     [N][3] FP32 (input), original order;
  *   grad  [N][3] FP32 (output), original order:

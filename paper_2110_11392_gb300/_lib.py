@@ -109,6 +109,8 @@ def load(build: bool = True) -> ctypes.CDLL:
         "nf_forces_total": (i32, [P, i64, f64, i32, i32, f64, i32, P, sz, P, P, sz, P, sz, P]),
         "nf_kdk_step_far": (i32, [P, P, P, i64, f64, i32, i32, f64, i32, P, sz, P, P, P, sz, P, sz, P]),
         "nf_set_debug": (i32, [i32]),
+        "nf_set_density_mode": (i32, [i32]),
+        "nf_get_density_mode": (i32, []),
         "nf_debug_check": (i32, [P, P]),
     }
     for name, (res, args) in sig.items():
@@ -129,7 +131,7 @@ def exported_symbols() -> Sequence[str]:
             "nf_kdk_step", "nf_multipoles", "nf_set_debug", "nf_debug_check",
             "nf_derivatives_bytes", "nf_far_workspace_bytes", "nf_derivatives", "nf_far_forces",
             "nf_far_profile_read", "nf_far_release", "nf_kdk_step_far", "nf_forces_total",
-            "nf_far_set_arith", "nf_far_get_arith")
+            "nf_far_set_arith", "nf_far_get_arith", "nf_set_density_mode", "nf_get_density_mode")
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -391,6 +393,17 @@ def nf_far_get_arith() -> int:
 
 def nf_far_release() -> None:
     _check(load().nf_far_release(), "nf_far_release")
+
+
+NF_DENS_AUTO, NF_DENS_FUSED, NF_DENS_DEFERRED = 0, 1, 2
+
+
+def nf_set_density_mode(mode: int) -> None:
+    _check(load().nf_set_density_mode(int(mode)), "nf_set_density_mode")
+
+
+def nf_get_density_mode() -> int:
+    return int(load().nf_get_density_mode())
 
 
 def nf_set_debug(on: bool) -> None:

@@ -52,6 +52,12 @@ thread_local std::string g_last_error;
 // starts and checked when it ends (process-wide; off by default).
 bool g_debug = false;
 
+// Top-hat density: 0 = pick per box (deferred for b <= kDensDeferCells cell
+// widths, fused above), 1 = always fused, 2 = always deferred.  Both modes
+// give bit-identical results; the choice only moves work.
+int g_dens_mode = 0;
+constexpr double kDensDeferCells = 0.25;
+
 struct GuardList {
     int count;
     long long off[24];
@@ -374,14 +380,15 @@ int run_forces(const Plan& p, bool adjoint, const ForceTuning& t, const float* p
             "work items");
     float4* gs = at<float4>(ws, p.o_gs);
     if (adjoint) NF_CUDA(launch_gather_g(g, perm, (int)p.N, gs, s), "gather g");
-    float* partial = at<float>(ws, p.o_partial);
+    float4* partial = at<float4>(ws, p.o_partial);
+    const int pstride = 2 * p.max_R + 1;  // partial row of a particle: one float4 per pencil slot
     NF_CUDA(prof_mark(2, s), "profile");
     NF_CUDA(launch_force(adjoint, rho != nullptr, t, boxes, off, rel, gs, at<int4>(ws, p.o_items), hdr, partial,
-                         (int)p.N, p.max_nseg, s),
+                         pstride, p.max_nseg, s),
             adjoint ? "adjoint kernel" : "force kernel");
     NF_CUDA(prof_mark(3, s), "profile");
     double* chunk_sums = net ? at<double>(ws, p.o_chunk_sums) : nullptr;
-    NF_CUDA(launch_combine(adjoint, boxes, p.nboxes, p.nchunks, partial, perm, (int)p.N, out, rho, chunk_sums, s),
+    NF_CUDA(launch_combine(adjoint, boxes, p.nboxes, p.nchunks, partial, pstride, out, rho, chunk_sums, s),
             "combine");
     if (net) NF_CUDA(launch_net(boxes, p.nboxes, chunk_sums, net, s), "net force");
     NF_CUDA(prof_mark(4, s), "profile");
@@ -432,6 +439,7 @@ int forces_entry(const nf_box* boxes, int nboxes, bool adjoint, const float* pos
             const double bc = dens_b / w;
             p.boxes[b].dens_b2 = (float)(bc * bc);
             p.boxes[b].dens_inv_b2 = (float)(1.0 / (bc * bc));
+            p.boxes[b].dens_defer = g_dens_mode == 2 || (g_dens_mode == 0 && bc <= kDensDeferCells);
         }
     }
     rc = check_ws(p, ws, ws_bytes);
@@ -1203,6 +1211,16 @@ int nf_kdk_step_far(float* pos, float* vel, float* acc, int64_t N, double box, i
     if (rc) return rc;
     return finish_call(ws, s);
 }
+
+int nf_set_density_mode(int mode)
+{
+    g_last_error.clear();
+    if (mode < 0 || mode > 2) return fail(NF_ERR_ARG, "density mode %d is not 0 (auto), 1 (fused) or 2 (deferred)", mode);
+    g_dens_mode = mode;
+    return NF_OK;
+}
+
+int nf_get_density_mode(void) { return g_dens_mode; }
 
 int nf_set_debug(int on)
 {

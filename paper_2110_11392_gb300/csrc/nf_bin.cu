@@ -150,12 +150,24 @@ __device__ __forceinline__ int particle_key(const float* x, int e, const BoxDev*
 }
 
 // Copies the coordinates of particles [base, base + n) into shared memory
-// (3n floats) with coalesced loads, 16 bytes at a time when aligned.
+// (3n floats) with coalesced loads, 16 bytes at a time when aligned.  A full
+// tile issues all of a thread's loads before its first store, so their
+// latencies overlap instead of adding up.
 __device__ __forceinline__ void stage_positions(const float* __restrict__ pos, size_t base, int n, float* spos)
 {
     const float* src = pos + 3 * base;
     const int nf = 3 * n;
-    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+    constexpr int kPer = 3 * kSortTile / 4 / (kSortWarps * 32);
+    static_assert(kPer * 4 * kSortWarps * 32 == 3 * kSortTile, "a tile's coordinates split evenly into float4s");
+    if (n == kSortTile && (reinterpret_cast<uintptr_t>(src) & 15) == 0 && blockDim.x == kSortWarps * 32) {
+        const float4* s4 = reinterpret_cast<const float4*>(src);
+        float4* d4 = reinterpret_cast<float4*>(spos);
+        float4 t[kPer];
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) t[r] = s4[r * kSortWarps * 32 + threadIdx.x];
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) d4[r * kSortWarps * 32 + threadIdx.x] = t[r];
+    } else if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
         const int n4 = nf >> 2;
         const float4* s4 = reinterpret_cast<const float4*>(src);
         float4* d4 = reinterpret_cast<float4*>(spos);

@@ -528,6 +528,8 @@ constexpr int kFftThreads = 256;
 constexpr int kFftPoints = 2048;  // complex points of one block's lines in shared memory
 
 __host__ __device__ inline int fft_lines_per_block(int K) { return K >= kFftPoints ? 1 : kFftPoints / K; }
+// The z passes transform lines of K/2 points: twice as many lines fit.
+__host__ __device__ inline int fft_z_lines_per_block(int K) { return fft_lines_per_block(K / 2); }
 
 // The stages over nl lines of K points in shared memory (bit-reversed order
 // in, natural order out), two radix-2 stages at a time: a thread loads four
@@ -616,7 +618,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_z_fwd(const dfl* __restrict
     float4* tw = fsm;
     float4* line = fsm + K / 2;
     const int M = K / 2, logM = logK - 1, H = M + 1;
-    const int FB = fft_lines_per_block(K);
+    const int FB = fft_z_lines_per_block(K);
     const int chunk = blockIdx.x % nchunk;
     const long long xy = blockIdx.x / nchunk;
     const int f0 = chunk * FB, nfc = min(FB, nf - f0);
@@ -690,7 +692,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_z_inv(const float4* __restr
     float4* tw = fsm;
     float4* line = fsm + K / 2;
     const int M = K / 2, logM = logK - 1, H = M + 1;
-    const int FB = fft_lines_per_block(K);
+    const int FB = fft_z_lines_per_block(K);
     const int chunk = blockIdx.x % nchunk;
     const long long xy = blockIdx.x / nchunk;
     const int f0 = chunk * FB, nfc = min(FB, nf - f0);
@@ -1624,11 +1626,12 @@ cudaError_t launch_far_fft_df(int K, int nf, bool forward, const void* real_in, 
     if (!far_df_fft(K)) return launch_gfft<ArDF>(K, nf, forward, real_in, spec, real_out, tw, s);
     int logK = 0;
     while ((1 << logK) < K) ++logK;
-    const int H = K / 2 + 1, FB = fft_lines_per_block(K);
+    const int H = K / 2 + 1, FB = fft_lines_per_block(K), FBz = fft_z_lines_per_block(K);
+    // the same points per block for both kinds of pass: FB lines of K or FBz lines of K/2
     const size_t smem = ((size_t)K / 2 + (size_t)FB * K) * sizeof(float4);
     const float4* twg = static_cast<const float4*>(tw);
     float4* S = static_cast<float4*>(spec);
-    const int zchunks = (nf + FB - 1) / FB, lchunks = (H + FB - 1) / FB;
+    const int zchunks = (nf + FBz - 1) / FBz, lchunks = (H + FB - 1) / FB;
     const long long zblocks = (long long)K * K * zchunks, lblocks = (long long)nf * K * lchunks;
     const long long KH = (long long)K * H;
     cudaError_t e;

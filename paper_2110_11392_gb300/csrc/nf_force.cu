@@ -223,6 +223,7 @@ struct Coef {
     float c0, c1, c2;  // Eq. (spline) polynomial in cell units: c0 + r^2 (c2 + c1/r)
     float e0, e1;      // f'(r)/r inside the softening: e1 + e0/r
     float eps2;
+    int dens_defer;    // top hat only in stages where some lane met r < b
 };
 
 // Packed FP32x2 arithmetic (sm_100+ `add/mul/fma.rn.f32x2`): one instruction
@@ -241,15 +242,25 @@ typedef unsigned long long f2;
 #ifndef NF_ADJ_RCP
 #define NF_ADJ_RCP 0
 #endif
-// Unroll depth of the fast pair loops over groups of four sources.
+// Unroll depth of the fast pair loops over groups of four sources, with the
+// r^2 tracking (stages near the sink) and without it (_FAR: the stages of
+// ring 2 and beyond, which need fewer registers).
 #ifndef NF_FWD_UNROLL
 #define NF_FWD_UNROLL 1
 #endif
 #ifndef NF_ADJ_UNROLL
 #define NF_ADJ_UNROLL 1
 #endif
+#ifndef NF_FWD_UNROLL_FAR
+#define NF_FWD_UNROLL_FAR 1
+#endif
+#ifndef NF_ADJ_UNROLL_FAR
+#define NF_ADJ_UNROLL_FAR 1
+#endif
 constexpr int kFwdUnroll = NF_FWD_UNROLL;
 constexpr int kAdjUnroll = NF_ADJ_UNROLL;
+constexpr int kFwdUnrollFar = NF_FWD_UNROLL_FAR;
+constexpr int kAdjUnrollFar = NF_ADJ_UNROLL_FAR;
 
 __device__ __forceinline__ f2 pk(float lo, float hi)
 {
@@ -351,7 +362,7 @@ template <int S, bool DENS, bool TRK = true>
 __device__ __forceinline__ void stage_fwd_fast(const StageView& v, int cnt, SinkSet<S>& k, float& trk, f2 b2)
 {
     const f2 tiny = pk(kTiny, kTiny);
-#pragma unroll kFwdUnroll
+#pragma unroll (TRK ? kFwdUnroll : kFwdUnrollFar)
     for (int q = 0; q < cnt; q += 4) {
         const float4 xs = v.X[q >> 2], ys = v.Y[q >> 2], zs = v.Z[q >> 2];
         const f2 px[2] = {pk(xs.x, xs.y), pk(xs.z, xs.w)};
@@ -376,6 +387,33 @@ __device__ __forceinline__ void stage_fwd_fast(const StageView& v, int cnt, Sink
                 k.sx[s] = fma2(dx, f, k.sx[s]);
                 k.sy[s] = fma2(dy, f, k.sy[s]);
                 k.sz[s] = fma2(dz, f, k.sz[s]);
+            }
+        }
+    }
+}
+
+// Top-hat density term alone, for a stage in which some pair is closer than b
+// (the deferred mode): the same operations in the same order as the fused
+// term of stage_fwd_fast, so both modes give bit-identical sums.
+template <int S>
+__device__ __forceinline__ void stage_density(const StageView& v, int cnt, SinkSet<S>& k, f2 b2)
+{
+    const f2 tiny = pk(kTiny, kTiny);
+#pragma unroll 1
+    for (int q = 0; q < cnt; q += 4) {
+        const float4 xs = v.X[q >> 2], ys = v.Y[q >> 2], zs = v.Z[q >> 2];
+        const f2 px[2] = {pk(xs.x, xs.y), pk(xs.z, xs.w)};
+        const f2 py[2] = {pk(ys.x, ys.y), pk(ys.z, ys.w)};
+        const f2 pz[2] = {pk(zs.x, zs.y), pk(zs.z, zs.w)};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const f2 dx = add2(px[h], k.nx[s]), dy = add2(py[h], k.ny[s]), dz = add2(pz[h], k.nz[s]);
+                f2 r2 = fma2(dx, dx, tiny);
+                r2 = fma2(dy, dy, r2);
+                r2 = fma2(dz, dz, r2);
+                k.sw[s] = add2(k.sw[s], tophat2(r2, b2));
             }
         }
     }
@@ -421,7 +459,7 @@ __device__ __forceinline__ void stage_adj_fast(const StageView& v, int cnt, Sink
 {
     const f2 tiny = pk(kTiny, kTiny);
     const f2 m3 = pk(-3.0f, -3.0f);
-#pragma unroll kAdjUnroll
+#pragma unroll (TRK ? kAdjUnroll : kAdjUnrollFar)
     for (int q = 0; q < cnt; q += 4) {
         const float4 xs = v.X[q >> 2], ys = v.Y[q >> 2], zs = v.Z[q >> 2];
         const float4 gxs = v.GX[q >> 2], gys = v.GY[q >> 2], gzs = v.GZ[q >> 2];
@@ -586,7 +624,7 @@ __device__ __forceinline__ void run_item(const ItemCtx& it, const Coef& cf, f2 b
                                          const float4* __restrict__ rel, const float4* __restrict__ gs,
                                          const WarpBufs& wb, const int* seg_pre,
                                          const int* seg_start, const float* seg_dy, const float* seg_dz,
-                                         float* __restrict__ partial, int Ntot, WsHeader* hdr)
+                                         float4* __restrict__ partial, int pstride, WsHeader* hdr)
 {
     const int lane = threadIdx.x & 31;
     SinkSet<S> k;
@@ -614,6 +652,9 @@ __device__ __forceinline__ void run_item(const ItemCtx& it, const Coef& cf, f2 b
     constexpr int PER = B / 32;
     const bool dens_near_only = lo(b2) <= 1.0f;    // b <= one cell width
     const bool soft_near_only = cf.eps2 <= 1.0f;   // eps_s <= one cell width
+    // deferred top hat (small b): the fast path tracks the smallest r^2 of the
+    // stage anyway, and the term is added only where it is below b^2
+    const bool dens_defer = DENS && cf.dens_defer != 0 && dens_near_only;
     const int nst0 = (it.n_c0 + B - 1) / B;
     const int nst = nst0 + (it.n_src - it.n_c0 + B - 1) / B;
     int cur = 0;
@@ -709,10 +750,15 @@ __device__ __forceinline__ void run_item(const ItemCtx& it, const Coef& cf, f2 b
                 else stage_fwd_fast<S, false, false>(v, cnt, k, trk, b2);
             } else {
                 if constexpr (ADJ) stage_adj_fast<S>(v, cnt, k, trk);
-                else if (dens) stage_fwd_fast<S, DENS>(v, cnt, k, trk, b2);
+                else if (dens && !dens_defer) stage_fwd_fast<S, DENS>(v, cnt, k, trk, b2);
                 else stage_fwd_fast<S, false>(v, cnt, k, trk, b2);
                 exact = __any_sync(kFull, trk < cf.eps2);
                 if (exact && lane == 0) atomicAdd(&hdr->stages_rerun, 1ull);  // rare
+                if constexpr (DENS && !ADJ) {
+                    // a pair closer than b gives a positive term; elsewhere every term is +0
+                    if (dens && dens_defer && !exact && __any_sync(kFull, trk < lo(b2)))
+                        stage_density<S>(v, cnt, k, b2);
+                }
             }
         }
         if (exact) {
@@ -737,11 +783,13 @@ __device__ __forceinline__ void run_item(const ItemCtx& it, const Coef& cf, f2 b
         int at, slot;
         sink_lookup(it, p, &at, &slot);
         if (p < it.n_sink) {
-            const size_t base = (size_t)slot * 4 * (size_t)Ntot + (size_t)at;
-            partial[base] = k.ax[s];
-            partial[base + (size_t)Ntot] = k.ay[s];
-            partial[base + 2 * (size_t)Ntot] = k.az[s];
-            if constexpr (DENS) partial[base + 3 * (size_t)Ntot] = k.aw[s];
+            // the sink's row of partials, by its original index (rel .w)
+            const int e = __float_as_int(reinterpret_cast<const float*>(rel + at)[3]);
+            float* dst = reinterpret_cast<float*>(partial + ((size_t)e * (size_t)pstride + (size_t)slot));
+            dst[0] = k.ax[s];
+            dst[1] = k.ay[s];
+            dst[2] = k.az[s];
+            if constexpr (DENS) dst[3] = k.aw[s];
         }
     }
 }
@@ -752,7 +800,7 @@ template <int SMAX, int B, bool ADJ, int MINB, bool DENS>
 __global__ void __launch_bounds__(256, MINB)
 k_force(const BoxDev* __restrict__ boxes, const int* __restrict__ off, const float4* __restrict__ rel,
         const float4* __restrict__ gs, const int4* __restrict__ items, WsHeader* hdr,
-        float* __restrict__ partial, int Ntot, int max_nseg)
+        float4* __restrict__ partial, int pstride, int max_nseg)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     using W = WarpSmem<B, ADJ>;
@@ -789,6 +837,7 @@ k_force(const BoxDev* __restrict__ boxes, const int* __restrict__ off, const flo
         cf.e0 = Bx.e0;
         cf.e1 = Bx.e1;
         cf.eps2 = Bx.eps2;
+        cf.dens_defer = Bx.dens_defer;
         const f2 b2 = pk(Bx.dens_b2, Bx.dens_b2);
         const int K = it.K, R = it.R;
         const int l = item.x - it.cb;
@@ -845,15 +894,15 @@ k_force(const BoxDev* __restrict__ boxes, const int* __restrict__ off, const flo
         const int S = (n_chunk + 31) >> 5;
         if (SMAX >= 4 && S >= 4)
             run_item<(SMAX >= 4 ? 4 : 1), B, ADJ, DENS>(it, cf, b2, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz,
-                                                  partial, Ntot, hdr);
+                                                  partial, pstride, hdr);
         else if (SMAX >= 3 && S == 3)
             run_item<(SMAX >= 3 ? 3 : 1), B, ADJ, DENS>(it, cf, b2, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz,
-                                                  partial, Ntot, hdr);
+                                                  partial, pstride, hdr);
         else if (SMAX >= 2 && S == 2)
             run_item<(SMAX >= 2 ? 2 : 1), B, ADJ, DENS>(it, cf, b2, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz,
-                                                  partial, Ntot, hdr);
+                                                  partial, pstride, hdr);
         else
-            run_item<1, B, ADJ, DENS>(it, cf, b2, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz, partial, Ntot, hdr);
+            run_item<1, B, ADJ, DENS>(it, cf, b2, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz, partial, pstride, hdr);
         __syncwarp();
     }
 }
@@ -873,11 +922,12 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
 }
 
 __global__ void __launch_bounds__(256)
-k_combine(const BoxDev* __restrict__ boxes, int nboxes, const float* __restrict__ partial,
-          const int* __restrict__ perm, int Ntot, float* __restrict__ out, float* __restrict__ rho,
-          double* __restrict__ chunk_sums, bool adjoint)
+k_combine(const BoxDev* __restrict__ boxes, int nboxes, const float4* __restrict__ partial, int pstride,
+          float* __restrict__ out, float* __restrict__ rho, double* __restrict__ chunk_sums, bool adjoint)
 {
-    // block = one chunk of kCombineChunk sorted slots of a single box
+    // block = one chunk of kCombineChunk particles (original order) of a single box;
+    // a particle's 2R+1 partials are one contiguous row, so the loads and the
+    // output rows of a warp are both contiguous
     __shared__ double red[3][8];
     int chunk = blockIdx.x;
     int lo = 0, hi = nboxes - 1;
@@ -894,29 +944,27 @@ k_combine(const BoxDev* __restrict__ boxes, int nboxes, const float* __restrict_
     const float s_lo = (float)(scale - (double)s_hi);
     const double m = 1.0 / (double)B.N;
     const bool out_aligned8 = (reinterpret_cast<uintptr_t>(out) & 7) == 0;
-    const int s0 = B.part_base + (chunk - B.chunk_base) * kCombineChunk;
-    const int s1 = min(s0 + kCombineChunk, B.part_base + B.N);
+    const int e0 = B.part_base + (chunk - B.chunk_base) * kCombineChunk;
+    const int e1 = min(e0 + kCombineChunk, B.part_base + B.N);
     double net[3] = {0.0, 0.0, 0.0};
     constexpr int kMaxSlots = 2 * NF_MAX_R + 1;
-    for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
-        const int e = perm[s];
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const float4* row_in = partial + (size_t)e * (size_t)pstride;
         // issue every partial load first (they are independent), then sum
-        float v[3][kMaxSlots];
+        float4 v[kMaxSlots];
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int q = 0; q < kMaxSlots; ++q)
-                v[c][q] = q < nslot ? partial[((size_t)q * 4 + c) * (size_t)Ntot + s] : 0.0f;
+        for (int q = 0; q < kMaxSlots; ++q) v[q] = q < nslot ? row_in[q] : make_float4(0.f, 0.f, 0.f, 0.f);
         float a3[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             // the 2R+1 pencil partials, summed without rounding error into (sh, sl)
-            float sh = v[c][0], sl = 0.0f;
+            float sh = c == 0 ? v[0].x : (c == 1 ? v[0].y : v[0].z), sl = 0.0f;
 #pragma unroll
             for (int q = 1; q < kMaxSlots; ++q) {
                 if (q < nslot) {
+                    const float x = c == 0 ? v[q].x : (c == 1 ? v[q].y : v[q].z);
                     float t, err;
-                    two_sum(sh, v[c][q], t, err);
+                    two_sum(sh, x, t, err);
                     sh = t;
                     sl = __fadd_rn(sl, err);
                 }
@@ -944,12 +992,15 @@ k_combine(const BoxDev* __restrict__ boxes, int nboxes, const float* __restrict_
         }
         if (rho) {
             // density partials (b^2 - r^2 sums), compensated, times 1/b^2
-            float sh = partial[(size_t)3 * (size_t)Ntot + s], sl = 0.0f;
-            for (int q = 1; q < nslot; ++q) {
-                float t, err;
-                two_sum(sh, partial[((size_t)q * 4 + 3) * (size_t)Ntot + s], t, err);
-                sh = t;
-                sl = __fadd_rn(sl, err);
+            float sh = v[0].w, sl = 0.0f;
+#pragma unroll
+            for (int q = 1; q < kMaxSlots; ++q) {
+                if (q < nslot) {
+                    float t, err;
+                    two_sum(sh, v[q].w, t, err);
+                    sh = t;
+                    sl = __fadd_rn(sl, err);
+                }
             }
             rho[e] = __fmul_rn(__fadd_rn(sh, sl), B.dens_inv_b2);
         }
@@ -993,7 +1044,7 @@ int grid_for(size_t n, int threads)
 }
 
 typedef void (*ForceKernel)(const BoxDev*, const int*, const float4*, const float4*, const int4*,
-                            WsHeader*, float*, int, int);
+                            WsHeader*, float4*, int, int);
 
 // The lean (85-register) variant is used when the tuning asks for 24 or more
 // resident warps per SM.
@@ -1098,7 +1149,7 @@ cudaError_t launch_gather_g(const float* g, const int* perm, int Ntot, float4* g
 
 cudaError_t launch_force(bool adjoint, bool density, const ForceTuning& t, const BoxDev* boxes,
                          const int* cell_off, const float4* rel, const float4* gs, const int4* items,
-                         WsHeader* hdr, float* partial, int Ntot, int max_nseg, cudaStream_t s)
+                         WsHeader* hdr, float4* partial, int pstride, int max_nseg, cudaStream_t s)
 {
     ForceKernel kfn = pick(adjoint, density, t);
     if (!kfn) return cudaErrorInvalidValue;
@@ -1113,17 +1164,17 @@ cudaError_t launch_force(bool adjoint, bool density, const ForceTuning& t, const
     if (e != cudaSuccess) return e;
     if (nb < 1) return cudaErrorInvalidConfiguration;
     if (t.blocks_per_sm > 0 && t.blocks_per_sm < nb) nb = t.blocks_per_sm;
-    kfn<<<sms * nb, t.warps_per_block * 32, smem, s>>>(boxes, cell_off, rel, gs, items, hdr, partial, Ntot,
+    kfn<<<sms * nb, t.warps_per_block * 32, smem, s>>>(boxes, cell_off, rel, gs, items, hdr, partial, pstride,
                                                        max_nseg);
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_combine(bool adjoint, const BoxDev* boxes, int nboxes, int nchunks, const float* partial,
-                           const int* perm, int Ntot, float* out, float* rho, double* chunk_sums, cudaStream_t s)
+cudaError_t launch_combine(bool adjoint, const BoxDev* boxes, int nboxes, int nchunks, const float4* partial,
+                           int pstride, float* out, float* rho, double* chunk_sums, cudaStream_t s)
 {
     if (nchunks <= 0) return cudaSuccess;
-    k_combine<<<nchunks, 256, 0, s>>>(boxes, nboxes, partial, perm, Ntot, out, rho, chunk_sums, adjoint);
+    k_combine<<<nchunks, 256, 0, s>>>(boxes, nboxes, partial, pstride, out, rho, chunk_sums, adjoint);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -9,8 +9,8 @@
 //   rel         float4 [N]      sorted cell-centred offsets, .w = index bits
 //   perm        int32 [N]       sorted slot -> particle (global index)
 //   items       int4 [<= M]     work items: (global centre cell, chunk, box, -)
-//   partial     float [(2R+1)*4][N]  per-pencil partial sums (ax, ay, az, density),
-//                                    sorted order
+//   partial     float4 [N][2R+1]  per-pencil partial sums (ax, ay, az, density),
+//                                 one row per particle in original order
 // A "global cell" numbers the cells of all boxes of a batch back to back:
 // box b owns cells [cell_base_b, cell_base_b + K_b^3).
 #pragma once
@@ -48,7 +48,9 @@ struct BoxDev {
     float dens_b2, dens_inv_b2;
     // K / box when it is a power of two (then x * K / box is exact in FP32), else 0
     float kl_pow2;
-    float pad1;
+    // 1: the top-hat term runs only in the pair-kernel stages where some pair
+    // is closer than b (small b); 0: it is fused into every stage that can hold one
+    int dens_defer;
 };
 static_assert(sizeof(BoxDev) % 16 == 0, "BoxDev must stay 16-byte aligned");
 
@@ -240,10 +242,11 @@ cudaError_t launch_gather_g(const float* g, const int* perm, int Ntot, float4* g
                             cudaStream_t s);
 cudaError_t launch_force(bool adjoint, bool density, const ForceTuning& t, const BoxDev* boxes,
                          const int* cell_off, const float4* rel, const float4* gs,
-                         const int4* items, WsHeader* hdr, float* partial, int Ntot,
+                         const int4* items, WsHeader* hdr, float4* partial, int pstride,
                          int max_nseg, cudaStream_t s);
+// partial rows of pstride float4 (2 max R + 1) per particle, original order
 cudaError_t launch_combine(bool adjoint, const BoxDev* boxes, int nboxes, int nchunks,
-                           const float* partial, const int* perm, int Ntot, float* out,
+                           const float4* partial, int pstride, float* out,
                            float* rho, double* chunk_sums, cudaStream_t s);
 cudaError_t launch_net(const BoxDev* boxes, int nboxes, const double* chunk_sums,
                        double* net, cudaStream_t s);

@@ -174,3 +174,13 @@ def test_far_arith_switch_on_host():
     assert lib.nf_far_set_arith(5) == _lib.NF_ERR_ARG
     assert lib.nf_far_set_arith(_lib.NF_FAR_FP64) == _lib.NF_OK and lib.nf_far_get_arith() == _lib.NF_FAR_FP64
     assert lib.nf_far_set_arith(before) == _lib.NF_OK
+
+
+def test_density_mode_switch_on_host():
+    lib = _lib.load()
+    assert lib.nf_get_density_mode() == _lib.NF_DENS_AUTO
+    assert lib.nf_set_density_mode(3) == _lib.NF_ERR_ARG
+    assert lib.nf_set_density_mode(-1) == _lib.NF_ERR_ARG
+    assert lib.nf_get_density_mode() == _lib.NF_DENS_AUTO
+    for m in (_lib.NF_DENS_FUSED, _lib.NF_DENS_DEFERRED, _lib.NF_DENS_AUTO):
+        assert lib.nf_set_density_mode(m) == _lib.NF_OK and lib.nf_get_density_mode() == m

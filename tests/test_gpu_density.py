@@ -68,3 +68,33 @@ def test_density_radius_outside_near_field_is_rejected():
     with pytest.raises(_lib.NFError):
         nf.forces_density(to_dev(w.pos), w.box, w.K, w.R, w.eps, 2.01 / w.K)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("b_cells", [0.05, 0.25, 0.5, 2.0])
+def test_fused_and_deferred_density_are_bit_identical(b_cells):
+    """The deferred top hat (a second sweep only over stages with a pair
+    closer than b) runs the fused term's operations in the same order, so
+    rho and acc must be equal bit for bit in both modes (and in auto)."""
+    import torch
+    import paper_2110_11392_gb300 as nf
+    from paper_2110_11392_gb300 import _lib
+    w = config_clustered(N=1 << 18, K=16)
+    pos = to_dev(w.pos)
+    b = b_cells * w.box / w.K
+    before = _lib.nf_get_density_mode()
+    out = {}
+    try:
+        for mode in (_lib.NF_DENS_FUSED, _lib.NF_DENS_DEFERRED, _lib.NF_DENS_AUTO):
+            _lib.nf_set_density_mode(mode)
+            out[mode] = nf.forces_density(pos, w.box, w.K, w.R, w.eps, b)
+        torch.cuda.synchronize()
+    finally:
+        _lib.nf_set_density_mode(before)
+    (a1, r1), (a2, r2), (a0, r0) = out[1], out[2], out[0]
+    assert torch.equal(a1, a2) and torch.equal(a1, a0)
+    assert torch.equal(r1, r2) and torch.equal(r1, r0)
+    if b_cells <= 0.25:
+        idx = sample_sinks(w, 2000, seed=11)
+        ref = oracle.density(w.pos, w.box, w.K, w.R, b, sinks=idx)
+        err = np.abs(r2.cpu().numpy().astype(np.float64)[idx] - ref) / ref
+        assert np.median(err) <= RHO_MEDIAN and err.max() <= RHO_MAX, (np.median(err), err.max())

@@ -283,3 +283,27 @@ def test_the_two_arithmetics_agree(K):
     assert ((t64 - tdf).abs().amax(dim=0) / tscale).max().item() < 1e-12
     with pytest.raises(_lib.NFError):
         _lib.nf_far_set_arith(2)
+
+
+def test_largest_power_of_two_grid_in_both_arithmetics():
+    """K = 256, the largest grid of the radix-4/2 double-float transforms (8 fields per line
+    block, 16 per z block): the double-float far field equals the FP64 one (mixed-radix
+    transforms) to 1e-12.  Low order and few particles keep the buffers small."""
+    import torch
+    import paper_2110_11392_gb300 as nf
+    from paper_2110_11392_gb300 import _lib
+    K = 256
+    pos = to_dev(_uniform(30000, 17))
+    ff = nf.FarField(K, 2, 2)
+    before = _lib.nf_far_get_arith()
+    try:
+        _lib.nf_far_set_arith(_lib.NF_FAR_FP64)
+        a64 = ff(pos)
+        _lib.nf_far_set_arith(_lib.NF_FAR_DOUBLE_FLOAT)
+        adf = ff(pos)
+        torch.cuda.synchronize()
+    finally:
+        _lib.nf_far_set_arith(before)
+    scale = a64.abs().max().item()
+    assert scale > 0
+    assert (a64 - adf).abs().max().item() < 1e-12 * scale
