@@ -30,7 +30,7 @@ std::map<std::pair<int, const void*>, int> g_smem_set;
 
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
-cudaError_t ensure_smem(const void* fn, int bytes)
+cudaError_t ensure_smem(const void* fn, int bytes, bool max_carveout)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -40,6 +40,10 @@ cudaError_t ensure_smem(const void* fn, int bytes)
     auto it = g_smem_set.find(key);
     if (it != g_smem_set.end() && it->second >= bytes) return cudaSuccess;
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    // shared memory over L1 as far as it goes, so that occupancy is set by the
+    // kernel's own limits
+    if (e == cudaSuccess && max_carveout)
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e == cudaSuccess) g_smem_set[key] = bytes;
     return e;
 }

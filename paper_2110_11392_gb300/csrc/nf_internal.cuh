@@ -197,7 +197,7 @@ cudaError_t launch_taylor_forces(int p, const int* off, const float4* rel, const
 // Counts kernel launches (all translation units).
 void count_launches(int n);
 // Sets the dynamic shared-memory limit of a kernel once per (device, size).
-cudaError_t ensure_smem(const void* fn, int bytes);
+cudaError_t ensure_smem(const void* fn, int bytes, bool max_carveout = false);
 
 // ---- launch wrappers (nf_bin.cu) ----
 cudaError_t launch_fill_boxes(const BoxFill& f, BoxDev* boxes, cudaStream_t s);
