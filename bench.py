@@ -52,9 +52,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="large", choices=["plain", "clustered", "medium", "large", "adjoint"],
+    ap.add_argument("--workload", default="large",
+                    choices=["plain", "clustered", "medium", "medium128", "large", "adjoint"],
                     help="large: the 512^3 box (default); medium: the same recipe at 256^3, K = 64 (for "
-                         "profiling at sizes beyond L2); clustered: 128^3; adjoint: 64^3; plain: 32^3 uniform")
+                         "profiling at sizes beyond L2); medium128: 256^3 at K = 128 (the binning of the "
+                         "512^3 box: three sort passes); clustered: 128^3; adjoint: 64^3; plain: 32^3 uniform")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -81,6 +83,8 @@ def make_workload(name: str, rank: int):
         w = W.config_large(seed=2 + 1000 * rank)
     elif name == "medium":
         w = W.config_large(N=256 ** 3, K=64, seed=2 + 1000 * rank)
+    elif name == "medium128":
+        w = W.config_large(N=256 ** 3, K=128, seed=2 + 1000 * rank)
     else:
         w = W.config_adjoint(seed=3 + 1000 * rank)
     g = W.upstream_gradient(w.N, 33 + 1000 * rank)
