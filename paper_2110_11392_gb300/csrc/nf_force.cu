@@ -41,9 +41,11 @@
 // farther than eps_s from every sink gives the same value with f = r^-3
 // alone, so the "fast" path computes only that and tracks the smallest r^2
 // it met; if any lane saw r < eps_s, the warp recomputes the stage with the
-// exact path.  Stages with the item's own centre cell (self pairs) always
-// take the exact path: the source list puts that cell first, in stages of
-// its own; the other source cells follow in rings around it (c_ring).
+// exact path.  The source list puts the item's centre cell first, in stages
+// of its own; the other source cells follow in rings around it (c_ring).
+// A chunk with sinks in the centre cell meets its self pairs there and runs
+// those stages on the exact path from the start; any other chunk runs them
+// on the tracked fast path like the rest of the first ring.
 #include <cuda_runtime.h>
 
 #include "nf_internal.cuh"
@@ -130,8 +132,11 @@ __global__ void k_pencils(const BoxDev* __restrict__ boxes, int nboxes, int Ctot
         const int l = g - cb;
         const int i = l / (K * K), j = (l / K) % K, k = l % K;
         int st;
-        int n_sink = 0;
-        for (int c = -R; c <= R; ++c) n_sink += cell_count(off, cb + (wrap(i + c, K) * K + j) * K + k, &st);
+        int n_sink = 0, c_first = 0;
+        for (int c = -R; c <= R; ++c) {
+            if (c == 0) c_first = n_sink;
+            n_sink += cell_count(off, cb + (wrap(i + c, K) * K + j) * K + k, &st);
+        }
         int n_src = 0;
         for (int b = -R; b <= R; ++b)
             for (int d = -R; d <= R; ++d)
@@ -146,10 +151,14 @@ __global__ void k_pencils(const BoxDev* __restrict__ boxes, int nboxes, int Ctot
         if (nch) atomicAdd(&bucket_count[bk], (unsigned)nch);
         pairs += (unsigned long long)n_sink * (unsigned long long)n_src;
         // every chunk of this pencil runs the centre cell's sources in stages of their
-        // own (exact path) and the rest in stages of SB (the pair kernel's stage_range)
+        // own and the rest in stages of SB (the pair kernel's stage_range); the
+        // chunks holding sinks of the centre cell run those stages exactly
         const int st0 = (occ + SB - 1) / SB;
         stages += (unsigned long long)nch * (unsigned long long)(st0 + (n_src - occ + SB - 1) / SB);
-        stages_exact += (unsigned long long)nch * (unsigned long long)st0;
+        if (occ > 0) {
+            const int self_chunks = (c_first + occ + CH - 1) / CH - c_first / CH;
+            stages_exact += (unsigned long long)self_chunks * (unsigned long long)st0;
+        }
         if (nch) {
             int rem = n_sink - (nch - 1) * CH;
             unsigned long long lanes = (unsigned long long)(nch - 1) * CH + 32ull * ((rem + 31) / 32);
@@ -596,6 +605,8 @@ struct ItemCtx {
     int n_src;
     int n_c0;         // sources of the centre cell (processed first, exact path)
     int n_near;       // sources of the centre cell and its first ring
+    bool has_self;    // some sink of this chunk lies in the centre cell (self pairs)
+    bool near_x;      // some sink of this chunk lies within one cell (in x) of the source plane
 };
 
 // Sorted slot and partial slot of the sink at pencil position p.
@@ -737,11 +748,15 @@ __device__ __forceinline__ void run_item(const ItemCtx& it, const Coef& cf, f2 b
         v.GX = reinterpret_cast<const float4*>(soa + (ADJ ? 3 : 0) * B);
         v.GY = reinterpret_cast<const float4*>(soa + (ADJ ? 4 : 0) * B);
         v.GZ = reinterpret_cast<const float4*>(soa + (ADJ ? 5 : 0) * B);
-        bool exact = st < nst0;
+        // the centre cell's stages hold the self pairs only for chunks with sinks
+        // in that cell; other chunks run them on the tracked fast path
+        bool exact = it.has_self && st < nst0;
         // Sources of ring 2 and beyond are at least one cell away from every
-        // sink of the pencil: the top-hat (b <= one cell) and the softened
-        // branch (eps_s <= one cell) cannot occur there.
-        const bool far = beg >= it.n_near;
+        // sink of the pencil, and every source is more than one cell away from
+        // the sinks of cells two or more cells from the plane in x: the top hat
+        // (b <= one cell) and the softened branch (eps_s <= one cell) cannot
+        // occur there.
+        const bool far = beg >= it.n_near || !it.near_x;
         const bool dens = DENS && (!dens_near_only || !far);
         if (!exact) {
 #pragma unroll
@@ -894,6 +909,16 @@ k_force(const BoxDev* __restrict__ boxes, const int* __restrict__ off, const flo
         it.n_c0 = seg_pre[1];
         it.n_near = seg_pre[nseg < 9 ? nseg : 9];
         const int n_chunk = min(CH, it.n_sink - it.chunk_begin);
+        {
+            const int c_cnt = __shfl_sync(kFull, it.sc_cnt, R);
+            const int c_first = __shfl_sync(kFull, it.sc_incl, R) - c_cnt;  // pencil position of the centre cell
+            it.has_self = c_cnt > 0 && it.chunk_begin < c_first + c_cnt && it.chunk_begin + n_chunk > c_first;
+            // sinks of the cells R-1 .. R+1 of the pencil occupy positions [n_lo, n_hi)
+            const int l0 = R > 0 ? R - 1 : 0, l1 = R > 0 ? R + 1 : 0;
+            const int n_lo = __shfl_sync(kFull, it.sc_incl, l0) - __shfl_sync(kFull, it.sc_cnt, l0);
+            const int n_hi = __shfl_sync(kFull, it.sc_incl, l1);
+            it.near_x = it.chunk_begin < n_hi && it.chunk_begin + n_chunk > n_lo;
+        }
         const int S = (n_chunk + 31) >> 5;
         if (SMAX >= 4 && S >= 4)
             run_item<(SMAX >= 4 ? 4 : 1), B, ADJ, DENS>(it, cf, b2, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz,

@@ -167,8 +167,9 @@ def test_stats_pair_count():
 def test_stage_counters_match_the_work_list():
     """nf_stage_stats_read: the pair kernel's stages and exact-from-start stages equal the count
     implied by the cell occupancies (each pencil chunk runs its centre cell's sources in
-    stages of their own, the rest of the plane in stages of the tuning's size); re-runs are
-    rare and never more than the fast stages."""
+    stages of their own, the rest of the plane in stages of the tuning's size; only the
+    chunks holding sinks of the centre cell run those stages exactly from the start);
+    re-runs are rare and never more than the fast stages."""
     import torch
     from paper_2110_11392_gb300 import _lib
     from workloads import config_adjoint
@@ -177,6 +178,7 @@ def test_stage_counters_match_the_work_list():
     n = np.diff(off).reshape(w.K, w.K, w.K).astype(np.int64)
     R = w.R
     sink = sum(np.roll(n, -c, axis=0) for c in range(-R, R + 1))
+    before = sum(np.roll(n, -c, axis=0) for c in range(-R, 0))    # sinks of the pencil ahead of its centre cell
     src = sum(np.roll(n, (-b, -d), axis=(1, 2)) for b in range(-R, R + 1) for d in range(-R, R + 1))
     pos = torch.from_numpy(w.pos).cuda()
     g = torch.from_numpy(np.ones_like(w.pos)).cuda()
@@ -186,7 +188,9 @@ def test_stage_counters_match_the_work_list():
         S, B = tune[0], tune[1]
         CH = 32 * S
         nch = (sink + CH - 1) // CH
-        exact = int((nch * ((n + B - 1) // B)).sum())
+        self_chunks = np.where(n > 0, (before + n + CH - 1) // CH - before // CH, 0)
+        assert (self_chunks <= nch).all()
+        exact = int((self_chunks * ((n + B - 1) // B)).sum())
         total = int((nch * ((n + B - 1) // B + (src - n + B - 1) // B)).sum())
         if adjoint:
             _lib.nf_forces_adjoint(pos, g, w.box, w.K, R, w.eps, out, ws)
