@@ -148,7 +148,14 @@ __global__ void k_pencils(const BoxDev* __restrict__ boxes, int nboxes, int Ctot
         unsigned long long cost = (unsigned long long)n_src * (unsigned long long)min(n_sink, CH);
         int bk = cost_bucket(cost);
         bucket_of[g] = (unsigned char)bk;
-        if (nch) atomicAdd(&bucket_count[bk], (unsigned)nch);
+        {
+            // one atomic per bucket per warp: most cells of a box fall in a few buckets
+            const unsigned am = __activemask();
+            const int key = nch ? bk : -1;
+            const unsigned peers = __match_any_sync(am, key);
+            const unsigned tot = __reduce_add_sync(peers, (unsigned)nch);
+            if (key >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&bucket_count[bk], tot);
+        }
         pairs += (unsigned long long)n_sink * (unsigned long long)n_src;
         // every chunk of this pencil runs the centre cell's sources in stages of their
         // own and the rest in stages of SB (the pair kernel's stage_range); the
@@ -210,7 +217,25 @@ __global__ void k_items(const BoxDev* __restrict__ boxes, int nboxes, int Ctot,
         int nch = chunks[g];
         if (!nch) continue;
         int b = find_box_by_cell(boxes, nboxes, g);
-        unsigned base = atomicAdd(&cursor[bucket_of[g]], (unsigned)nch);
+        // one atomic per bucket per warp; each lane's chunks follow those of the
+        // lanes below it in the same bucket (the order of items within a bucket
+        // does not change any result)
+        const unsigned am = __activemask();
+        const int bk = bucket_of[g];
+        const unsigned peers = __match_any_sync(am, bk);
+        const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+        unsigned pre = 0, tot = 0;
+        for (int src = 0; src < 32; ++src) {
+            if (!((am >> src) & 1u)) continue;  // the same for every lane of am
+            const unsigned v = __shfl_sync(am, (unsigned)nch, src);
+            if ((peers >> src) & 1u) {
+                tot += v;
+                if (src < lane) pre += v;
+            }
+        }
+        unsigned base = 0;
+        if (lane == leader) base = atomicAdd(&cursor[bk], tot);
+        base = __shfl_sync(peers, base, leader) + pre;
         for (int q = 0; q < nch; ++q) items[base + q] = make_int4(g, q, b, 0);
     }
 }
