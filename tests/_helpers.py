@@ -63,3 +63,28 @@ def sample_sinks(w, count, seed, include_densest=True):
         dense = np.bincount(cid).argmax()
         idx = np.union1d(idx, np.nonzero(cid == dense)[0])
     return np.sort(idx)
+
+
+def dense_pencil_with_close_pairs(seed: int = 21, K: int = 6, per_cell: int = 300, pairs: int = 20):
+    """Positions (box 1) for the pair kernel's stage paths: a dense x-pencil of cells (j, k) = (2, 3),
+    with `per_cell` particles in each cell (so a 128-sink chunk can lie inside one cell, away from the
+    centre cell of its item or two cells from the source plane), plus close pairs (6e-4 box apart)
+    straddling every x-face of the pencil and the y-face to its neighbour pencil.  With eps = 0.002
+    (eps_s = 0.00432) the straddling pairs are inside the softening, so the stages holding them must
+    take the exact path even where no self pair is present."""
+    rng = np.random.default_rng(seed)
+    w = 1.0 / K
+    parts = []
+    for i in range(K):
+        parts.append((np.array([i, 2, 3]) + 0.5 + rng.uniform(-0.45, 0.45, (per_cell, 3))) * w)
+    for i in range(K):
+        xf = ((i + 1) % K) * w
+        for _ in range(pairs):
+            y, z = (2 + rng.uniform(0.05, 0.95)) * w, (3 + rng.uniform(0.05, 0.95)) * w
+            parts.append(np.array([[xf - 3e-4, y, z], [xf + 3e-4, y + 1e-4, z]]))
+        yf = 3 * w
+        for _ in range(pairs):
+            x, z = (i + rng.uniform(0.05, 0.95)) * w, (3 + rng.uniform(0.05, 0.95)) * w
+            parts.append(np.array([[x, yf - 3e-4, z], [x + 1e-4, yf + 3e-4, z]]))
+    x = np.concatenate(parts) % 1.0
+    return x.astype(np.float32)

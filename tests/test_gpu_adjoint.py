@@ -7,7 +7,7 @@ import oracle
 from workloads import config_adjoint, config_plain, fd_sample, uniform_positions, upstream_gradient
 from workloads.recipes import Workload
 
-from _helpers import frac_stats, to_dev
+from _helpers import dense_pencil_with_close_pairs, frac_stats, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -87,6 +87,17 @@ def test_adjoint_softened_and_coincident_pairs():
     g = rng.standard_normal(x.shape).astype(np.float32)
     grad = _gpu_grad(w, g)
     ref = oracle.adjoint(x, g.astype(np.float64), 1.0, 6, 2, 0.004)
+    med, p99, mx = frac_stats(grad, ref)
+    assert med <= ADJ_MEDIAN and mx <= ADJ_MAX, (med, p99, mx)
+
+
+def test_adjoint_dense_pencil_with_close_pairs_across_faces():
+    """The adjoint's stage paths on dense single-cell chunks and close pairs across cell faces."""
+    x = dense_pencil_with_close_pairs(seed=22)
+    w = Workload("dense-pencil", x, 1.0, 6, 2, 0.002)
+    g = np.random.default_rng(23).standard_normal(x.shape).astype(np.float32)
+    grad = _gpu_grad(w, g)
+    ref = oracle.adjoint(x, g.astype(np.float64), 1.0, 6, 2, 0.002)
     med, p99, mx = frac_stats(grad, ref)
     assert med <= ADJ_MEDIAN and mx <= ADJ_MAX, (med, p99, mx)
 

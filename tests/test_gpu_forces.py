@@ -6,7 +6,7 @@ import oracle
 from workloads import clustered_positions, config_adjoint, config_clustered, config_plain, uniform_positions
 from workloads.recipes import Workload
 
-from _helpers import assert_force_parity, gpu_forces, sample_sinks
+from _helpers import assert_force_parity, dense_pencil_with_close_pairs, gpu_forces, sample_sinks
 
 pytestmark = pytest.mark.gpu
 
@@ -110,6 +110,18 @@ def test_softening_regime_and_coincident_particles():
     acc = gpu_forces(w)
     ref = oracle.forces(x, 1.0, 6, 2, eps)
     assert_force_parity(acc, ref, label="softened pairs")
+
+
+@pytest.mark.parametrize("tune", [None, (4, 64, 8, 0), (2, 128, 8, 0), (1, 128, 4, 0)])
+def test_dense_pencil_with_close_pairs_across_faces(tune):
+    """Chunks inside one cell away from their item's centre cell run the centre cell's stages on
+    the tracked fast path, chunks two cells from the source plane skip the tracking; the close
+    pairs straddling the faces must still reach the exact (softened) branch."""
+    x = dense_pencil_with_close_pairs()
+    w = Workload("dense-pencil", x, 1.0, 6, 2, 0.002)
+    acc = gpu_forces(w, tune=tune)
+    ref = oracle.forces(x, 1.0, 6, 2, 0.002)
+    assert_force_parity(acc, ref, label=f"dense pencil {tune}")
 
 
 def test_empty_regions_and_clustered_voids():
