@@ -364,9 +364,12 @@ def run_native(args, rank, world, local):
                 "frac_of_measured_fma": achieved / max(fma["scalar_tflops"], fma["packed_tflops"])}
     hbm = peaks.get("hbm_gbs", 6786.2)
     bin_bytes = 32.0 * N + 8.0 * (w.K ** 3 + 1)
+    bin_traffic = kernel_traffic("bin", args.workload)
     bin_roof = {"bound": "hbm", "achieved": bin_bytes / (bin_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
-                "frac": bin_bytes / (bin_ms / 1e3) / 1e9 / hbm, "traffic": kernel_traffic("bin", args.workload),
-                "bytes_per_particle": 32, "note": "algorithmic bytes: pos 12 + rel 16 + perm 4 per particle + offsets"}
+                "frac": bin_bytes / (bin_ms / 1e3) / 1e9 / hbm, "traffic": bin_traffic,
+                "traffic_gbs": bin_traffic / (bin_ms / 1e3) / 1e9 if bin_traffic else None,
+                "bytes_per_particle": 32, "note": "algorithmic bytes: pos 12 + rel 16 + perm 4 per particle + offsets; "
+                "traffic_gbs: the ncu DRAM bytes of one call over its event time"}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -780,33 +783,43 @@ def measure_e2e(args, w, g_np, dev, P, flush):
         hgr.copy_(grad, non_blocking=True)
 
     def pipelined(n):
+        # per step the forward needs only the positions and the adjoint also g, and the
+        # accelerations can leave while the adjoint runs: the positions go up first, g
+        # second; acc comes down after the forward, the gradient after the adjoint
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        in_done, comp_done, out_done = [ev(), ev()], [ev(), ev()], [ev(), ev()]
+        pos_in, g_in = [ev(), ev()], [ev(), ev()]
+        fwd_done, comp_done, out_done = [ev(), ev()], [ev(), ev()], [ev(), ev()]
+
+        def upload(b):
+            dpos[b].copy_(hp, non_blocking=True)
+            pos_in[b].record(cin)
+            dg[b].copy_(hg, non_blocking=True)
+            g_in[b].record(cin)
+
         t0.record(stream)
         cin.wait_event(t0)
         with torch.cuda.stream(cin):
-            dpos[0].copy_(hp, non_blocking=True)
-            dg[0].copy_(hg, non_blocking=True)
-            in_done[0].record(cin)
+            upload(0)
         for i in range(n):
             b = i % 2
             if i + 1 < n:  # next step's upload into the other buffers, once step i-1 is done with them
                 with torch.cuda.stream(cin):
                     if i >= 1:
                         cin.wait_event(comp_done[1 - b])
-                    dpos[1 - b].copy_(hp, non_blocking=True)
-                    dg[1 - b].copy_(hg, non_blocking=True)
-                    in_done[1 - b].record(cin)
-            stream.wait_event(in_done[b])
+                    upload(1 - b)
+            stream.wait_event(pos_in[b])
             if i >= 2:
                 stream.wait_event(out_done[b])  # step i-2's download of these outputs
             flush.zero_()
             nf.forces(dpos[b], w.box, w.K, w.R, w.eps, out=dacc[b])
+            fwd_done[b].record(stream)
+            stream.wait_event(g_in[b])
             nf.forces_adjoint(dpos[b], dg[b], w.box, w.K, w.R, w.eps, out=dgr[b])
             comp_done[b].record(stream)
             with torch.cuda.stream(cout):
-                cout.wait_event(comp_done[b])
+                cout.wait_event(fwd_done[b])
                 ha.copy_(dacc[b], non_blocking=True)
+                cout.wait_event(comp_done[b])
                 hgr.copy_(dgr[b], non_blocking=True)
                 out_done[b].record(cout)
         stream.wait_event(out_done[(n - 1) % 2])
@@ -833,8 +846,8 @@ def measure_e2e(args, w, g_np, dev, P, flush):
             "d2h_bytes_per_step": 2 * w.pos.nbytes, "steps": n,
             "serial_value": 2 * P * n / tot,
             "note": "pinned host pos and g in, acc and grad out, every step; uploads and downloads on "
-                    "their own streams overlapping the neighbouring steps' compute (serial_value: one "
-                    "step at a time)"}
+                    "their own streams overlapping the compute (positions first, g during the forward; "
+                    "acc during the adjoint, the gradient after it; serial_value: one step at a time)"}
 
 
 def measure_batched(dev, flush, rank=0, world=1):
