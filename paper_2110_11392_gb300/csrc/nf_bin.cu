@@ -78,12 +78,67 @@ __device__ __forceinline__ int cell_coord_fp64(float x, double kl, int K, float*
     return (int)cm;
 }
 
-// The same function in integer arithmetic, used when kl = kl_mant * 2^kl_exp
-// with a short odd mantissa (the unit box: kl = K).  Then t = x * kl, floor(t),
-// t - c and (t - c) - 1/2 are all exact in FP64 for 2^-29 <= |x| < 2^30, so the
-// FP64 definition reduces to one rounding of an exact value, which this path
-// computes with 64-bit integers (the GPU's FP64 pipe is slow).  Other inputs
-// take the FP64 path; both give identical results.
+struct CellCoord {
+    int c;      // cell index in [0, K)
+    float off;  // cell-centred offset
+    int bad;    // non-finite input
+};
+
+// The same function for any K / box and any x.  In integer arithmetic when
+// kl = kl_mant * 2^kl_exp with a short odd mantissa (the unit box: kl = K):
+// then t = x * kl, floor(t), t - c and (t - c) - 1/2 are all exact in FP64 for
+// 2^-29 <= |x| < 2^30, so the FP64 definition reduces to one rounding of an
+// exact value, which this path computes with 64-bit integers (the GPU's FP64
+// pipe is slow).  Other inputs take the FP64 path; both give identical
+// results.  Out of line: the sort passes inline only the power-of-two path of
+// cell_coord, which keeps their code (24 coordinates per thread) small.
+#ifndef NF_BIN_SLOW_NOINLINE
+#define NF_BIN_SLOW_NOINLINE 1
+#endif
+#if NF_BIN_SLOW_NOINLINE
+__device__ __noinline__
+#else
+__device__ __forceinline__
+#endif
+CellCoord cell_coord_general(float x, int K, int kl_mant, int kl_exp, double kl)
+{
+    CellCoord r;
+    r.bad = 0;
+    const unsigned bits = __float_as_uint(x);
+    const int E = (int)((bits >> 23) & 0xFF);
+    if (kl_mant > 0 && E >= 127 - 29 && E < 127 + 30) {
+        const long long P = (long long)((bits & 0x7FFFFFu) | 0x800000u) * (long long)kl_mant;
+        const int s = 150 - E - kl_exp;  // t = +-P * 2^-s
+        if (s >= 1 && s <= 53) {
+            const long long one = 1LL << s;
+            const long long low = P & (one - 1);
+            long long c;
+            long long frac;  // (t - c) * 2^s, in [0, 2^s)
+            if ((int)(bits >> 31) == 0) {
+                c = P >> s;
+                frac = low;
+            } else {
+                c = -(P >> s) - (low != 0);
+                frac = low ? one - low : 0;
+            }
+            const long long o = frac - (one >> 1);
+            // exact scaling of the rounded integer by 2^-s
+            r.off = __ll2float_rn(o) * __int_as_float((127 - s) << 23);
+            if (c >= 0 && c < K) {  // inside the box: no wrap (64-bit % is slow)
+                r.c = (int)c;
+                return r;
+            }
+            long long cm = c % K;
+            r.c = (int)(cm < 0 ? cm + K : cm);
+            return r;
+        }
+    }
+    bool bad = false;
+    r.c = cell_coord_fp64(x, kl, K, &r.off, &bad);
+    r.bad = bad;
+    return r;
+}
+
 __device__ __forceinline__ int cell_coord(float x, const BoxDev& B, float* off, bool* bad)
 {
     // K / box a power of two and x >= 0: t = x * K/box is exact in FP32 as in
@@ -100,32 +155,10 @@ __device__ __forceinline__ int cell_coord(float x, const BoxDev& B, float* off, 
             return ci % B.K;
         }
     }
-    const unsigned bits = __float_as_uint(x);
-    const int E = (int)((bits >> 23) & 0xFF);
-    if (B.kl_mant > 0 && E >= 127 - 29 && E < 127 + 30) {
-        const long long P = (long long)((bits & 0x7FFFFFu) | 0x800000u) * (long long)B.kl_mant;
-        const int s = 150 - E - B.kl_exp;  // t = +-P * 2^-s
-        if (s >= 1 && s <= 53) {
-            const long long one = 1LL << s;
-            const long long low = P & (one - 1);
-            long long c;
-            long long frac;  // (t - c) * 2^s, in [0, 2^s)
-            if ((int)(bits >> 31) == 0) {
-                c = P >> s;
-                frac = low;
-            } else {
-                c = -(P >> s) - (low != 0);
-                frac = low ? one - low : 0;
-            }
-            const long long o = frac - (one >> 1);
-            // exact scaling of the rounded integer by 2^-s
-            *off = __ll2float_rn(o) * __int_as_float((127 - s) << 23);
-            if (c >= 0 && c < B.K) return (int)c;  // inside the box: no wrap (64-bit % is slow)
-            long long cm = c % B.K;
-            return (int)(cm < 0 ? cm + B.K : cm);
-        }
-    }
-    return cell_coord_fp64(x, B.kl, B.K, off, bad);
+    const CellCoord r = cell_coord_general(x, B.K, B.kl_mant, B.kl_exp, B.kl);
+    *off = r.off;
+    if (r.bad) *bad = true;
+    return r.c;
 }
 
 __global__ void k_fill_boxes(BoxFill f, BoxDev* boxes)
@@ -324,6 +357,10 @@ __host__ __device__ constexpr size_t sort_smem_bytes(int B)
 // Resident blocks per SM the register budget is sized for (3: 80 registers;
 // measured on GB300 at 512^3: 5.65 ms per binning call against 6.64 ms with 2
 // and 5.67 ms with 4).  The pass is bound by latency, so occupancy pays.
+// Ranking within a warp: 1 = one ballot per digit bit, 0 = __match_any_sync.
+#ifndef NF_SORT_BALLOT
+#define NF_SORT_BALLOT 1
+#endif
 #ifndef NF_SORT_MINB
 #define NF_SORT_MINB 3
 #endif
@@ -388,7 +425,18 @@ k_sort_pass(const float* __restrict__ pos, const BoxDev* __restrict__ boxes, int
     for (int r = 0; r < R; ++r) {
         const bool valid = w * 32 * R + r * 32 + lane < n;
         const int d = valid ? ((key[r] >> shift) & mask) : B;
+#if NF_SORT_BALLOT
+        // the lanes holding the same digit, one vote per digit bit
+        unsigned peers = __ballot_sync(kFull, valid);
+        if (!valid) peers = ~peers;
+        for (int b = 0; b < bits; ++b) {
+            const bool bit = (d >> b) & 1;
+            const unsigned bal = __ballot_sync(kFull, bit);
+            peers &= bit ? bal : ~bal;
+        }
+#else
         const unsigned peers = __match_any_sync(kFull, d);
+#endif
         const unsigned c = valid ? my[d] : 0u;
         __syncwarp();
         if (valid && lane == __ffs(peers) - 1) my[d] = c + __popc(peers);
