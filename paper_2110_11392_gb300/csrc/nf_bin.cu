@@ -211,6 +211,31 @@ __device__ __forceinline__ void stage_positions(const float* __restrict__ pos, s
     }
 }
 
+// One warp copies the coordinates of its own particles [base, base + n),
+// n <= 32 * kWarpElems, into shared memory (3n floats) with coalesced loads,
+// all of a lane's loads issued before its first store.  Only this warp reads
+// them back, so a __syncwarp orders the copy (no block-wide barrier).
+constexpr int kWarpElems = kSortTile / (kSortWarps * 32);  // elements per lane
+__device__ __forceinline__ void stage_positions_warp(const float* __restrict__ pos, size_t base, int n,
+                                                     float* spos, int lane)
+{
+    const float* src = pos + 3 * base;
+    constexpr int kPer = 3 * kWarpElems * 32 / 4 / 32;  // float4 per lane for a full warp share
+    static_assert(kPer * 4 * 32 == 3 * kWarpElems * 32, "a warp's coordinates split evenly into float4s");
+    if (n == 32 * kWarpElems && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        const float4* s4 = reinterpret_cast<const float4*>(src);
+        float4* d4 = reinterpret_cast<float4*>(spos);
+        float4 t[kPer];
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) t[r] = s4[r * 32 + lane];
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) d4[r * 32 + lane] = t[r];
+    } else {
+        for (int i = lane; i < 3 * n; i += 32) spos[i] = src[i];
+    }
+    __syncwarp();
+}
+
 // Counts of every digit value in each tile, written to M[digit * tiles + tile].
 // FIRST computes the cell ids from the positions (and flags non-finite input).
 template <bool FIRST>
@@ -389,11 +414,13 @@ k_sort_pass(const float* __restrict__ pos, const BoxDev* __restrict__ boxes, int
     for (int d = tid; d < B; d += blockDim.x) s_gbase[d] = M[(size_t)d * tiles + tile];  // scanned: first output slot
     const size_t base = (size_t)tile * kSortTile;
     const int n = (int)min((size_t)kSortTile, (size_t)N - base);
-    // the first pass reads the tile's positions into the (still unused) reorder buffer
+    // the first pass reads the tile's positions into the (still unused) reorder
+    // buffer, each warp its own elements
     float* spos = reinterpret_cast<float*>(sbuf);
     if constexpr (FIRST) {
-        stage_positions(pos, base, n, spos);
-        __syncthreads();
+        const int lo = w * 32 * kWarpElems;
+        const int nw = n - lo < 0 ? 0 : (n - lo > 32 * kWarpElems ? 32 * kWarpElems : n - lo);
+        stage_positions_warp(pos, base + lo, nw, spos + 3 * lo, lane);
     }
 
     // load: warp w owns the consecutive elements [w*32R, (w+1)*32R) of the tile
@@ -456,6 +483,9 @@ k_sort_pass(const float* __restrict__ pos, const BoxDev* __restrict__ boxes, int
     }
     __syncthreads();
     block_scan_array(s_start, B);  // first slot of every digit's run in the tile
+    // output slot of tile position i = s_gbase[d] - s_start[d] + i (mod 2^32; the
+    // result is below N): one table read per element below
+    for (int d = tid; d < B; d += blockDim.x) s_gbase[d] -= s_start[d];
     // reorder the tile in shared memory
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -474,7 +504,7 @@ k_sort_pass(const float* __restrict__ pos, const BoxDev* __restrict__ boxes, int
     for (int i = tid; i < n; i += blockDim.x) {
         const int k = skey[i];
         const int d = (k >> shift) & mask;
-        const size_t g = (size_t)s_gbase[d] + (size_t)(i - (int)s_start[d]);
+        const size_t g = (size_t)(s_gbase[d] + (unsigned)i);
         if (g >= (size_t)N) continue;  // never: the scanned counts keep every run inside the output
         const float4 x = sbuf[i];
         rel_out[g] = x;
