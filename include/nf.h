@@ -489,8 +489,8 @@ int nf_stage_stats_read(void *ws, int64_t *out, void *stream);
  *   bin_ms       cell ids, offsets, radix sort, cell-centred offsets;
  *   worklist_ms  pencil sizes, cost order, work items (and the gather of g);
  *   pair_ms      the persistent force or adjoint kernel alone;
- *   combine_ms   combine of the partial sums (error-free FP32 TwoSum), scatter
- *                and the FP64 net force;
+ *   combine_ms   combine of the partial sums (error-free FP32 TwoSum, one row
+ *                per particle in input order) and the FP64 net force;
  *   total_ms     first event to last. */
 typedef struct {
     double bin_ms;

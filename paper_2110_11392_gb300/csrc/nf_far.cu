@@ -911,6 +911,17 @@ __device__ __forceinline__ void store_far(int orig, double ax, double ay, double
     }
 }
 
+// The double-float Taylor evaluation's three Horner loops fully unrolled
+// (compile-time term offsets: no index arithmetic in the loop body), or not.
+#ifndef NF_TAYLOR_UNROLL
+#define NF_TAYLOR_UNROLL 1
+#endif
+#if NF_TAYLOR_UNROLL
+#define NF_TAYLOR_PRAGMA _Pragma("unroll")
+#else
+#define NF_TAYLOR_PRAGMA _Pragma("unroll 1")
+#endif
+
 template <int P>
 __global__ void __launch_bounds__(128) k_taylor_forces_df(const int* __restrict__ off, const float4* __restrict__ rel,
                                                          const dfl* __restrict__ T, int N, int C, double scale,
@@ -928,14 +939,15 @@ __global__ void __launch_bounds__(128) k_taylor_forces_df(const int* __restrict_
         const float4 r0 = rel[i], r1 = rel[jj];
         dfl F0 = zero, Fx0 = zero, Fy0 = zero, Fz0 = zero;
         dfl F1 = zero, Fx1 = zero, Fy1 = zero, Fz1 = zero;
-#pragma unroll 1
+NF_TAYLOR_PRAGMA
         for (int a = P; a >= 0; --a) {
             const int base_a = NT - (P - a + 3) * (P - a + 2) * (P - a + 1) / 6;
             dfl U0 = zero, Uy0 = zero, Uz0 = zero, U1 = zero, Uy1 = zero, Uz1 = zero;
-#pragma unroll 1
+NF_TAYLOR_PRAGMA
             for (int b = P - a; b >= 0; --b) {
                 const int base = base_a + b * (P - a + 1) - b * (b - 1) / 2;
                 dfl S0 = zero, Sz0 = zero, S1 = zero, Sz1 = zero;
+NF_TAYLOR_PRAGMA
                 for (int c = P - a - b; c >= 0; --c) {
                     const float2 t0 = __ldg(reinterpret_cast<const float2*>(T0 + base + c));
                     const float2 t1 = __ldg(reinterpret_cast<const float2*>(T1 + base + c));

@@ -961,9 +961,9 @@ k_force(const BoxDev* __restrict__ boxes, const int* __restrict__ off, const flo
 }
 
 // ---------------------------------------------------------------------------
-// Combine: sum the 2R+1 partials without rounding error (FP32 TwoSum into a
-// hi/lo pair), scale by a float-pair constant, round once, scatter to input
-// order; the optional net force is an FP64 sum
+// Combine: per particle in input order, sum its row of 2R+1 partials without
+// rounding error (FP32 TwoSum into a hi/lo pair), scale by a float-pair
+// constant, round once; the optional net force is an FP64 sum
 // ---------------------------------------------------------------------------
 
 // Error-free sum of two floats: s + e == a + b exactly (Knuth's TwoSum).
