@@ -1039,6 +1039,7 @@ int far_prepare(const float* pos, int64_t N, double box, int K, int R, int p, co
 struct Binned {
     const int32_t* off;
     const float4* rel;
+    const int32_t* keys;  // cell id of every sorted slot
 };
 
 int run_far(const FarCall& fc, const float* pos, int64_t N, double box, int K, int p, const void* derivs,
@@ -1051,6 +1052,7 @@ int run_far(const FarCall& fc, const float* pos, int64_t N, double box, int K, i
     auto mark = [&](int i) { return profile ? prof_mark(i, s) : cudaSuccess; };
     const int32_t* off = binned ? binned->off : at<int32_t>(ws, pl.o_off);
     const float4* rel = binned ? binned->rel : at<float4>(ws, pl.o_rel);
+    const int32_t* keys = binned ? binned->keys : at<int32_t>(ws, pl.o_keys_a);  // sorted cell ids
     NF_CUDA(mark(0), "profile");
     if (!binned) {
         int rc = run_binning(pl, pos, ws, at<int32_t>(ws, pl.o_off), at<float4>(ws, pl.o_rel),
@@ -1122,7 +1124,7 @@ int run_far(const FarCall& fc, const float* pos, int64_t N, double box, int K, i
     NF_CUDA(mark(3), "profile");
     const double scale = 1.0 / ((double)N * (box / K));  // m / w: cell-unit gradient to box units
     if ((acc_far || acc_add) && dfl)
-        NF_CUDA(launch_taylor_forces_df(p, off, rel, at<void>(ws, F.o_Tdf), (int)N, C, scale, acc_far, acc_add, s),
+        NF_CUDA(launch_taylor_forces_df(p, keys, rel, at<void>(ws, F.o_Tdf), (int)N, C, scale, acc_far, acc_add, s),
                 "Taylor forces (double-float)");
     else if (acc_far || acc_add)
         NF_CUDA(launch_taylor_forces(p, off, rel, T, (int)N, C, 1.0, scale, acc_far, acc_add, s), "Taylor forces");
@@ -1169,7 +1171,7 @@ int nf_forces_total(const float* pos, int64_t N, double box, int K, int R, doubl
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     rc = run_forces(pn, false, t, pos, nullptr, acc, nullptr, nullptr, ws, s);
     if (rc) return rc;
-    const Binned bn{at<int32_t>(ws, pn.o_off), at<float4>(ws, pn.o_rel)};
+    const Binned bn{at<int32_t>(ws, pn.o_off), at<float4>(ws, pn.o_rel), at<int32_t>(ws, pn.o_keys_a)};
     rc = run_far(fc, pos, N, box, K, p, derivs, nullptr, acc, nullptr, ws_far, s, false, &bn);
     if (rc) return rc;
     rc = finish_call(ws_far, s);
@@ -1202,7 +1204,7 @@ int nf_kdk_step_far(float* pos, float* vel, float* acc, int64_t N, double box, i
     NF_CUDA(launch_drift(pos, vel, (int)N, dt, (float)box, s), "drift");
     rc = run_forces(pn, false, t, pos, nullptr, acc, nullptr, nullptr, ws, s);
     if (rc) return rc;
-    const Binned bn{at<int32_t>(ws, pn.o_off), at<float4>(ws, pn.o_rel)};
+    const Binned bn{at<int32_t>(ws, pn.o_off), at<float4>(ws, pn.o_rel), at<int32_t>(ws, pn.o_keys_a)};
     rc = run_far(fc, pos, N, box, K, p, derivs, nullptr, acc, nullptr, ws_far, s, false, &bn);
     if (rc) return rc;
     NF_CUDA(launch_kick(vel, acc, (int)N, dt, 0.5, s), "kick");

@@ -788,7 +788,10 @@ __global__ void k_to_df(const double* __restrict__ src, long long n, dfl* __rest
 // error-free transformations stay on scalar FP32 instructions: in probes the
 // packed .f32x2 form of the same sequence did not always keep the product's
 // rounding error, depending on the surrounding code.)
-constexpr int kMpChunk = 32;
+#ifndef NF_MP_CHUNK
+#define NF_MP_CHUNK 32
+#endif
+constexpr int kMpChunk = NF_MP_CHUNK;
 template <int P>
 __global__ void k_multipoles_red_df(const int* __restrict__ off, const float4* __restrict__ rel, int C,
                                     const int* __restrict__ rseg, const int* __restrict__ rk,
@@ -883,19 +886,6 @@ __global__ void k_multipoles_red_df(const int* __restrict__ off, const float4* _
 // independent chains keep the FP32 pipe busy.  The steps skip the
 // renormalisation (df_fma_f_nr, 11 instructions); the sums are converted to
 // FP64 as hi + lo at the end.
-__device__ __forceinline__ int cell_of_slot(const int* __restrict__ off, int C, int i)
-{
-    int lo = 0, hi = C;  // off[lo] <= i < off[hi]
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(off + mid) <= i)
-            lo = mid;
-        else
-            hi = mid;
-    }
-    return lo;
-}
-
 __device__ __forceinline__ void store_far(int orig, double ax, double ay, double az, double* __restrict__ acc_far,
                                           float* __restrict__ acc_add)
 {
@@ -923,7 +913,7 @@ __device__ __forceinline__ void store_far(int orig, double ax, double ay, double
 #endif
 
 template <int P>
-__global__ void __launch_bounds__(128) k_taylor_forces_df(const int* __restrict__ off, const float4* __restrict__ rel,
+__global__ void __launch_bounds__(128) k_taylor_forces_df(const int* __restrict__ cell, const float4* __restrict__ rel,
                                                          const dfl* __restrict__ T, int N, int C, double scale,
                                                          double* __restrict__ acc_far, float* __restrict__ acc_add)
 {
@@ -934,8 +924,9 @@ __global__ void __launch_bounds__(128) k_taylor_forces_df(const int* __restrict_
         const int j = i + half;                 // the second particle (may be past the end)
         const bool two = j < N;
         const int jj = two ? j : i;             // evaluate something valid, store only if two
-        const dfl* __restrict__ T0 = T + (size_t)cell_of_slot(off, C, i) * NT;
-        const dfl* __restrict__ T1 = T + (size_t)cell_of_slot(off, C, jj) * NT;
+        // the binning's sorted cell ids give each slot's cell (no search of the offsets)
+        const dfl* __restrict__ T0 = T + (size_t)cell[i] * NT;
+        const dfl* __restrict__ T1 = T + (size_t)cell[jj] * NT;
         const float4 r0 = rel[i], r1 = rel[jj];
         dfl F0 = zero, Fx0 = zero, Fy0 = zero, Fz0 = zero;
         dfl F1 = zero, Fx1 = zero, Fy1 = zero, Fz1 = zero;
@@ -1738,7 +1729,7 @@ cudaError_t launch_multipoles_red_df(const int* off, const float4* rel, int C, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_taylor_forces_df(int p, const int* off, const float4* rel, const void* Tdf, int N, int C,
+cudaError_t launch_taylor_forces_df(int p, const int* cell, const float4* rel, const void* Tdf, int N, int C,
                                     double scale, double* acc_far, float* acc_add, cudaStream_t s)
 {
     const dfl* Td = static_cast<const dfl*>(Tdf);
@@ -1747,7 +1738,7 @@ cudaError_t launch_taylor_forces_df(int p, const int* off, const float4* rel, co
     switch (p) {
 #define NF_TAYLOR_DF_CASE(P)                                                                        \
     case P:                                                                                         \
-        k_taylor_forces_df<P><<<grid, 128, 0, s>>>(off, rel, Td, N, C, scale, acc_far, acc_add);    \
+        k_taylor_forces_df<P><<<grid, 128, 0, s>>>(cell, rel, Td, N, C, scale, acc_far, acc_add);   \
         break;
         NF_TAYLOR_DF_CASE(0)
         NF_TAYLOR_DF_CASE(1)

@@ -186,7 +186,8 @@ cudaError_t launch_far_fft_df(int K, int nf, bool forward, const void* real_in, 
 cudaError_t launch_far_contract_df(int K, int nout, const int* seg, const FarPair* pairs, const void* pcoef,
                                    const void* Dr, const void* Mh, void* Th, cudaStream_t s);
 cudaError_t launch_to_df(const double* src, long long n, void* dst, cudaStream_t s);
-cudaError_t launch_taylor_forces_df(int p, const int* off, const float4* rel, const void* Tdf, int N, int C,
+// cell: the cell id of every sorted slot (the binning's sorted keys)
+cudaError_t launch_taylor_forces_df(int p, const int* cell, const float4* rel, const void* Tdf, int N, int C,
                                     double scale, double* acc_far, float* acc_add, cudaStream_t s);
 // Th[n][q] for nout output fields (the reduced Taylors) from the pair table
 cudaError_t launch_far_contract(int K, int nout, const int* seg, const FarPair* pairs, const double* Dr,
