@@ -126,51 +126,54 @@ __global__ void k_pencils(const BoxDev* __restrict__ boxes, int nboxes, int Ctot
 {
     unsigned long long pairs = 0, lane_pairs = 0, stages = 0, stages_exact = 0;
     int max_occ = 0;
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < Ctot; g += gridDim.x * blockDim.x) {
-        const BoxDev& B = boxes[find_box_by_cell(boxes, nboxes, g)];
-        const int K = B.K, R = B.R, cb = B.cell_base;
-        const int l = g - cb;
-        const int i = l / (K * K), j = (l / K) % K, k = l % K;
-        int st;
-        int n_sink = 0, c_first = 0;
-        for (int c = -R; c <= R; ++c) {
-            if (c == 0) c_first = n_sink;
-            n_sink += cell_count(off, cb + (wrap(i + c, K) * K + j) * K + k, &st);
+    // every lane of a warp runs the same iterations (blockDim is a multiple of
+    // 32), so the warp-wide votes below see all 32 lanes
+    for (int gb = blockIdx.x * blockDim.x; gb < Ctot; gb += gridDim.x * blockDim.x) {
+        const int g = gb + (int)threadIdx.x;
+        int nch = 0, bk = 0;
+        if (g < Ctot) {
+            const BoxDev& B = boxes[find_box_by_cell(boxes, nboxes, g)];
+            const int K = B.K, R = B.R, cb = B.cell_base;
+            const int l = g - cb;
+            const int i = l / (K * K), j = (l / K) % K, k = l % K;
+            int st;
+            int n_sink = 0, c_first = 0;
+            for (int c = -R; c <= R; ++c) {
+                if (c == 0) c_first = n_sink;
+                n_sink += cell_count(off, cb + (wrap(i + c, K) * K + j) * K + k, &st);
+            }
+            int n_src = 0;
+            for (int b = -R; b <= R; ++b)
+                for (int d = -R; d <= R; ++d)
+                    n_src += cell_count(off, cb + (i * K + wrap(j + b, K)) * K + wrap(k + d, K), &st);
+            int occ = cell_count(off, g, &st);
+            max_occ = max(max_occ, occ);
+            nch = (n_sink + CH - 1) / CH;
+            chunks[g] = nch;
+            unsigned long long cost = (unsigned long long)n_src * (unsigned long long)min(n_sink, CH);
+            bk = cost_bucket(cost);
+            bucket_of[g] = (unsigned char)bk;
+            pairs += (unsigned long long)n_sink * (unsigned long long)n_src;
+            // every chunk of this pencil runs the centre cell's sources in stages of their
+            // own and the rest in stages of SB (the pair kernel's stage_range); the
+            // chunks holding sinks of the centre cell run those stages exactly
+            const int st0 = (occ + SB - 1) / SB;
+            stages += (unsigned long long)nch * (unsigned long long)(st0 + (n_src - occ + SB - 1) / SB);
+            if (occ > 0) {
+                const int self_chunks = (c_first + occ + CH - 1) / CH - c_first / CH;
+                stages_exact += (unsigned long long)self_chunks * (unsigned long long)st0;
+            }
+            if (nch) {
+                int rem = n_sink - (nch - 1) * CH;
+                unsigned long long lanes = (unsigned long long)(nch - 1) * CH + 32ull * ((rem + 31) / 32);
+                lane_pairs += lanes * (unsigned long long)n_src;
+            }
         }
-        int n_src = 0;
-        for (int b = -R; b <= R; ++b)
-            for (int d = -R; d <= R; ++d)
-                n_src += cell_count(off, cb + (i * K + wrap(j + b, K)) * K + wrap(k + d, K), &st);
-        int occ = cell_count(off, g, &st);
-        max_occ = max(max_occ, occ);
-        int nch = (n_sink + CH - 1) / CH;
-        chunks[g] = nch;
-        unsigned long long cost = (unsigned long long)n_src * (unsigned long long)min(n_sink, CH);
-        int bk = cost_bucket(cost);
-        bucket_of[g] = (unsigned char)bk;
-        {
-            // one atomic per bucket per warp: most cells of a box fall in a few buckets
-            const unsigned am = __activemask();
-            const int key = nch ? bk : -1;
-            const unsigned peers = __match_any_sync(am, key);
-            const unsigned tot = __reduce_add_sync(peers, (unsigned)nch);
-            if (key >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&bucket_count[bk], tot);
-        }
-        pairs += (unsigned long long)n_sink * (unsigned long long)n_src;
-        // every chunk of this pencil runs the centre cell's sources in stages of their
-        // own and the rest in stages of SB (the pair kernel's stage_range); the
-        // chunks holding sinks of the centre cell run those stages exactly
-        const int st0 = (occ + SB - 1) / SB;
-        stages += (unsigned long long)nch * (unsigned long long)(st0 + (n_src - occ + SB - 1) / SB);
-        if (occ > 0) {
-            const int self_chunks = (c_first + occ + CH - 1) / CH - c_first / CH;
-            stages_exact += (unsigned long long)self_chunks * (unsigned long long)st0;
-        }
-        if (nch) {
-            int rem = n_sink - (nch - 1) * CH;
-            unsigned long long lanes = (unsigned long long)(nch - 1) * CH + 32ull * ((rem + 31) / 32);
-            lane_pairs += lanes * (unsigned long long)n_src;
-        }
+        // one atomic per bucket per warp: most cells of a box fall in a few buckets
+        const int key = nch ? bk : -1;
+        const unsigned peers = __match_any_sync(kFull, key);
+        const unsigned tot = __reduce_add_sync(peers, (unsigned)nch);
+        if (key >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&bucket_count[bk], tot);
     }
     for (int o = 16; o; o >>= 1) {
         pairs += __shfl_xor_sync(kFull, pairs, o);
@@ -213,30 +216,32 @@ __global__ void k_items(const BoxDev* __restrict__ boxes, int nboxes, int Ctot,
                         const int* __restrict__ chunks, const unsigned char* __restrict__ bucket_of,
                         unsigned* __restrict__ cursor, int4* __restrict__ items)
 {
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < Ctot; g += gridDim.x * blockDim.x) {
-        int nch = chunks[g];
-        if (!nch) continue;
-        int b = find_box_by_cell(boxes, nboxes, g);
+    // every lane of a warp runs the same iterations (blockDim is a multiple of 32)
+    const int lane = threadIdx.x & 31;
+    for (int gb = blockIdx.x * blockDim.x; gb < Ctot; gb += gridDim.x * blockDim.x) {
+        const int g = gb + (int)threadIdx.x;
+        const int nch = g < Ctot ? chunks[g] : 0;
+        const int bk = nch ? (int)bucket_of[g] : -1;
         // one atomic per bucket per warp; each lane's chunks follow those of the
         // lanes below it in the same bucket (the order of items within a bucket
         // does not change any result)
-        const unsigned am = __activemask();
-        const int bk = bucket_of[g];
-        const unsigned peers = __match_any_sync(am, bk);
-        const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+        const unsigned peers = __match_any_sync(kFull, bk);
+        const int leader = __ffs(peers) - 1;
         unsigned pre = 0, tot = 0;
         for (int src = 0; src < 32; ++src) {
-            if (!((am >> src) & 1u)) continue;  // the same for every lane of am
-            const unsigned v = __shfl_sync(am, (unsigned)nch, src);
+            const unsigned v = __shfl_sync(kFull, (unsigned)nch, src);
             if ((peers >> src) & 1u) {
                 tot += v;
                 if (src < lane) pre += v;
             }
         }
         unsigned base = 0;
-        if (lane == leader) base = atomicAdd(&cursor[bk], tot);
-        base = __shfl_sync(peers, base, leader) + pre;
-        for (int q = 0; q < nch; ++q) items[base + q] = make_int4(g, q, b, 0);
+        if (nch && lane == leader) base = atomicAdd(&cursor[bk], tot);
+        base = __shfl_sync(kFull, base, leader) + pre;
+        if (nch) {
+            const int b = find_box_by_cell(boxes, nboxes, g);
+            for (int q = 0; q < nch; ++q) items[base + q] = make_int4(g, q, b, 0);
+        }
     }
 }
 
