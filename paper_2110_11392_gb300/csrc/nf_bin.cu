@@ -16,8 +16,9 @@
 //                each particle's cell id and cell-centred offsets from its
 //                position, later passes read them back; a tile ranks its
 //                particles by digit in input order (each warp ranks its own
-//                consecutive elements with __match_any_sync), reorders the
-//                tile in shared memory and writes every run contiguously.  The
+//                consecutive elements, finding the lanes with the same digit
+//                by one vote per digit bit), reorders the tile in shared
+//                memory and writes every run contiguously.  The
 //                offsets travel with the particle (float4, .w = original
 //                index), so no pass gathers positions at random;
 //   k_cell_off   cell_offsets from the sorted cell ids (the first slot of
