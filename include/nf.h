@@ -184,9 +184,13 @@ typedef struct {
  *                   many as fit.  Asking for 24 or more warps per SM
  *                   (warps_per_block * blocks_per_sm) with sinks_per_lane <= 2
  *                   selects the register-lean build of the kernel (at most
- *                   85 registers per thread).
+ *                   85 registers per thread); asking for 1 with stage 128
+ *                   and 3 or 4 sinks per lane selects the build that has the
+ *                   whole register file (up to 255 registers per thread;
+ *                   not for nf_forces_density, which then runs its usual
+ *                   build at one block per SM).
  * Unsupported combinations are rejected with NF_ERR_ARG.  The built-in
- * default is {2, 128, 8, 0}. */
+ * defaults are below. */
 typedef struct {
     int sinks_per_lane;
     int stage;
@@ -198,7 +202,7 @@ typedef struct {
  * (nf_forces, nf_forces_density, nf_forces_batched, the time steps and
  * nf_forces_total) and one for the adjoint calls (nf_forces_adjoint,
  * nf_forces_adjoint_batched).  The built-in defaults, measured best on GB300,
- * are {4, 128, 8, 0} forward and {2, 128, 8, 0} adjoint.
+ * are {4, 128, 8, 0} forward and {4, 128, 8, 1} adjoint.
  * nf_set_default_tuning copies *t (validated) into both; NULL restores both
  * built-ins.  nf_set_default_tuning_adjoint sets the adjoint's alone (NULL:
  * its built-in).  All are process-wide and not thread-safe against running

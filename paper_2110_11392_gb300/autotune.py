@@ -24,6 +24,7 @@ Tuning = Tuple[int, int, int, int]
 CANDIDATES: List[Tuning] = [
     (2, 128, 8, 0), (2, 64, 8, 0), (2, 128, 4, 0), (3, 128, 8, 0), (3, 64, 8, 0), (4, 128, 8, 0), (4, 64, 8, 0),
     (2, 128, 8, 3), (2, 64, 8, 3), (1, 128, 8, 3), (1, 64, 8, 3), (1, 128, 8, 0),
+    (4, 128, 8, 1), (3, 128, 8, 1),
 ]
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "nf_tuning.json")

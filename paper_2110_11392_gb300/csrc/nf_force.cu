@@ -949,18 +949,19 @@ k_force(const BoxDev* __restrict__ boxes, const int* __restrict__ off, const flo
             const int n_hi = __shfl_sync(kFull, it.sc_incl, l1);
             it.near_x = it.chunk_begin < n_hi && it.chunk_begin + n_chunk > n_lo;
         }
-        const int S = (n_chunk + 31) >> 5;
-        if (SMAX >= 4 && S >= 4)
-            run_item<(SMAX >= 4 ? 4 : 1), B, ADJ, DENS>(it, cf, b2, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz,
-                                                  partial, pstride, hdr);
-        else if (SMAX >= 3 && S == 3)
-            run_item<(SMAX >= 3 ? 3 : 1), B, ADJ, DENS>(it, cf, b2, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz,
-                                                  partial, pstride, hdr);
-        else if (SMAX >= 2 && S == 2)
-            run_item<(SMAX >= 2 ? 2 : 1), B, ADJ, DENS>(it, cf, b2, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz,
-                                                  partial, pstride, hdr);
-        else
-            run_item<1, B, ADJ, DENS>(it, cf, b2, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz, partial, pstride, hdr);
+        const int S = (n_chunk + 31) >> 5;  // <= SMAX
+#define NF_RUN_ITEM(SS)                                                                                   \
+    run_item<(SMAX >= SS ? SS : 1), B, ADJ, DENS>(it, cf, b2, rel, gs, wb, seg_pre, seg_start, seg_dy, seg_dz, \
+                                                  partial, pstride, hdr)
+        if (SMAX >= 8 && S == 8) NF_RUN_ITEM(8);
+        else if (SMAX >= 7 && S == 7) NF_RUN_ITEM(7);
+        else if (SMAX >= 6 && S == 6) NF_RUN_ITEM(6);
+        else if (SMAX >= 5 && S == 5) NF_RUN_ITEM(5);
+        else if (SMAX >= 4 && S == 4) NF_RUN_ITEM(4);
+        else if (SMAX >= 3 && S == 3) NF_RUN_ITEM(3);
+        else if (SMAX >= 2 && S == 2) NF_RUN_ITEM(2);
+        else NF_RUN_ITEM(1);
+#undef NF_RUN_ITEM
         __syncwarp();
     }
 }
@@ -1112,6 +1113,12 @@ template <bool ADJ, bool DENS>
 ForceKernel pick_kernel(const ForceTuning& t)
 {
     const int smax = t.sinks_per_lane, stage = t.stage;
+    if (t.blocks_per_sm == 1 && stage == 128 && !DENS) {
+        // one resident block of 8 warps per SM: the whole register file, so
+        // three or four sinks per lane fit the adjoint without spills
+        if (smax == 4) return k_force<4, 128, ADJ, 1, DENS>;
+        if (smax == 3) return k_force<3, 128, ADJ, 1, DENS>;
+    }
     if (wants_lean(t)) {
         if (stage == 128) {
             if (smax == 2) return k_force<2, 128, ADJ, 3, DENS>;

@@ -35,7 +35,7 @@ def test_header_symbols_exported():
 def test_version_and_default_tuning():
     assert "sm_103a" in _lib.nf_version()
     assert _lib.nf_get_default_tuning() == (4, 128, 8, 0)
-    assert _lib.nf_get_default_tuning_adjoint() == (2, 128, 8, 0)
+    assert _lib.nf_get_default_tuning_adjoint() == (4, 128, 8, 1)
     # setting the default sets both directions; the adjoint's can then differ; NULL restores both
     _lib.nf_set_default_tuning((2, 64, 4, 0))
     assert _lib.nf_get_default_tuning() == (2, 64, 4, 0) == _lib.nf_get_default_tuning_adjoint()
@@ -46,7 +46,7 @@ def test_version_and_default_tuning():
         _lib.nf_set_default_tuning_adjoint((3, 96, 8, 0))
     _lib.nf_set_default_tuning(None)
     assert _lib.nf_get_default_tuning() == (4, 128, 8, 0)
-    assert _lib.nf_get_default_tuning_adjoint() == (2, 128, 8, 0)
+    assert _lib.nf_get_default_tuning_adjoint() == (4, 128, 8, 1)
 
 
 def test_workspace_bytes():

@@ -115,3 +115,23 @@ def test_adjoint_ragged(N, K, R):
     ref = oracle.adjoint(x, g.astype(np.float64), 1.0, K, R, eps)
     med, p99, mx = frac_stats(grad, ref)
     assert med <= ADJ_MEDIAN and mx <= ADJ_MAX, (med, p99, mx)
+
+
+@pytest.mark.parametrize("tune", [(1, 64, 4, 0), (2, 128, 8, 0), (4, 128, 8, 0), (3, 128, 8, 1), (4, 128, 8, 1)])
+def test_adjoint_tunings_meet_parity(tune):
+    """The adjoint kernel variants (sinks per lane, stage, warps, blocks per SM; one block per SM
+    selects the build with the whole register file) against the FP64 oracle gradient."""
+    import torch
+    from paper_2110_11392_gb300 import _lib
+    w = config_plain()
+    g = upstream_gradient(w.N, 34)
+    box = dict(N=w.N, K=w.K, R=w.R, eps=w.eps, box=w.box)
+    arr = _lib.make_boxes([box])
+    ws = torch.empty(_lib.nf_workspace_bytes_batched([box]), dtype=torch.uint8, device="cuda")
+    pos = to_dev(w.pos)
+    out = torch.empty_like(pos)
+    _lib.nf_forces_adjoint_batched(arr, pos, to_dev(g), out, tune, ws)
+    torch.cuda.synchronize()
+    ref = oracle.adjoint(w.pos, g.astype(np.float64), w.box, w.K, w.R, w.eps)
+    med, p99, mx = frac_stats(out.cpu().numpy(), ref)
+    assert med <= ADJ_MEDIAN and mx <= ADJ_MAX, (tune, med, p99, mx)

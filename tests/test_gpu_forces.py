@@ -112,7 +112,7 @@ def test_softening_regime_and_coincident_particles():
     assert_force_parity(acc, ref, label="softened pairs")
 
 
-@pytest.mark.parametrize("tune", [None, (4, 64, 8, 0), (2, 128, 8, 0), (1, 128, 4, 0)])
+@pytest.mark.parametrize("tune", [None, (4, 64, 8, 0), (2, 128, 8, 0), (1, 128, 4, 0), (4, 128, 8, 1)])
 def test_dense_pencil_with_close_pairs_across_faces(tune):
     """Chunks inside one cell away from their item's centre cell run the centre cell's stages on
     the tracked fast path, chunks two cells from the source plane skip the tracking; the close
@@ -135,7 +135,7 @@ def test_empty_regions_and_clustered_voids():
 
 
 @pytest.mark.parametrize("tune", [(1, 64, 4, 0), (2, 128, 8, 0), (4, 64, 8, 0), (4, 128, 4, 1),
-                                  (2, 64, 8, 2)])
+                                  (2, 64, 8, 2), (3, 128, 8, 1), (4, 128, 8, 1)])
 def test_all_tunings_meet_parity(tune):
     w = config_plain()
     acc = gpu_forces(w, tune=tune)
